@@ -1,0 +1,336 @@
+/*
+ * CPU ORACLE for DAWN (Feng et al., "DAWN: Matrix Operation-Optimized Algorithm
+ * for Shortest Paths Problem on Unweighted Graphs", ICS '24).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path calls this file; only
+ * the tests, the smoke check and the CPU-baseline leg of the benchmark do.  It
+ * shares no code, header or table with the CUDA library.  It is plain,
+ * single-threaded and deliberately slow: every loop follows the paper's
+ * algorithm in its own order, with dense Boolean vectors where the paper has
+ * them.
+ *
+ * Conventions (readings of the paper, see the design notes):
+ *   - dist[v] = -1 means "no path"; dist[src] = 0.  The paper uses 0 for
+ *     "unset", which collides with the source's own distance (Thm 1 requires
+ *     i != j), so the source is pre-marked reached with distance 0.
+ *   - step counts from 1: the first expansion stamps distance 1.
+ *   - the outer loop runs while step < n, as printed, and ends early on the
+ *     first step that reaches no new vertex (Sec. 3.1, stop condition 2).
+ *
+ * Functions and the passages they follow:
+ *   oracle_sssp_sovm     Alg. 3 (SOVM), Eq. 5-7: push over CSR rows of alpha.
+ *   oracle_sssp_bovm     Alg. 1 (BOVM), Eq. 2-4: pull over CSC columns with
+ *                        the first-hit exit; merge of alpha and beta after
+ *                        the whole vertex loop.
+ *   oracle_bfs_queue     Alg. 2 (General BFS), FIFO queue.
+ *   oracle_apsp_floyd    brute force on the unit-weight digraph (Floyd-Warshall),
+ *                        small n only.
+ *   oracle_apsp_powers   Thm 1 read literally: d(i,j) = the first k with
+ *                        (A^k)_{ij} != 0, i != j, with Boolean matrix powers
+ *                        (Lemma 1); small n only.
+ *   oracle_certificate   O(n+m) check that a distance vector is the exact
+ *                        unweighted distance from src (Thm 1 with Fact 1).
+ *   oracle_wcc           weakly connected component labels (union-find).
+ *   oracle_msbfs         APSP as SOVM from each listed source (Sec. 3.3,
+ *                        "APSP repeats the SSSP per source"), plus per-source
+ *                        eccentricity (largest finite distance, Table 1's
+ *                        epsilon(i)), distance sum and reached count.
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+/*
+ * Alg. 3, Sparse Optimized Boolean Vector-Matrix Operation.
+ * alpha: the vertices whose distance was set in the previous step (dense bool).
+ * beta:  the vertices whose distance is set in this step (dense bool).
+ * For each alpha[i], every CSR arc i->c with c unset gets beta[c] = 1 and
+ * dist[c] = step; then alpha takes beta and beta is cleared.
+ *
+ * edge_visits (nullable) counts every arc examined; Sec. 3.3 gives its value
+ * as the sum of out-degrees over the reached vertices.  levels (nullable)
+ * receives the number of steps that found at least one vertex.
+ * Returns 0, or -1 on allocation failure / bad source.
+ */
+int oracle_sssp_sovm(int32_t n, const int32_t* row_ptr, const int32_t* col_idx,
+                     int32_t src, int32_t* dist, int64_t* edge_visits, int32_t* levels) {
+    if (n <= 0 || src < 0 || src >= n) return -1;
+    uint8_t* alpha = (uint8_t*)calloc((size_t)n, 1);
+    uint8_t* beta = (uint8_t*)calloc((size_t)n, 1);
+    if (!alpha || !beta) { free(alpha); free(beta); return -1; }
+    for (int32_t v = 0; v < n; ++v) dist[v] = -1;
+    dist[src] = 0;
+    alpha[src] = 1;
+    int64_t visits = 0;
+    int32_t found_levels = 0;
+    int32_t step = 0;
+    while (step < n) {
+        step += 1;
+        int converged = 1;
+        for (int32_t i = 0; i < n; ++i) {
+            if (!alpha[i]) continue;
+            int32_t start = row_ptr[i], end = row_ptr[i + 1];
+            for (int32_t j = start; j < end; ++j) {
+                int32_t c = col_idx[j];
+                visits += 1;
+                if (dist[c] == -1) {
+                    beta[c] = 1;
+                    dist[c] = step;
+                    converged = 0;
+                }
+            }
+        }
+        /* alpha <- beta, beta <- 0 ("reset the vector by swap") */
+        uint8_t* t = alpha;
+        alpha = beta;
+        beta = t;
+        memset(beta, 0, (size_t)n);
+        if (converged) break;
+        found_levels = step;
+    }
+    free(alpha);
+    free(beta);
+    if (edge_visits) *edge_visits = visits;
+    if (levels) *levels = found_levels;
+    return 0;
+}
+
+/*
+ * Alg. 1, Boolean Vector-Matrix Operation, on the CSC (in-adjacency) of the
+ * graph: csc_ptr[i]..csc_ptr[i+1] lists the in-neighbours of i.
+ * alpha: every vertex reached so far (dense bool).  For each i not in alpha,
+ * the compressed inner product of Eq. 4 is evaluated over i's in-neighbours
+ * and stops at the first in-neighbour in alpha; then beta[i] = 1 and
+ * dist[i] = step.  alpha <- alpha OR beta and beta <- 0 happen after the whole
+ * i loop, so that every test in a step sees the vertex set of the step start.
+ */
+int oracle_sssp_bovm(int32_t n, const int32_t* csc_ptr, const int32_t* csc_row,
+                     int32_t src, int32_t* dist, int32_t* levels) {
+    if (n <= 0 || src < 0 || src >= n) return -1;
+    uint8_t* alpha = (uint8_t*)calloc((size_t)n, 1);
+    uint8_t* beta = (uint8_t*)calloc((size_t)n, 1);
+    if (!alpha || !beta) { free(alpha); free(beta); return -1; }
+    for (int32_t v = 0; v < n; ++v) dist[v] = -1;
+    dist[src] = 0;
+    alpha[src] = 1;
+    int32_t found_levels = 0;
+    int32_t step = 0;
+    while (step < n) {
+        step += 1;
+        int converged = 1;
+        for (int32_t i = 0; i < n; ++i) {
+            if (alpha[i]) continue;
+            int32_t start = csc_ptr[i], end = csc_ptr[i + 1];
+            for (int32_t j = start; j < end; ++j) {
+                int32_t r = csc_row[j];
+                if (alpha[r] && r != i) {
+                    beta[i] = 1;
+                    dist[i] = step;
+                    converged = 0;
+                    break;
+                }
+            }
+        }
+        for (int32_t i = 0; i < n; ++i) {
+            alpha[i] = (uint8_t)(alpha[i] | beta[i]);
+            beta[i] = 0;
+        }
+        if (converged) break;
+        found_levels = step;
+    }
+    free(alpha);
+    free(beta);
+    if (levels) *levels = found_levels;
+    return 0;
+}
+
+/* Alg. 2, General BFS, with a FIFO queue; a popped vertex i stamps
+ * dist[i] + 1 on every unset out-neighbour and enqueues it. */
+int oracle_bfs_queue(int32_t n, const int32_t* row_ptr, const int32_t* col_idx,
+                     int32_t src, int32_t* dist) {
+    if (n <= 0 || src < 0 || src >= n) return -1;
+    int32_t* q = (int32_t*)malloc((size_t)n * sizeof(int32_t));
+    if (!q) return -1;
+    for (int32_t v = 0; v < n; ++v) dist[v] = -1;
+    int64_t head = 0, tail = 0;
+    dist[src] = 0;
+    q[tail++] = src;
+    while (head < tail) {
+        int32_t i = q[head++];
+        for (int32_t j = row_ptr[i]; j < row_ptr[i + 1]; ++j) {
+            int32_t c = col_idx[j];
+            if (dist[c] == -1) {
+                dist[c] = dist[i] + 1;
+                q[tail++] = c;
+            }
+        }
+    }
+    free(q);
+    return 0;
+}
+
+/* Floyd-Warshall on the unit-weight digraph; d is n*n row-major, -1 = no path. */
+int oracle_apsp_floyd(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, int32_t* d) {
+    if (n <= 0 || n > 4096) return -1;
+    const int32_t INF = 0x3fffffff;
+    for (int64_t x = 0; x < (int64_t)n * n; ++x) d[x] = INF;
+    for (int32_t i = 0; i < n; ++i) {
+        d[(int64_t)i * n + i] = 0;
+        for (int32_t j = row_ptr[i]; j < row_ptr[i + 1]; ++j) {
+            int32_t c = col_idx[j];
+            if (c != i) d[(int64_t)i * n + c] = 1;
+        }
+    }
+    for (int32_t k = 0; k < n; ++k)
+        for (int32_t i = 0; i < n; ++i) {
+            int32_t dik = d[(int64_t)i * n + k];
+            if (dik == INF) continue;
+            for (int32_t j = 0; j < n; ++j) {
+                int32_t via = dik + d[(int64_t)k * n + j];
+                if (d[(int64_t)k * n + j] != INF && via < d[(int64_t)i * n + j])
+                    d[(int64_t)i * n + j] = via;
+            }
+        }
+    for (int64_t x = 0; x < (int64_t)n * n; ++x)
+        if (d[x] == INF) d[x] = -1;
+    return 0;
+}
+
+/*
+ * Thm 1 with Lemma 1: with P_k = Boolean A^k, d(i,j) for i != j is the first
+ * k in 1..n-1 with P_k[i][j] = 1; d(i,i) = 0; never set = -1.
+ * P_{k+1}[i][j] = OR_l P_k[i][l] AND A[l][j].  O(n^4) worst case: small n only.
+ */
+int oracle_apsp_powers(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, int32_t* d) {
+    if (n <= 0 || n > 512) return -1;
+    size_t nn = (size_t)n * n;
+    uint8_t* A = (uint8_t*)calloc(nn, 1);
+    uint8_t* P = (uint8_t*)calloc(nn, 1);
+    uint8_t* Q = (uint8_t*)calloc(nn, 1);
+    if (!A || !P || !Q) { free(A); free(P); free(Q); return -1; }
+    for (int32_t i = 0; i < n; ++i)
+        for (int32_t j = row_ptr[i]; j < row_ptr[i + 1]; ++j) A[(size_t)i * n + col_idx[j]] = 1;
+    for (size_t x = 0; x < nn; ++x) d[x] = -1;
+    for (int32_t i = 0; i < n; ++i) d[(size_t)i * n + i] = 0;
+    memcpy(P, A, nn); /* P = A^1 */
+    for (int32_t k = 1; k < n; ++k) {
+        int any_new = 0;
+        for (int32_t i = 0; i < n; ++i)
+            for (int32_t j = 0; j < n; ++j)
+                if (i != j && P[(size_t)i * n + j] && d[(size_t)i * n + j] == -1) {
+                    d[(size_t)i * n + j] = k;
+                    any_new = 1;
+                }
+        (void)any_new;
+        /* Q = P * A over (OR, AND) */
+        memset(Q, 0, nn);
+        for (int32_t i = 0; i < n; ++i)
+            for (int32_t l = 0; l < n; ++l) {
+                if (!P[(size_t)i * n + l]) continue;
+                const uint8_t* arow = A + (size_t)l * n;
+                uint8_t* qrow = Q + (size_t)i * n;
+                for (int32_t j = 0; j < n; ++j) qrow[j] |= arow[j];
+            }
+        uint8_t* t = P; P = Q; Q = t;
+    }
+    free(A); free(P); free(Q);
+    return 0;
+}
+
+/*
+ * Certificate that dist is the exact unweighted distance vector from src.
+ * Returns 0 when all hold, otherwise the number of the first failed item:
+ *   1  dist[src] != 0, or some v != src has dist 0, or some dist < -1
+ *   2  an arc (u,v) with dist[u] >= 0 has dist[v] == -1 or dist[v] > dist[u]+1
+ *   3  some v with dist[v] > 0 has no in-neighbour u with dist[u] == dist[v]-1
+ * Items 1-3 together characterise the distance vector: item 2 closes the
+ * reached set under out-arcs and bounds dist above by the true distance;
+ * item 3 exhibits a path of length dist[v] from src, bounding it below.
+ * `bad` (nullable) receives the offending vertex.
+ */
+int oracle_certificate(int32_t n, const int32_t* row_ptr, const int32_t* col_idx,
+                       int32_t src, const int32_t* dist, int32_t* bad) {
+    if (bad) *bad = -1;
+    if (src < 0 || src >= n || dist[src] != 0) { if (bad) *bad = src; return 1; }
+    for (int32_t v = 0; v < n; ++v)
+        if (dist[v] < -1 || (dist[v] == 0 && v != src)) { if (bad) *bad = v; return 1; }
+    uint8_t* supported = (uint8_t*)calloc((size_t)n, 1);
+    if (!supported) return -1;
+    for (int32_t u = 0; u < n; ++u) {
+        if (dist[u] < 0) continue;
+        for (int32_t j = row_ptr[u]; j < row_ptr[u + 1]; ++j) {
+            int32_t v = col_idx[j];
+            if (dist[v] == -1 || dist[v] > dist[u] + 1) {
+                free(supported);
+                if (bad) *bad = v;
+                return 2;
+            }
+            if (dist[v] == dist[u] + 1) supported[v] = 1;
+        }
+    }
+    for (int32_t v = 0; v < n; ++v)
+        if (dist[v] > 0 && !supported[v]) {
+            free(supported);
+            if (bad) *bad = v;
+            return 3;
+        }
+    free(supported);
+    return 0;
+}
+
+static int32_t uf_find(int32_t* p, int32_t x) {
+    while (p[x] != x) {
+        p[x] = p[p[x]];
+        x = p[x];
+    }
+    return x;
+}
+
+/* Weakly connected components: label[v] = smallest vertex id of v's WCC. */
+int oracle_wcc(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, int32_t* label) {
+    int32_t* p = (int32_t*)malloc((size_t)n * sizeof(int32_t));
+    if (!p) return -1;
+    for (int32_t v = 0; v < n; ++v) p[v] = v;
+    for (int32_t u = 0; u < n; ++u)
+        for (int32_t j = row_ptr[u]; j < row_ptr[u + 1]; ++j) {
+            int32_t a = uf_find(p, u), b = uf_find(p, col_idx[j]);
+            if (a == b) continue;
+            if (a < b) p[b] = a; else p[a] = b;
+        }
+    for (int32_t v = 0; v < n; ++v) label[v] = uf_find(p, v);
+    free(p);
+    return 0;
+}
+
+/*
+ * APSP-style batch: SOVM from each of the k sources.  dist_block (nullable) is
+ * k x n source-major int32.  ecc[s] = largest finite distance from sources[s]
+ * (0 for an isolated source), dsum[s] = sum of finite distances, reached[s] =
+ * number of vertices with a finite distance (the source included).
+ */
+int oracle_msbfs(int32_t n, const int32_t* row_ptr, const int32_t* col_idx,
+                 const int32_t* sources, int32_t k, int32_t* dist_block,
+                 int32_t* ecc, int64_t* dsum, int32_t* reached) {
+    int32_t* dist = (int32_t*)malloc((size_t)n * sizeof(int32_t));
+    if (!dist) return -1;
+    for (int32_t s = 0; s < k; ++s) {
+        if (oracle_sssp_sovm(n, row_ptr, col_idx, sources[s], dist, NULL, NULL) != 0) {
+            free(dist);
+            return -1;
+        }
+        int32_t e = 0, r = 0;
+        int64_t sum = 0;
+        for (int32_t v = 0; v < n; ++v) {
+            if (dist[v] < 0) continue;
+            r += 1;
+            sum += dist[v];
+            if (dist[v] > e) e = dist[v];
+        }
+        if (ecc) ecc[s] = e;
+        if (dsum) dsum[s] = sum;
+        if (reached) reached[s] = r;
+        if (dist_block) memcpy(dist_block + (size_t)s * n, dist, (size_t)n * sizeof(int32_t));
+    }
+    free(dist);
+    return 0;
+}

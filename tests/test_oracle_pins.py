@@ -1,0 +1,301 @@
+"""Pins for the CPU oracle: each check ties it to something other than itself.
+
+* closed forms (path, directed cycle, star, complete graph, bond-complete
+  lattice with Manhattan distance, binary tree, empty graph, n = 1);
+* brute force on tiny digraphs: Floyd-Warshall and scipy's unweighted
+  shortest_path (a library routine), both against Alg. 3, Alg. 1 and Alg. 2;
+* Thm 1 / Lemma 1 evaluated independently with numpy integer matrix powers
+  (path counts), against the oracle's Boolean-power routine;
+* the SOVM cost identity of Sec. 3.3: edges examined = sum of out-degrees of
+  the reached vertices;
+* the certificate: accepts exact vectors, rejects every planted off-by-one;
+* WCC labels against scipy's connected_components.
+
+Run against a mutant (``DAWN_ORACLE_SO``) by ``test_oracle_mutants.py``.
+"""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+from scipy.sparse.csgraph import connected_components, shortest_path
+
+import oracle
+from paper_2208_04514_b300 import graphgen as gg
+
+RNG_SEEDS = list(range(40))
+
+
+def random_digraph(seed, n=None, p=None, loops=True, dups=True):
+    rng = np.random.default_rng(seed)
+    n = n or int(rng.integers(1, 48))
+    p = p if p is not None else float(rng.uniform(0.0, 0.25))
+    mask = rng.random((n, n)) < p
+    if not loops:
+        np.fill_diagonal(mask, False)
+    src, dst = np.nonzero(mask)
+    if dups and src.size:
+        k = int(rng.integers(0, src.size + 1))
+        pick = rng.integers(0, src.size, k)
+        src = np.concatenate([src, src[pick]])
+        dst = np.concatenate([dst, dst[pick]])
+    return gg.from_arcs(n, src, dst, f"rand{seed}")
+
+
+def scipy_dist(g, src):
+    n = g.n
+    a = sp.csr_matrix((np.ones(g.m), g.col_idx, g.row_ptr), shape=(n, n))
+    d = shortest_path(a, directed=True, unweighted=True, indices=[src])[0]
+    out = np.where(np.isinf(d), -1, d).astype(np.int64)
+    return out
+
+
+def all_oracle_sssp(g, src):
+    t = gg.transpose(g)
+    return (oracle.sssp_sovm(g.row_ptr, g.col_idx, src),
+            oracle.sssp_bovm(t.row_ptr, t.col_idx, src),
+            oracle.bfs_queue(g.row_ptr, g.col_idx, src))
+
+
+# ------------------------------------------------------------ closed forms --
+
+def path_graph(n, directed):
+    s = np.arange(n - 1)
+    if directed:
+        return gg.from_arcs(n, s, s + 1)
+    return gg.from_arcs(n, np.r_[s, s + 1], np.r_[s + 1, s], symmetric=True)
+
+
+@pytest.mark.parametrize("n", [1, 2, 7, 33])
+def test_path_closed_form(n):
+    g = path_graph(n, directed=False)
+    for src in {0, n // 2, n - 1}:
+        want = np.abs(np.arange(n) - src)
+        for d in all_oracle_sssp(g, src):
+            np.testing.assert_array_equal(d, want)
+    gd = path_graph(n, directed=True)
+    for src in {0, n // 2, n - 1}:
+        want = np.where(np.arange(n) >= src, np.arange(n) - src, -1)
+        for d in all_oracle_sssp(gd, src):
+            np.testing.assert_array_equal(d, want)
+
+
+@pytest.mark.parametrize("n", [2, 5, 40])
+def test_directed_cycle_closed_form(n):
+    s = np.arange(n)
+    g = gg.from_arcs(n, s, (s + 1) % n)
+    for src in range(0, n, max(1, n // 5)):
+        want = (np.arange(n) - src) % n
+        for d in all_oracle_sssp(g, src):
+            np.testing.assert_array_equal(d, want)
+
+
+def test_star_and_complete():
+    n = 17
+    leaves = np.arange(1, n)
+    star = gg.from_arcs(n, np.r_[np.zeros(n - 1, int), leaves], np.r_[leaves, np.zeros(n - 1, int)], symmetric=True)
+    for d in all_oracle_sssp(star, 0):
+        np.testing.assert_array_equal(d, np.r_[0, np.ones(n - 1, int)])
+    for d in all_oracle_sssp(star, 5):
+        want = np.full(n, 2)
+        want[0], want[5] = 1, 0
+        np.testing.assert_array_equal(d, want)
+    i, j = np.nonzero(~np.eye(n, dtype=bool))
+    comp = gg.from_arcs(n, i, j, symmetric=True)
+    for d in all_oracle_sssp(comp, 3):
+        want = np.ones(n, int)
+        want[3] = 0
+        np.testing.assert_array_equal(d, want)
+
+
+@pytest.mark.parametrize("w", [1, 2, 9, 24])
+def test_bond_complete_lattice_is_manhattan(w):
+    g = gg.lattice(w, w, p_delete=0.0, seed=0)
+    assert g.m == 4 * w * (w - 1)
+    r, c = np.divmod(np.arange(w * w), w)
+    for src in {0, w * w - 1, (w // 2) * w + w // 3}:
+        sr, sc = divmod(src, w)
+        want = np.abs(r - sr) + np.abs(c - sc)
+        for d in all_oracle_sssp(g, src):
+            np.testing.assert_array_equal(d, want)
+    _, ecc, dsum, reached = oracle.msbfs(g.row_ptr, g.col_idx, [0], keep_dist=False)
+    assert ecc[0] == 2 * (w - 1)
+    assert dsum[0] == w * w * (w - 1)  # sum over r,c of r + c
+    assert reached[0] == w * w
+
+
+def test_binary_tree_depths():
+    n = 100
+    child = np.arange(1, n)
+    parent = (child - 1) // 2
+    g = gg.from_arcs(n, np.r_[parent, child], np.r_[child, parent], symmetric=True)
+    want = np.floor(np.log2(np.arange(n) + 1)).astype(int)
+    for d in all_oracle_sssp(g, 0):
+        np.testing.assert_array_equal(d, want)
+
+
+def test_empty_and_single():
+    g = gg.from_arcs(6, [], [])
+    for d in all_oracle_sssp(g, 4):
+        np.testing.assert_array_equal(d, [-1, -1, -1, -1, 0, -1])
+    g1 = gg.from_arcs(1, [0], [0])  # one vertex with a self-loop
+    for d in all_oracle_sssp(g1, 0):
+        np.testing.assert_array_equal(d, [0])
+
+
+# -------------------------------------------------- brute force, n <= 48 --
+
+@pytest.mark.parametrize("seed", RNG_SEEDS)
+def test_random_digraphs_vs_floyd_and_scipy(seed):
+    g = random_digraph(seed)
+    fw = oracle.apsp_floyd(g.row_ptr, g.col_idx)
+    for src in range(g.n):
+        ref = scipy_dist(g, src)
+        np.testing.assert_array_equal(fw[src], ref)
+        for d in all_oracle_sssp(g, src):
+            np.testing.assert_array_equal(d, ref)
+
+
+def numpy_path_count_distances(g):
+    """Thm 1 from Lemma 1: (A^k)_ij counts i->j walks of length k; the
+    distance is the first k >= 1 with a non-zero count (i != j)."""
+    n = g.n
+    a = np.zeros((n, n), dtype=np.float64)
+    np.add.at(a, (np.repeat(np.arange(n), g.out_degree()), g.col_idx), 1.0)
+    a = (a > 0).astype(np.float64)
+    d = np.full((n, n), -1, dtype=np.int64)
+    np.fill_diagonal(d, 0)
+    p = a.copy()
+    for k in range(1, n):
+        hit = (p > 0) & (d == -1)
+        d[hit] = k
+        p = np.minimum(p @ a, 1e6)  # counts capped: only non-zero-ness matters
+    return d
+
+
+@pytest.mark.parametrize("seed", RNG_SEEDS[:20])
+def test_boolean_powers_definition(seed):
+    g = random_digraph(1000 + seed, n=int(np.random.default_rng(seed).integers(2, 30)))
+    want = numpy_path_count_distances(g)
+    np.testing.assert_array_equal(oracle.apsp_powers(g.row_ptr, g.col_idx), want)
+    for src in range(g.n):
+        np.testing.assert_array_equal(oracle.sssp_sovm(g.row_ptr, g.col_idx, src), want[src])
+
+
+# ----------------------------------------------------------- cost identity --
+
+@pytest.mark.parametrize("seed", RNG_SEEDS[:10])
+def test_sovm_edge_visits_identity(seed):
+    g = random_digraph(2000 + seed, n=40)
+    deg = g.out_degree()
+    for src in range(0, g.n, 3):
+        d, visits, levels = oracle.sssp_sovm(g.row_ptr, g.col_idx, src, with_stats=True)
+        assert visits == int(deg[d >= 0].sum())
+        assert levels == int(d.max())
+
+
+def test_edge_visits_identity_er():
+    g = gg.erdos_renyi(1024, 8.0, seed=1)
+    deg = g.out_degree()
+    for src in range(4):
+        d, visits, levels = oracle.sssp_sovm(g.row_ptr, g.col_idx, src, with_stats=True)
+        assert visits == int(deg[d >= 0].sum())
+
+
+# ------------------------------------------------------------- certificate --
+
+@pytest.mark.parametrize("seed", RNG_SEEDS[:15])
+def test_certificate_accepts_exact_rejects_planted(seed):
+    g = random_digraph(3000 + seed, n=45, p=0.06)
+    rng = np.random.default_rng(seed)
+    for src in range(0, g.n, 4):
+        d = scipy_dist(g, src).astype(np.int32)
+        assert oracle.certificate(g.row_ptr, g.col_idx, src, d) == (0, -1)
+        for v in rng.choice(g.n, size=min(8, g.n), replace=False):
+            for delta in (-1, 1):
+                bad = d.copy()
+                if bad[v] == -1 and delta == -1:
+                    continue
+                bad[v] = bad[v] + delta if bad[v] >= 0 else 1
+                if v == src and bad[v] < 0:
+                    bad[v] = 1
+                assert oracle.certificate(g.row_ptr, g.col_idx, src, bad)[0] != 0
+            if d[v] >= 0:
+                bad = d.copy()
+                bad[v] = -1
+                assert oracle.certificate(g.row_ptr, g.col_idx, src, bad)[0] != 0
+
+
+def test_certificate_on_er_and_lattice():
+    for g in (gg.erdos_renyi(1024, 8.0, seed=1), gg.lattice(64, 64, 0.1, seed=3)):
+        for src in range(3):
+            d = oracle.bfs_queue(g.row_ptr, g.col_idx, src)
+            np.testing.assert_array_equal(d, scipy_dist(g, src))
+            assert oracle.certificate(g.row_ptr, g.col_idx, src, d)[0] == 0
+
+
+# --------------------------------------------------------------------- WCC --
+
+@pytest.mark.parametrize("seed", RNG_SEEDS[:10])
+def test_wcc_vs_scipy(seed):
+    g = random_digraph(4000 + seed, n=60, p=0.02)
+    lab = oracle.wcc(g.row_ptr, g.col_idx)
+    a = sp.csr_matrix((np.ones(g.m), g.col_idx, g.row_ptr), shape=(g.n, g.n))
+    _, ref = connected_components(a, directed=True, connection="weak")
+    # same partition: labels equal iff scipy labels equal
+    assert ((lab[:, None] == lab[None, :]) == (ref[:, None] == ref[None, :])).all()
+    # label is the smallest id in the component
+    for c in np.unique(lab):
+        assert c == np.nonzero(lab == c)[0].min()
+
+
+def test_unreachable_outside_wcc_symmetric():
+    g = gg.rmat(10, seed=7)
+    lab = oracle.wcc(g.row_ptr, g.col_idx)
+    for src in (0, 1, 2, 3, 4):
+        d = oracle.sssp_sovm(g.row_ptr, g.col_idx, src)
+        np.testing.assert_array_equal(d >= 0, lab == lab[src])
+
+
+# ----------------------------------------------------------------- batches --
+
+def test_msbfs_matches_scipy_rows():
+    g = gg.rmat(9, seed=11)
+    srcs = np.array([0, 5, 17, 100, 511], dtype=np.int32)
+    block, ecc, dsum, reached = oracle.msbfs(g.row_ptr, g.col_idx, srcs)
+    for i, s in enumerate(srcs):
+        ref = scipy_dist(g, int(s))
+        np.testing.assert_array_equal(block[i], ref)
+        fin = ref[ref >= 0]
+        assert ecc[i] == fin.max() and dsum[i] == fin.sum() and reached[i] == fin.size
+
+
+# ---------------------------------------------------------- golden fixtures --
+
+def test_golden_fixtures():
+    """Small hand-derived graphs under tests/golden (derivations in the files)."""
+    from pathlib import Path
+    gdir = Path(__file__).parent / "golden"
+    files = sorted(gdir.glob("hand_*.txt"))
+    assert files, "no golden fixtures"
+    for f in files:
+        n, arcs, cases = parse_golden(f)
+        g = gg.from_arcs(n, [a for a, _ in arcs], [b for _, b in arcs])
+        for src, want in cases:
+            for d in all_oracle_sssp(g, src):
+                np.testing.assert_array_equal(d, want, err_msg=f"{f.name} src={src}")
+
+
+def parse_golden(path):
+    n, arcs, cases = None, [], []
+    for line in path.read_text().splitlines():
+        line = line.split("#", 1)[0].strip()
+        if not line:
+            continue
+        key, _, rest = line.partition(":")
+        vals = [int(x) for x in rest.split()]
+        if key == "n":
+            n = vals[0]
+        elif key == "arc":
+            arcs.append((vals[0], vals[1]))
+        elif key.startswith("dist"):
+            cases.append((int(key.split()[1]), np.array(vals)))
+    return n, arcs, cases
