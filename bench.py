@@ -1,0 +1,347 @@
+#!/usr/bin/env python
+"""Benchmark of the DAWN hot path on B300.
+
+Headline workload (default): single-source DAWN on RMAT scale 20 (2^20
+vertices, edge factor 16, a/b/c/d = .57/.19/.19/.05, ids permuted,
+symmetrised, duplicates and self-loops removed), 64 seeded sources drawn
+from the vertices with out-degree >= 1, run one at a time.  One bench step
+is those 64 single-source runs.  Metric: GTEPS = sum over sources of E_r
+(arcs out of the reached vertices, the SOVM cost of Sec. 3.3) / device time.
+
+Timing: CUDA events on the launching stream around each source's kernel; the
+L2 is flushed (a 512 MiB buffer written) between sources, outside the event
+pair.  W >= 3 untimed warm-up steps, then exactly K timed steps bracketed by a
+barrier and a device synchronize; the max over ranks is reported.  Multi-GPU
+runs are independent replicas (each rank runs the same 64 sources on its own
+copy of the graph; no collective on the data path).
+
+``--impl reference`` times the CPU oracle (Alg. 3, single thread) on the same
+workload, a bounded sample of sources per step.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+from pathlib import Path
+
+import numpy as np
+
+ROOT = Path(__file__).resolve().parent
+sys.path.insert(0, str(ROOT))
+
+METRIC = "SSSP GTEPS; batched sources/s and p50/p99 latency vs plain path, bit-exact"
+WORKLOAD = "rmat20_sssp_64src"
+CONFIG = {
+    "workload": WORKLOAD,
+    "graph": "RMAT scale 20, edge factor 16, a=.57 b=.19 c=.19 d=.05, permuted, symmetrised, dedup, no self-loops, seed 2",
+    "sources": "64 distinct seeded sources (seed 5) with out-degree >= 1, one at a time",
+    "dist": "int32, -1 unreachable",
+    "l2": "flushed between sources (512 MiB buffer written outside the timed event pairs)",
+    "parallelism": "replicas",
+}
+SSSP_SRC = ROOT / "paper_2208_04514_b300" / "csrc" / "sssp.cu"
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def measured_peaks():
+    p = ROOT / "MEASURED_PEAKS.json"
+    if p.exists():
+        d = json.loads(p.read_text())
+        return float(d["hbm_gbs"]), "measured"
+    return 6400.0, "fallback"
+
+
+def recorded_traffic(kernel_src: Path, profile: Path):
+    """Per-launch DRAM bytes recorded in a committed ncu summary, or None when
+    absent or taken on a different version of the kernel source."""
+    if not profile.exists():
+        return None
+    text = profile.read_text()
+    h = re.search(r"kernel_source_sha256:\s*([0-9a-f]+)", text)
+    t = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    if not h or not t:
+        return None
+    cur = hashlib.sha256(kernel_src.read_bytes()).hexdigest()
+    return float(t.group(1)) if h.group(1) == cur[: len(h.group(1))] else None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+        time.sleep(0.25)
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            time.sleep(0.15)
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        if not self.lines:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except (ValueError, IndexError):
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def algorithmic_bytes(n, stats):
+    """B_alg of one SSSP: 4 E_r (col_idx of reached rows) + 8 V_r (their
+    row_ptr pairs) + 8 V_r (frontier enqueue + dequeue) + 4 n (dist output) +
+    pull levels * ceil(n/8) (one pass over the visited bitmap per pull level)."""
+    return 4 * stats["edges"] + 16 * stats["reached"] + 4 * n + stats["pull_steps"] * ((n + 7) // 8)
+
+
+def build_workload():
+    from paper_2208_04514_b300 import graphgen as gg
+    g = gg.rmat(20, 16, 0.57, 0.19, 0.19, seed=2, symmetrise=True)
+    srcs = gg.sample_sources(g, 64, seed=5)
+    return g, srcs
+
+
+# ------------------------------------------------------------ reference arm --
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    g, srcs = build_workload()
+    deg = g.out_degree()
+    budget_s = args.ref_budget_s
+    # each step: sources in order until the step's CPU budget is spent
+    def one_step(offset):
+        t0 = time.perf_counter()
+        edges, done = 0, 0
+        i = offset
+        while True:
+            s = int(srcs[i % len(srcs)])
+            d = oracle.sssp_sovm(g.row_ptr, g.col_idx, s)
+            edges += int(deg[d >= 0].sum())
+            done += 1
+            i += 1
+            if time.perf_counter() - t0 >= budget_s or done >= len(srcs):
+                break
+        return edges, done, time.perf_counter() - t0
+    for w in range(args.warmup):  # warm-up steps: one source each
+        s = int(srcs[w % len(srcs)])
+        oracle.sssp_sovm(g.row_ptr, g.col_idx, s)
+    tot_e, tot_n, tot_t = 0, 0, 0.0
+    for k in range(args.steps):
+        e, d, t = one_step(args.warmup + k)
+        tot_e += e
+        tot_n += d
+        tot_t += t
+    gteps = tot_e / tot_t / 1e9
+    sample = f"{tot_n} of the 64 sources over {args.steps} steps (each step stops after {budget_s:.0f} s)"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": gteps, "unit": "GTEPS",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * tot_t / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int32", "data": "synthetic", "config": CONFIG,
+        "cpu_baseline": {"value": gteps, "unit": "GTEPS", "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": gteps, "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------- GPU arm --
+
+def cpu_baseline(g, srcs, budget_s):
+    import oracle
+    deg = g.out_degree()
+    t0 = time.perf_counter()
+    edges, done = 0, 0
+    for s in srcs:
+        d = oracle.sssp_sovm(g.row_ptr, g.col_idx, int(s))
+        edges += int(deg[d >= 0].sum())
+        done += 1
+        if time.perf_counter() - t0 >= budget_s:
+            break
+    t = time.perf_counter() - t0
+    return {"value": edges / t / 1e9, "unit": "GTEPS", "cores": 1, "kind": "oracle",
+            "sample": f"first {done} of the 64 sources, literal Alg. 3 single-threaded, {t:.1f} s"}
+
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as distrib
+    from paper_2208_04514_b300 import dawn
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        distrib.init_process_group("nccl")
+
+    def barrier():
+        if world > 1:
+            distrib.barrier()
+
+    g, srcs = build_workload()
+    n = g.n
+    stream = torch.cuda.current_stream()
+    h = dawn.dawn_graph_upload(g.row_ptr, g.col_idx, flags=dawn.DAWN_SYMMETRIC, stream=stream)
+    dist = torch.empty((len(srcs), n), dtype=torch.int32, device="cuda")
+    stats = torch.zeros((len(srcs), dawn.STATS_WORDS), dtype=torch.int64, device="cuda")
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.int32, device="cuda")
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in srcs]
+
+    def step():
+        for i, s in enumerate(srcs):
+            flush.fill_(i)
+            ev[i][0].record(stream)
+            dawn.dawn_sssp_async(h, int(s), dist[i], None, stats[i], stream)
+            ev[i][1].record(stream)
+
+    for _ in range(args.warmup):
+        step()
+    dawn.dawn_graph_sync(h, stream)
+    # parity of the warm-up output on the host (certificate on every source)
+    if args.verify:
+        import oracle
+        dh = dist.cpu().numpy()
+        for i, s in enumerate(srcs):
+            rc = oracle.certificate(g.row_ptr, g.col_idx, int(s), dh[i])
+            if rc != (0, -1):
+                raise SystemExit(f"bench: certificate failed for source {s}: {rc}")
+
+    barrier()
+    torch.cuda.synchronize()
+    kernel_ms = 0.0
+    with ClockSampler(local) as clk:
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            step()
+            torch.cuda.synchronize()
+            kernel_ms += sum(a.elapsed_time(b) for a, b in ev)
+        barrier()
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+    dawn.dawn_graph_sync(h, stream)
+    st = [dawn.stats_from_words(r) for r in stats.cpu().numpy()]
+    edges_per_step = sum(x["edges"] for x in st)
+    ms_step = kernel_ms / args.steps
+    # max over ranks of the device time
+    t_ms = torch.tensor([ms_step], dtype=torch.float64, device="cuda")
+    if world > 1:
+        distrib.all_reduce(t_ms, op=distrib.ReduceOp.MAX)
+    ms_step_max = float(t_ms.item())
+    value = world * edges_per_step / (ms_step_max * 1e-3) / 1e9
+
+    # roofline of the persistent SSSP kernel (one launch = one source)
+    peak, peak_kind = measured_peaks()
+    balg = sum(algorithmic_bytes(n, x) for x in st) / len(st)
+    avg_launch_s = ms_step * 1e-3 / len(srcs)
+    achieved = balg / avg_launch_s / 1e9
+    traffic = recorded_traffic(SSSP_SRC, ROOT / "profiles" / "sssp_kernel_rmat20.md")
+
+    # end to end through the public call with a pinned host result buffer
+    host_dist = torch.empty(n, dtype=torch.int32, pin_memory=True)
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        for s in srcs:
+            dawn.dawn_sssp(h, int(s), host_dist, stream)
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / args.steps
+    e2e = {"value": world * edges_per_step / e2e_s / 1e9, "unit": "GTEPS",
+           "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 4 * n * len(srcs),
+           "note": "dawn_sssp with a pinned host dist buffer per source (synchronous call, D2H inside); no L2 flush"}
+
+    dawn.dawn_graph_free(h)
+    if rank != 0:
+        return 0
+    line = {
+        "metric": METRIC, "value": value, "unit": "GTEPS", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step_max, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int32", "data": "synthetic", "config": dict(CONFIG, n=n, m=g.m),
+        "wall_ms_per_step": 1e3 * wall / args.steps,
+        "per_source": {"levels_median": statistics.median(x["levels"] for x in st),
+                       "reached_median": statistics.median(x["reached"] for x in st),
+                       "edges_per_step": edges_per_step,
+                       "push_steps": sum(x["push_steps"] for x in st), "pull_steps": sum(x["pull_steps"] for x in st),
+                       "us_per_source": 1e3 * ms_step / len(srcs)},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic, "kernel": "sssp_kernel",
+                     "peak_kind": f"{peak_kind} hbm_gbs (copy bandwidth)",
+                     "bytes_alg_per_launch": balg},
+        "e2e": e2e,
+        "gpu_launches": args.steps * len(srcs),
+        "clocks": clk.summary(),
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(g, srcs, args.cpu_budget_s)
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        distrib.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["dawn", "reference"], default="dawn")
+    ap.add_argument("--verify", action="store_true", help="certificate-check the warm-up output")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget-s", type=float, default=15.0)
+    ap.add_argument("--ref-budget-s", type=float, default=10.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("at least 3 warm-up steps")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,235 @@
+/*
+ * dawn.h -- C ABI of the B300 (sm_103a) implementation of DAWN's hot path.
+ *
+ * DAWN (Feng et al., ICS '24) computes exact unweighted shortest-path lengths
+ * as a level-synchronous Boolean vector-matrix product over (OR, AND): the
+ * frontier vector alpha is multiplied by the adjacency matrix, the product is
+ * masked by the set of vertices already reached, and every newly reached
+ * vertex gets dist = step (Sec. 3.2 Eq. 2-4 and Alg. 1 "BOVM"; Sec. 3.3
+ * Eq. 5-7 and Alg. 3 "SOVM").  A single source runs until a step reaches no
+ * new vertex (Sec. 3.1, stop condition 2); all-pairs runs it from every
+ * source (Sec. 3.3, the APSP cost T < 2 S_wcc E_wcc).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - Every call returns an int status: DAWN_OK (0) or a DAWN_E_* code below.
+ *    No exception and no CUDA error crosses the ABI.  dawn_last_error()
+ *    gives a human-readable message for the calling thread's last failure.
+ *  - Graphs are CSR, int32: row_ptr[n+1] (row_ptr[0] = 0, non-decreasing,
+ *    row_ptr[n] = m) and col_idx[m] with 0 <= col_idx[j] < n.  Arc i -> c
+ *    exists when c is listed in row i (the paper's A[i][c] = 1).  Duplicate
+ *    arcs and self-loops are tolerated and do not change any result.
+ *    m < 2^31.
+ *  - Distances: dist[v] = number of arcs on a shortest src -> v path
+ *    (Thm 1), dist[src] = 0, dist[v] = -1 when no path exists.  The paper
+ *    writes 0 for "unset"; this ABI reserves 0 for the source and uses -1.
+ *    The result is unique, so every call is bit-exact and deterministic.
+ *  - Pointers marked "host or device" may point to pageable host memory,
+ *    pinned host memory or device memory of the current device; the
+ *    library inspects them with cudaPointerGetAttributes.
+ *  - `stream` is a cudaStream_t (NULL = the legacy default stream).  Calls
+ *    that produce results synchronize `stream` before they return, so caller
+ *    buffers are only borrowed for the duration of the call.
+ *  - A graph handle owns one set of device work buffers: calls on the same
+ *    handle must not run concurrently (from several host threads); calls on
+ *    different handles may.
+ *  - Every device-side wait (the grid barrier between levels, the serving
+ *    loop's polls) is bounded; on expiry the call returns DAWN_E_TIMEOUT and
+ *    the device stays usable.
+ */
+#ifndef DAWN_H
+#define DAWN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define DAWN_API __attribute__((visibility("default")))
+#else
+#define DAWN_API
+#endif
+
+/* ------------------------------------------------------------ status codes */
+#define DAWN_OK          0
+#define DAWN_E_INVALID   1 /* malformed CSR, source out of range, bad k / flags / sizes */
+#define DAWN_E_NOMEM     2 /* device allocation failed, or a request can never fit the budget */
+#define DAWN_E_OVERFLOW  3 /* an int16 distance block would need a level above 32767 */
+#define DAWN_E_TIMEOUT   4 /* a bounded device wait expired */
+#define DAWN_E_CUDA      5 /* a CUDA runtime call failed (see dawn_last_error) */
+#define DAWN_E_STATE     6 /* unknown request id, or a call made in the wrong state */
+
+/* ------------------------------------------------------------- graph flags */
+#define DAWN_DIRECTED    0u /* general digraph: the in-adjacency (CSC) is built on the device */
+#define DAWN_SYMMETRIC   1u /* caller asserts that every arc has its reverse: the CSR is its own CSC */
+
+/* --------------------------------------------------------- traversal modes */
+#define DAWN_MODE_AUTO   0 /* per level: SOVM push or BOVM pull, chosen from frontier counters */
+#define DAWN_MODE_PUSH   1 /* SOVM only (Alg. 3): expand the frontier's CSR rows */
+#define DAWN_MODE_PULL   2 /* BOVM only (Alg. 1): unreached vertices test their in-neighbours */
+
+/* ------------------------------------------------------ dist block layouts */
+#define DAWN_SOURCE_MAJOR 0 /* dist_block[s * n + v] */
+#define DAWN_VERTEX_MAJOR 1 /* dist_block[v * k + s] */
+
+/* ----------------------------------------------------------- request state */
+#define DAWN_REQ_PENDING 0 /* admitted to the queue, not yet on the device */
+#define DAWN_REQ_RUNNING 1 /* some of its sources occupy bit lanes on the device */
+#define DAWN_REQ_DONE    2 /* every distance row is in the caller's buffer */
+#define DAWN_REQ_FAILED  3 /* the request ended with an error (see dawn_serve_poll's return) */
+
+typedef struct dawn_graph* dawn_graph_t;
+typedef struct dawn_server* dawn_server_t;
+
+/*
+ * Copy a CSR graph to the current device and prepare it for traversal.
+ * Defines the adjacency A of Sec. 3.1 (Table 1: "CSR" / "CSC").
+ *   row_ptr  host or device, int32[n+1]; col_idx host or device, int32[m].
+ *   n >= 1, 0 <= m < 2^31, flags = DAWN_DIRECTED or DAWN_SYMMETRIC.
+ * The library validates the CSR on the device (DAWN_E_INVALID with the first
+ * offending index in dawn_last_error), builds the in-adjacency for directed
+ * graphs, and allocates the per-graph work buffers (about 4m + 40n bytes
+ * beyond the CSR for a directed graph, 24n for a symmetric one).  The caller
+ * keeps ownership of its arrays; *out owns the device copy until
+ * dawn_graph_free.  Synchronizes `stream`.
+ */
+DAWN_API int dawn_graph_upload(const int32_t* row_ptr, const int32_t* col_idx, int32_t n, int64_t m,
+                               uint32_t flags, void* stream, dawn_graph_t* out);
+
+/* Release every device buffer of g.  g may be NULL.  Not to be called while a
+ * call on g is in flight or while a server created over g exists. */
+DAWN_API int dawn_graph_free(dawn_graph_t g);
+
+/* n, m and flags of an uploaded graph (any pointer may be NULL). */
+DAWN_API int dawn_graph_info(dawn_graph_t g, int32_t* n, int64_t* m, uint32_t* flags);
+
+/*
+ * Single-source shortest paths (Alg. 3 SOVM and Alg. 1 BOVM, Sec. 3.2-3.3).
+ *   src   0 <= src < n, else DAWN_E_INVALID.
+ *   dist  host or device, int32[n], written in full.
+ * Runs the level loop from src until a step reaches no vertex, in one
+ * persistent cooperative kernel on `stream`, then synchronizes `stream`.
+ * DAWN_MODE_AUTO is used; see dawn_sssp_ex for the other modes.
+ */
+DAWN_API int dawn_sssp(dawn_graph_t g, int32_t src, int32_t* dist, void* stream);
+
+typedef struct {
+    int32_t mode;          /* DAWN_MODE_*; 0 = AUTO */
+    int32_t alpha;         /* push -> pull when m_f * alpha > m_u; 0 = default (15) */
+    int32_t beta;          /* pull -> push when n_f * beta < n and n_f shrank; 0 = default (18) */
+    int32_t blocks_per_sm; /* CTAs per SM of the persistent grid; 0 = occupancy-derived */
+    int64_t spin_limit;    /* grid-barrier spin budget in SM clock cycles; 0 = default (~2 s) */
+} dawn_sssp_opts;
+
+typedef struct {
+    int32_t levels;        /* eccentricity of src: the last step that reached a vertex */
+    int32_t push_steps;    /* levels run as SOVM push */
+    int32_t pull_steps;    /* levels run as BOVM pull */
+    int32_t reserved;
+    int64_t reached;       /* vertices with dist >= 0 (src included) */
+    int64_t edges;         /* E_r: sum of out-degrees of the reached vertices, the
+                              SOVM cost T = E_wcc(i) of Sec. 3.3 */
+} dawn_sssp_stats;
+
+/* dawn_sssp with options (opts may be NULL) and per-call statistics (stats may be NULL). */
+DAWN_API int dawn_sssp_ex(dawn_graph_t g, int32_t src, int32_t* dist, const dawn_sssp_opts* opts,
+                          dawn_sssp_stats* stats, void* stream);
+
+/*
+ * Stream-ordered dawn_sssp_ex: enqueue the level loop and return without
+ * synchronizing, so that many sources (and the caller's own work and events)
+ * can be queued back to back.
+ *   dist_dev   device memory, int32[n] (DAWN_E_INVALID otherwise).
+ *   stats_dev  device memory or NULL; receives this call's dawn_sssp_stats.
+ * A device-side failure (DAWN_E_TIMEOUT) is sticky: later calls on g do no
+ * work until dawn_graph_sync reports and clears it.
+ */
+DAWN_API int dawn_sssp_async(dawn_graph_t g, int32_t src, int32_t* dist_dev, const dawn_sssp_opts* opts,
+                             dawn_sssp_stats* stats_dev, void* stream);
+
+/* Synchronize `stream` and return (then clear) the sticky device status of g:
+ * DAWN_OK, DAWN_E_TIMEOUT or DAWN_E_OVERFLOW. */
+DAWN_API int dawn_graph_sync(dawn_graph_t g, void* stream);
+
+/*
+ * Multi-source (APSP-style) batch: SSSP from each of k sources (Sec. 3.3,
+ * APSP as repeated SSSP), advanced together as bit lanes: 64 * W sources per
+ * pass share each vertex's W uint64 visited words, and one level does
+ * new[v] = (OR over in-neighbours u of visited[u]) AND NOT visited[v].
+ *   sources     host or device, int32[k], each in [0, n); repeats allowed.
+ *   k           >= 1.
+ *   dist_block  host or device or NULL; int16 (dist_bytes = 2) or int32
+ *               (dist_bytes = 4); k x n in `layout` order.  NULL keeps each
+ *               pass's block in a device scratch buffer only (the reductions
+ *               are still produced).
+ *   ecc, dsum, reached  host or device or NULL, int32[k] / int64[k] / int32[k]:
+ *               largest finite distance (epsilon(i) of Table 1; 0 for an
+ *               isolated source), sum of finite distances, count of reached
+ *               vertices (src included).
+ * DAWN_E_OVERFLOW when dist_bytes = 2 and some level exceeds 32767 (the
+ * block is then incomplete; nothing wraps).  Synchronizes `stream`.
+ */
+DAWN_API int dawn_msbfs(dawn_graph_t g, const int32_t* sources, int32_t k, void* dist_block,
+                        int dist_bytes, int layout, int32_t* ecc, int64_t* dsum, void* stream);
+
+typedef struct {
+    int32_t lanes;         /* sources per pass: 64, 128 or 256; 0 = autotuned */
+    int32_t reserved;
+    int64_t spin_limit;    /* as in dawn_sssp_opts */
+} dawn_msbfs_opts;
+
+/* dawn_msbfs with the reached counts and options (reached, opts may be NULL). */
+DAWN_API int dawn_msbfs_ex(dawn_graph_t g, const int32_t* sources, int32_t k, void* dist_block,
+                           int dist_bytes, int layout, int32_t* ecc, int64_t* dsum, int32_t* reached,
+                           const dawn_msbfs_opts* opts, void* stream);
+
+/*
+ * Continuous-batching server over several resident graphs.  Requests name a
+ * graph and k sources; their sources are packed into free bit lanes of that
+ * graph's running batch as lanes free up, so requests that arrive while
+ * others run share the device.  Every lane advances one level per device
+ * iteration; a lane's distance is (iteration - its start iteration), so the
+ * result of a request is identical alone and in any mix.
+ *   graphs          ngraphs handles (borrowed; must outlive the server).
+ *   mem_budget_bytes  device bytes available to admitted requests' distance
+ *                   blocks (k * n * dist_bytes each); 0 = no limit.
+ *   max_lanes       lanes per graph batch: 64, 128 or 256.
+ */
+DAWN_API int dawn_serve_create(const dawn_graph_t* graphs, int ngraphs, size_t mem_budget_bytes,
+                               int max_lanes, dawn_server_t* out);
+
+/*
+ * Enqueue a request (non-blocking).  dist_out: host or device, k x n
+ * source-major, int16 (dist_bytes = 2) or int32 (4); caller-owned, borrowed
+ * until dawn_serve_poll reports DAWN_REQ_DONE or DAWN_REQ_FAILED.
+ * *req_id identifies the request.  DAWN_E_NOMEM when the request alone can
+ * never fit mem_budget_bytes.
+ */
+DAWN_API int dawn_serve_submit(dawn_server_t s, int graph_idx, const int32_t* sources, int32_t k,
+                               int dist_bytes, void* dist_out, uint64_t* req_id);
+
+/* State of a request (DAWN_REQ_*).  Returns the request's error code once it
+ * has failed (e.g. DAWN_E_OVERFLOW), DAWN_E_STATE for an unknown id. */
+DAWN_API int dawn_serve_poll(dawn_server_t s, uint64_t req_id, int* state);
+
+/* Block until every submitted request is done or failed (timeout_ms < 0:
+ * no limit).  DAWN_E_TIMEOUT if the time ran out first. */
+DAWN_API int dawn_serve_drain(dawn_server_t s, int64_t timeout_ms);
+
+/* Drain, stop the server thread and free its buffers. */
+DAWN_API int dawn_serve_destroy(dawn_server_t s);
+
+/* Message of the calling thread's last failed call ("" if none). */
+DAWN_API const char* dawn_last_error(void);
+
+/* Library version, (major << 16) | minor. */
+DAWN_API int dawn_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DAWN_H */

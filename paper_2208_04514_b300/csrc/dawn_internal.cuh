@@ -1,0 +1,105 @@
+// Internal declarations of the DAWN CUDA library (sm_103a).  Not part of the ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+
+#include "dawn.h"
+
+namespace dawn {
+
+// ------------------------------------------------------------------ errors --
+// Thread-local message behind dawn_last_error(); every failing call sets it.
+int fail(int code, const char* fmt, ...);
+int cuda_fail(cudaError_t e, const char* what, const char* file, int line);
+
+#define DAWN_CUDA_TRY(call)                                                      \
+    do {                                                                         \
+        cudaError_t e_ = (call);                                                 \
+        if (e_ != cudaSuccess) return ::dawn::cuda_fail(e_, #call, __FILE__, __LINE__); \
+    } while (0)
+
+// True when p is device (or managed) memory of the current device.
+bool is_device_ptr(const void* p);
+
+// ---------------------------------------------------------- device status --
+// Sticky device-side status word values (0 = fine).
+enum DeviceStatus : int {
+    DEV_OK = 0,
+    DEV_TIMEOUT = 1,   // a bounded grid-barrier wait expired
+    DEV_OVERFLOW = 2,  // an int16 distance would exceed 32767
+};
+
+// Frontier work entries cover at most this many arcs, so that one
+// high-degree vertex is spread over many warps.
+constexpr int kEntryArcs = 256;
+
+// One counter slot per level, padded to its own 128-byte line.  Levels use
+// slots (step % 3): written during step s, read after the barrier that ends
+// step s, reset during step s + 1 (see the level loop in sssp.cu).
+struct alignas(128) CtrSlot {
+    unsigned long long qtail;  // work entries appended to the level's queue
+    unsigned long long nf;     // vertices first reached at this level
+    unsigned long long mf;     // sum of their out-degrees
+    unsigned long long grab;   // next 32-entry group of the input queue to take
+    unsigned long long pad[12];
+};
+
+struct alignas(128) Ctl {
+    unsigned int bar_count;    // arrivals at the current grid barrier
+    unsigned int pad0[31];
+    unsigned int bar_gen;      // barrier generation
+    unsigned int pad1[31];
+    int status;                // sticky DeviceStatus
+    int pad2[31];
+    CtrSlot ctr[3];
+};
+
+// Default barrier spin budget in SM clock cycles (~2 s at 2 GHz).
+constexpr long long kDefaultSpin = 4000000000LL;
+
+}  // namespace dawn
+
+// ------------------------------------------------------------- the graph --
+struct dawn_graph {
+    int device = 0;
+    int sms = 0;
+    int32_t n = 0;
+    int64_t m = 0;
+    uint32_t flags = 0;
+    int32_t nwords = 0;               // ceil(n / 32), bitmap words
+    int32_t* row_ptr = nullptr;       // CSR, device
+    int32_t* col_idx = nullptr;
+    int32_t* in_ptr = nullptr;        // CSC (== CSR when symmetric), device
+    int32_t* in_idx = nullptr;
+    uint32_t* excl = nullptr;         // bit v set: v has no in-arc (or v >= n)
+    // single-source work buffers
+    uint32_t* vis[2] = {nullptr, nullptr};
+    int2* queue[2] = {nullptr, nullptr};
+    int64_t queue_cap = 0;
+    int32_t* dist_tmp = nullptr;      // result staging for host outputs
+    dawn::Ctl* ctl = nullptr;         // device control block
+    dawn_sssp_stats* stats_dev = nullptr;
+    dawn_sssp_stats* stats_host = nullptr;  // pinned
+    int* status_host = nullptr;              // pinned
+    int sssp_blocks_per_sm = 0;       // occupancy of the persistent kernel
+    // multi-source work buffers (allocated on first use)
+    uint64_t* ms_vis[2] = {nullptr, nullptr};
+    int ms_words_cap = 0;             // W capacity of ms_vis
+    void* ms_scratch = nullptr;       // per-pass distance block when the caller passes none
+    size_t ms_scratch_bytes = 0;
+    int32_t* ms_counts = nullptr;     // per-lane per-level new-vertex counts
+    size_t ms_counts_cap = 0;
+    int ms_blocks_per_sm = 0;
+};
+
+namespace dawn {
+// sssp.cu
+int sssp_launch(dawn_graph* g, int32_t src, int32_t* dist_dev, const dawn_sssp_opts* opts,
+                dawn_sssp_stats* stats_dev, cudaStream_t stream);
+int sssp_occupancy(dawn_graph* g);
+// graph.cu
+int graph_sync_status(dawn_graph* g, cudaStream_t stream);
+}  // namespace dawn

@@ -1,0 +1,342 @@
+// Device graph store: CSR upload, validation, in-adjacency (CSC) build and the
+// per-graph work buffers of the single-source level loop.
+//
+// The paper's BOVM (Alg. 1) reads the CSC and SOVM (Alg. 3) the CSR (Sec. 3.3:
+// "SOVM operates on CSR matrices, while BOVM operates on CSC matrices").  For a
+// symmetric graph both are the same array, so nothing is built.
+#include <climits>
+#include <cstring>
+
+#include "dawn_internal.cuh"
+
+namespace dawn {
+namespace {
+
+constexpr int kThreads = 256;
+
+int grid_for(int64_t work, int sms) {
+    int64_t b = (work + kThreads - 1) / kThreads;
+    int64_t cap = (int64_t)sms * 8;
+    if (b > cap) b = cap;
+    return b < 1 ? 1 : (int)b;
+}
+
+// bad[0]: smallest bad row_ptr index; bad[1]: smallest bad col_idx index.
+__global__ void validate_csr_kernel(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                                    int32_t n, long long m, unsigned long long* bad) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const long long t0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    for (long long i = t0; i <= n; i += stride) {
+        int v = rp[i];
+        bool ok = v >= 0 && v <= m;
+        if (i == 0) ok = ok && v == 0;
+        else ok = ok && v >= rp[i - 1];
+        if (i == n) ok = ok && v == m;
+        if (!ok) atomicMin(&bad[0], (unsigned long long)i);
+    }
+    for (long long j = t0; j < m; j += stride) {
+        int c = ci[j];
+        if (c < 0 || c >= n) atomicMin(&bad[1], (unsigned long long)j);
+    }
+}
+
+__global__ void indegree_kernel(const int32_t* __restrict__ ci, long long m, int32_t* indeg) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < m; j += stride)
+        atomicAdd(&indeg[ci[j]], 1);
+}
+
+// Exclusive scan of x[0..n) into y[0..n], y[0] = 0, in three kernels:
+// per-block scan, one-block scan of the block totals, add-back.
+constexpr int kScanBlock = 1024;
+
+__global__ void scan_blocks_kernel(const int32_t* __restrict__ x, int32_t n, int32_t* y, int32_t* sums) {
+    __shared__ int32_t warp_tot[32];
+    const int i = blockIdx.x * kScanBlock + threadIdx.x;
+    int v = i < n ? x[i] : 0;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int s = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        int t = __shfl_up_sync(0xffffffffu, s, o);
+        if (lane >= o) s += t;
+    }
+    if (lane == 31) warp_tot[w] = s;
+    __syncthreads();
+    if (w == 0) {
+        int t = warp_tot[lane];
+        for (int o = 1; o < 32; o <<= 1) {
+            int u = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o) t += u;
+        }
+        warp_tot[lane] = t;
+    }
+    __syncthreads();
+    if (w > 0) s += warp_tot[w - 1];
+    if (i < n) y[i + 1] = s;  // inclusive value lands one slot to the right
+    if (threadIdx.x == kScanBlock - 1) sums[blockIdx.x] = s;
+}
+
+__global__ void scan_sums_kernel(int32_t* sums, int32_t nb) {
+    __shared__ int32_t carry_s;
+    __shared__ int32_t warp_tot[32];
+    if (threadIdx.x == 0) carry_s = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int base = 0; base < nb; base += kScanBlock) {
+        int i = base + threadIdx.x;
+        int v = i < nb ? sums[i] : 0;
+        int s = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            int t = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o) s += t;
+        }
+        if (lane == 31) warp_tot[w] = s;
+        __syncthreads();
+        if (w == 0) {
+            int t = warp_tot[lane];
+            for (int o = 1; o < 32; o <<= 1) {
+                int u = __shfl_up_sync(0xffffffffu, t, o);
+                if (lane >= o) t += u;
+            }
+            warp_tot[lane] = t;
+        }
+        __syncthreads();
+        if (w > 0) s += warp_tot[w - 1];
+        int carry = carry_s;
+        if (i < nb) sums[i] = carry + s - v;  // exclusive block offsets
+        __syncthreads();
+        if (threadIdx.x == kScanBlock - 1) carry_s = carry + s;
+        __syncthreads();
+    }
+}
+
+__global__ void scan_add_kernel(int32_t* y, int32_t n, const int32_t* __restrict__ sums) {
+    const int i = blockIdx.x * kScanBlock + threadIdx.x;
+    if (i < n) y[i + 1] += sums[blockIdx.x];
+    if (i == 0) y[0] = 0;
+}
+
+// Scatter every arc u -> c into column c of the CSC; one warp per row.
+__global__ void csc_scatter_kernel(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                                   int32_t n, int32_t* cursor, int32_t* in_idx) {
+    const int lane = threadIdx.x & 31;
+    const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long u = warp; u < n; u += nwarps) {
+        for (int j = rp[u] + lane; j < rp[u + 1]; j += 32) {
+            int pos = atomicAdd(&cursor[ci[j]], 1);
+            in_idx[pos] = (int32_t)u;
+        }
+    }
+}
+
+// excl bit v = (v >= n) or v has no in-arc: such a vertex is never reached
+// from another vertex, so the pull step never scans it.
+__global__ void excl_kernel(const int32_t* __restrict__ in_ptr, int32_t n, int32_t nwords, uint32_t* excl) {
+    const int stride = gridDim.x * blockDim.x;
+    for (int w = blockIdx.x * blockDim.x + threadIdx.x; w < nwords; w += stride) {
+        uint32_t bits = 0;
+        for (int b = 0; b < 32; ++b) {
+            long long v = (long long)w * 32 + b;
+            if (v >= n || in_ptr[v + 1] == in_ptr[v]) bits |= 1u << b;
+        }
+        excl[w] = bits;
+    }
+}
+
+int exclusive_scan(const int32_t* x, int32_t n, int32_t* y, cudaStream_t st) {
+    int32_t nb = (n + kScanBlock - 1) / kScanBlock;
+    if (nb < 1) nb = 1;
+    int32_t* sums = nullptr;
+    DAWN_CUDA_TRY(cudaMallocAsync((void**)&sums, sizeof(int32_t) * nb, st));
+    scan_blocks_kernel<<<nb, kScanBlock, 0, st>>>(x, n, y, sums);
+    scan_sums_kernel<<<1, kScanBlock, 0, st>>>(sums, nb);
+    scan_add_kernel<<<nb, kScanBlock, 0, st>>>(y, n, sums);
+    DAWN_CUDA_TRY(cudaGetLastError());
+    DAWN_CUDA_TRY(cudaFreeAsync(sums, st));
+    return DAWN_OK;
+}
+
+void release(dawn_graph* g) {
+    if (!g) return;
+    auto f = [](void* p) { if (p) cudaFree(p); };
+    f(g->row_ptr);
+    f(g->col_idx);
+    if (g->in_ptr != g->row_ptr) f(g->in_ptr);
+    if (g->in_idx != g->col_idx) f(g->in_idx);
+    f(g->excl);
+    f(g->vis[0]);
+    f(g->vis[1]);
+    f(g->queue[0]);
+    f(g->queue[1]);
+    f(g->dist_tmp);
+    f(g->ctl);
+    f(g->stats_dev);
+    f(g->ms_vis[0]);
+    f(g->ms_vis[1]);
+    f(g->ms_scratch);
+    f(g->ms_counts);
+    if (g->stats_host) cudaFreeHost(g->stats_host);
+    if (g->status_host) cudaFreeHost(g->status_host);
+    delete g;
+}
+
+int upload(const int32_t* row_ptr, const int32_t* col_idx, int32_t n, int64_t m, uint32_t flags,
+           cudaStream_t st, dawn_graph** out) {
+    dawn_graph* g = new dawn_graph();
+    g->n = n;
+    g->m = m;
+    g->flags = flags;
+    g->nwords = (int32_t)(((int64_t)n + 31) / 32);
+    DAWN_CUDA_TRY(cudaGetDevice(&g->device));
+    DAWN_CUDA_TRY(cudaDeviceGetAttribute(&g->sms, cudaDevAttrMultiProcessorCount, g->device));
+    const size_t mb = sizeof(int32_t) * (size_t)(m > 0 ? m : 1);
+    // words rounded up to a multiple of 4 so that 16-byte vector access stays in bounds
+    const size_t wb = sizeof(uint32_t) * (size_t)((g->nwords + 3) / 4 * 4);
+    auto alloc = [&](void** p, size_t bytes) { return cudaMalloc(p, bytes); };
+    cudaError_t e = cudaSuccess;
+    if ((e = alloc((void**)&g->row_ptr, sizeof(int32_t) * ((size_t)n + 1))) != cudaSuccess ||
+        (e = alloc((void**)&g->col_idx, mb)) != cudaSuccess) {
+        release(g);
+        return cuda_fail(e, "cudaMalloc(csr)", __FILE__, __LINE__);
+    }
+    e = cudaMemcpyAsync(g->row_ptr, row_ptr, sizeof(int32_t) * ((size_t)n + 1), cudaMemcpyDefault, st);
+    if (e == cudaSuccess && m > 0)
+        e = cudaMemcpyAsync(g->col_idx, col_idx, sizeof(int32_t) * (size_t)m, cudaMemcpyDefault, st);
+    if (e != cudaSuccess) { release(g); return cuda_fail(e, "cudaMemcpyAsync(csr)", __FILE__, __LINE__); }
+
+    // ---- validation on the device
+    unsigned long long* bad = nullptr;
+    unsigned long long bad_h[2];
+    e = cudaMallocAsync((void**)&bad, 2 * sizeof(unsigned long long), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(bad, 0xff, 2 * sizeof(unsigned long long), st);
+    if (e == cudaSuccess) {
+        validate_csr_kernel<<<grid_for((int64_t)n + 1 > m ? (int64_t)n + 1 : m, g->sms), kThreads, 0, st>>>(
+            g->row_ptr, g->col_idx, n, (long long)m, bad);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(bad_h, bad, sizeof(bad_h), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (bad) cudaFreeAsync(bad, st);
+    if (e != cudaSuccess) { release(g); return cuda_fail(e, "validate", __FILE__, __LINE__); }
+    if (bad_h[0] != ULLONG_MAX) {
+        release(g);
+        return fail(DAWN_E_INVALID, "row_ptr[%llu] breaks row_ptr[0] = 0 <= ... <= row_ptr[n] = m", bad_h[0]);
+    }
+    if (bad_h[1] != ULLONG_MAX) {
+        release(g);
+        return fail(DAWN_E_INVALID, "col_idx[%llu] is outside [0, n)", bad_h[1]);
+    }
+
+    // ---- in-adjacency
+    if (flags & DAWN_SYMMETRIC) {
+        g->in_ptr = g->row_ptr;
+        g->in_idx = g->col_idx;
+    } else {
+        int32_t* indeg = nullptr;
+        int32_t* cursor = nullptr;
+        if ((e = alloc((void**)&g->in_ptr, sizeof(int32_t) * ((size_t)n + 1))) != cudaSuccess ||
+            (e = alloc((void**)&g->in_idx, mb)) != cudaSuccess ||
+            (e = cudaMallocAsync((void**)&indeg, sizeof(int32_t) * (size_t)n, st)) != cudaSuccess) {
+            release(g);
+            return cuda_fail(e, "cudaMalloc(csc)", __FILE__, __LINE__);
+        }
+        e = cudaMemsetAsync(indeg, 0, sizeof(int32_t) * (size_t)n, st);
+        if (e == cudaSuccess && m > 0) {
+            indegree_kernel<<<grid_for(m, g->sms), kThreads, 0, st>>>(g->col_idx, (long long)m, indeg);
+            e = cudaGetLastError();
+        }
+        int rc = e == cudaSuccess ? exclusive_scan(indeg, n, g->in_ptr, st) : DAWN_OK;
+        if (e == cudaSuccess && rc == DAWN_OK) {
+            // reuse indeg as the scatter cursor: cursor[c] = in_ptr[c]
+            cursor = indeg;
+            e = cudaMemcpyAsync(cursor, g->in_ptr, sizeof(int32_t) * (size_t)n, cudaMemcpyDeviceToDevice, st);
+            if (e == cudaSuccess && m > 0) {
+                csc_scatter_kernel<<<grid_for((int64_t)n * 32, g->sms), kThreads, 0, st>>>(
+                    g->row_ptr, g->col_idx, n, cursor, g->in_idx);
+                e = cudaGetLastError();
+            }
+        }
+        cudaFreeAsync(indeg, st);
+        if (rc != DAWN_OK) { release(g); return rc; }
+        if (e != cudaSuccess) { release(g); return cuda_fail(e, "csc build", __FILE__, __LINE__); }
+    }
+
+    // ---- work buffers of the single-source level loop
+    g->queue_cap = (int64_t)n + m / kEntryArcs + 64;
+    if ((e = alloc((void**)&g->excl, wb)) != cudaSuccess ||
+        (e = alloc((void**)&g->vis[0], wb)) != cudaSuccess ||
+        (e = alloc((void**)&g->vis[1], wb)) != cudaSuccess ||
+        (e = alloc((void**)&g->queue[0], sizeof(int2) * (size_t)g->queue_cap)) != cudaSuccess ||
+        (e = alloc((void**)&g->queue[1], sizeof(int2) * (size_t)g->queue_cap)) != cudaSuccess ||
+        (e = alloc((void**)&g->dist_tmp, sizeof(int32_t) * (size_t)n)) != cudaSuccess ||
+        (e = alloc((void**)&g->ctl, sizeof(Ctl))) != cudaSuccess ||
+        (e = alloc((void**)&g->stats_dev, sizeof(dawn_sssp_stats))) != cudaSuccess ||
+        (e = cudaMallocHost((void**)&g->stats_host, sizeof(dawn_sssp_stats))) != cudaSuccess ||
+        (e = cudaMallocHost((void**)&g->status_host, sizeof(int))) != cudaSuccess) {
+        release(g);
+        return cuda_fail(e, "cudaMalloc(work buffers)", __FILE__, __LINE__);
+    }
+    e = cudaMemsetAsync(g->excl, 0, wb, st);
+    if (e == cudaSuccess) {
+        excl_kernel<<<grid_for(g->nwords, g->sms), kThreads, 0, st>>>(g->in_ptr, n, g->nwords, g->excl);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemsetAsync(g->ctl, 0, sizeof(Ctl), st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) { release(g); return cuda_fail(e, "graph setup", __FILE__, __LINE__); }
+    int rc = sssp_occupancy(g);
+    if (rc != DAWN_OK) { release(g); return rc; }
+    *out = g;
+    return DAWN_OK;
+}
+
+}  // namespace
+
+int graph_sync_status(dawn_graph* g, cudaStream_t st) {
+    DAWN_CUDA_TRY(cudaMemcpyAsync(g->status_host, &g->ctl->status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    DAWN_CUDA_TRY(cudaStreamSynchronize(st));
+    int s = *g->status_host;
+    if (s == DEV_OK) return DAWN_OK;
+    // clear the sticky word and the barrier state a timed-out launch left behind
+    DAWN_CUDA_TRY(cudaMemsetAsync(g->ctl, 0, sizeof(Ctl), st));
+    DAWN_CUDA_TRY(cudaStreamSynchronize(st));
+    if (s == DEV_TIMEOUT) return fail(DAWN_E_TIMEOUT, "a grid-barrier wait on the device ran out of its spin budget");
+    if (s == DEV_OVERFLOW) return fail(DAWN_E_OVERFLOW, "a distance exceeded the int16 range (32767)");
+    return fail(DAWN_E_CUDA, "unknown device status %d", s);
+}
+
+}  // namespace dawn
+
+extern "C" {
+
+DAWN_API int dawn_graph_upload(const int32_t* row_ptr, const int32_t* col_idx, int32_t n, int64_t m,
+                               uint32_t flags, void* stream, dawn_graph_t* out) {
+    if (!out) return dawn::fail(DAWN_E_INVALID, "out is NULL");
+    *out = nullptr;
+    if (!row_ptr || (m > 0 && !col_idx)) return dawn::fail(DAWN_E_INVALID, "row_ptr / col_idx is NULL");
+    if (n < 1) return dawn::fail(DAWN_E_INVALID, "n = %d: need n >= 1", n);
+    if (m < 0 || m >= (int64_t)INT32_MAX) return dawn::fail(DAWN_E_INVALID, "m = %lld: need 0 <= m < 2^31", (long long)m);
+    if (flags & ~DAWN_SYMMETRIC) return dawn::fail(DAWN_E_INVALID, "unknown flags 0x%x", flags);
+    return dawn::upload(row_ptr, col_idx, n, m, flags, (cudaStream_t)stream, out);
+}
+
+DAWN_API int dawn_graph_free(dawn_graph_t g) {
+    dawn::release(g);
+    return DAWN_OK;
+}
+
+DAWN_API int dawn_graph_info(dawn_graph_t g, int32_t* n, int64_t* m, uint32_t* flags) {
+    if (!g) return dawn::fail(DAWN_E_INVALID, "graph is NULL");
+    if (n) *n = g->n;
+    if (m) *m = g->m;
+    if (flags) *flags = g->flags;
+    return DAWN_OK;
+}
+
+DAWN_API int dawn_graph_sync(dawn_graph_t g, void* stream) {
+    if (!g) return dawn::fail(DAWN_E_INVALID, "graph is NULL");
+    return dawn::graph_sync_status(g, (cudaStream_t)stream);
+}
+
+}  // extern "C"

@@ -1,0 +1,464 @@
+// Single-source DAWN on sm_103a: the whole level loop in one persistent
+// cooperative kernel.
+//
+// One level ("step") of DAWN is the Boolean vector-matrix product of the
+// frontier alpha with the adjacency over (OR, AND), masked by the vertices
+// already reached; every newly reached vertex gets dist = step (Sec. 3.3,
+// Eq. 5-7 and Alg. 3; Sec. 3.2, Eq. 2-4 and Alg. 1).  The kernel evaluates a
+// level in one of two directions:
+//
+//  * push (SOVM, Alg. 3): the union of the CSR rows of the frontier
+//    vertices (Eq. 7).  The frontier is a queue of work entries
+//    {first arc, arc count <= kEntryArcs}; a warp takes 32 entries, scans
+//    their arc counts and walks the concatenated arcs 32 at a time, so every
+//    load of col_idx is a coalesced run.  A target is claimed with atomicOr
+//    on the visited bitmap; the lane whose atomicOr flipped the bit writes
+//    dist and appends the target's own row to the next queue (one atomic per
+//    warp).
+//  * pull (BOVM, Alg. 1): every vertex not yet reached evaluates the
+//    compressed inner product of Eq. 4 over its in-neighbours and stops at
+//    the first in-neighbour already reached.  The test reads the visited
+//    bitmap as it was at the start of the step (the merge of alpha and beta
+//    happens after the whole vertex loop), so a vertex found in this step
+//    never certifies another one in the same step.  New bits go to a second
+//    bitmap which becomes the current one after the grid barrier.  Testing
+//    against all reached vertices rather than the frontier alone is exact:
+//    an unreached v has d(v) >= step and a reached u has d(u) <= step - 1, so
+//    an arc u -> v gives d(v) = step.
+//
+// The direction is chosen per level from device counters with Beamer's rule
+// (push -> pull when m_f * alpha > m_u; pull -> push when n_f * beta < n and
+// the frontier shrank).  Levels are separated by a grid barrier whose spin is
+// bounded; on expiry the kernel records DEV_TIMEOUT and every CTA returns.
+#include "dawn_internal.cuh"
+
+namespace dawn {
+namespace {
+
+constexpr int kThreads = 512;
+constexpr int kWarps = kThreads / 32;
+constexpr unsigned kFull = 0xffffffffu;
+
+struct SsspArgs {
+    const int32_t* __restrict__ row_ptr;
+    const int32_t* __restrict__ col_idx;
+    const int32_t* __restrict__ in_ptr;
+    const int32_t* __restrict__ in_idx;
+    const uint32_t* __restrict__ excl;
+    uint32_t* vis0;
+    uint32_t* vis1;
+    int2* q0;
+    int2* q1;
+    int32_t* dist;
+    Ctl* ctl;
+    dawn_sssp_stats* stats;  // device, may be null
+    long long m;
+    long long spin_limit;
+    int32_t n;
+    int32_t nwords;
+    int32_t src;
+    int32_t mode;
+    int32_t alpha;
+    int32_t beta;
+};
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release(unsigned* p, unsigned v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ int ld_relaxed_s32(const int* p) {
+    int v;
+    asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Grid-wide barrier with a bounded spin.  Returns false (in every thread of
+// the CTA) when the wait ran out or another CTA already reported a failure.
+__device__ bool grid_barrier(Ctl* ctl, long long spin_limit) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        const unsigned gen = ld_acquire(&ctl->bar_gen);
+        __threadfence();
+        const unsigned arrived = atomicAdd(&ctl->bar_count, 1u);
+        if (arrived == gridDim.x - 1) {
+            ctl->bar_count = 0;
+            st_release(&ctl->bar_gen, gen + 1);
+        } else {
+            const long long t0 = clock64();
+            unsigned polls = 0;
+            while (ld_acquire(&ctl->bar_gen) == gen) {
+                if ((++polls & 63u) == 0) {
+                    if (ld_relaxed_s32(&ctl->status) != DEV_OK) { ok = 0; break; }
+                    if (clock64() - t0 > spin_limit) {
+                        atomicCAS(&ctl->status, DEV_OK, DEV_TIMEOUT);
+                        ok = 0;
+                        break;
+                    }
+                }
+            }
+        }
+        __threadfence();
+        if (ok && ld_relaxed_s32(&ctl->status) != DEV_OK) ok = 0;
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+__device__ __forceinline__ int warp_inclusive_scan(int x, int lane) {
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(kFull, x, o);
+        if (lane >= o) x += y;
+    }
+    return x;
+}
+
+// Append the CSR row [rb, re) of each lane with `has` set to the queue, split
+// into entries of at most kEntryArcs arcs.  Must be reached by the full warp.
+__device__ __forceinline__ void warp_enqueue(bool has, int rb, int re, int lane, int2* q,
+                                             unsigned long long* qtail) {
+    const int deg = has ? re - rb : 0;
+    const int cnt = (deg + kEntryArcs - 1) / kEntryArcs;
+    const int incl = warp_inclusive_scan(cnt, lane);
+    const int total = __shfl_sync(kFull, incl, 31);
+    if (total == 0) return;
+    unsigned long long base = 0;
+    if (lane == 31) base = atomicAdd(qtail, (unsigned long long)total);
+    base = __shfl_sync(kFull, base, 31);
+    int pos = (int)base + incl - cnt;
+    for (int k = 0; k < cnt; ++k) {
+        const int s = rb + k * kEntryArcs;
+        q[pos + k] = make_int2(s, min(kEntryArcs, re - s));
+    }
+}
+
+// Sum (nf, mf) over the CTA and add them to the level's counters.
+__device__ __forceinline__ void flush_counts(long long nf, long long mf, CtrSlot* out) {
+    __shared__ long long s_nf[kWarps], s_mf[kWarps];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        nf += __shfl_down_sync(kFull, nf, o);
+        mf += __shfl_down_sync(kFull, mf, o);
+    }
+    if (lane == 0) { s_nf[w] = nf; s_mf[w] = mf; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        long long a = 0, b = 0;
+        for (int i = 0; i < kWarps; ++i) { a += s_nf[i]; b += s_mf[i]; }
+        if (a) atomicAdd(&out->nf, (unsigned long long)a);
+        if (b) atomicAdd(&out->mf, (unsigned long long)b);
+    }
+}
+
+// SOVM push: expand the work entries of the frontier queue.
+__device__ void push_level(const SsspArgs& a, int step, uint32_t* vis, const int2* __restrict__ qin,
+                           int qn, int2* qout, CtrSlot* out, long long& nf, long long& mf) {
+    const int lane = threadIdx.x & 31;
+    const int ngroups = (qn + 31) >> 5;
+    while (true) {
+        int g = 0;
+        if (lane == 0) g = (int)atomicAdd(&out->grab, 1ull);
+        g = __shfl_sync(kFull, g, 0);
+        if (g >= ngroups) break;
+        const int idx = (g << 5) + lane;
+        const int2 e = idx < qn ? qin[idx] : make_int2(0, 0);
+        const int incl = warp_inclusive_scan(e.y, lane);
+        const int total = __shfl_sync(kFull, incl, 31);
+        const int ex = incl - e.y;
+        for (int off = 0; off < total; off += 32) {
+            const int t = off + lane;
+            // owner entry of arc t: the largest lane whose exclusive prefix is <= t
+            int lo = 0;
+#pragma unroll
+            for (int b = 16; b > 0; b >>= 1) {
+                const int cand = lo + b;
+                const int pv = __shfl_sync(kFull, ex, cand);
+                if (pv <= t) lo = cand;
+            }
+            const int ostart = __shfl_sync(kFull, e.x, lo);
+            const int oex = __shfl_sync(kFull, ex, lo);
+            bool claimed = false;
+            int c = 0;
+            if (t < total) {
+                c = __ldg(a.col_idx + ostart + (t - oex));
+                const uint32_t bit = 1u << (c & 31);
+                if (!(vis[c >> 5] & bit)) {
+                    const uint32_t old = atomicOr(&vis[c >> 5], bit);
+                    claimed = !(old & bit);
+                }
+            }
+            int rb = 0, re = 0;
+            if (claimed) {
+                a.dist[c] = step;
+                rb = __ldg(a.row_ptr + c);
+                re = __ldg(a.row_ptr + c + 1);
+                nf += 1;
+                mf += re - rb;
+            }
+            warp_enqueue(claimed, rb, re, lane, qout, &out->qtail);
+        }
+    }
+}
+
+// BOVM pull: every unreached vertex tests its in-neighbours against the
+// step-start bitmap vcur, stopping at the first hit; results go to vnext.
+__device__ void pull_level(const SsspArgs& a, int step, const uint32_t* __restrict__ vcur,
+                           uint32_t* __restrict__ vnext, long long& nf, long long& mf) {
+    const int lane = threadIdx.x & 31;
+    const int gw = blockIdx.x * kWarps + (threadIdx.x >> 5);
+    const int nw = gridDim.x * kWarps;
+    const bool symmetric = a.in_ptr == a.row_ptr;
+    for (int w = gw; w < a.nwords; w += nw) {
+        const uint32_t cur = vcur[w];
+        uint32_t newbits = 0;
+        if (cur != kFull) {
+            const int v = (w << 5) + lane;
+            bool found = false;
+            int ib = 0, ie = 0;
+            if (!((cur >> lane) & 1u)) {
+                ib = __ldg(a.in_ptr + v);
+                ie = __ldg(a.in_ptr + v + 1);
+                int j = ib;
+                for (; j + 4 <= ie && !found; j += 4) {
+                    const int u0 = __ldg(a.in_idx + j), u1 = __ldg(a.in_idx + j + 1);
+                    const int u2 = __ldg(a.in_idx + j + 2), u3 = __ldg(a.in_idx + j + 3);
+                    const uint32_t h = ((vcur[u0 >> 5] >> (u0 & 31)) | (vcur[u1 >> 5] >> (u1 & 31)) |
+                                        (vcur[u2 >> 5] >> (u2 & 31)) | (vcur[u3 >> 5] >> (u3 & 31))) & 1u;
+                    found = h != 0;
+                }
+                for (; j < ie && !found; ++j) {
+                    const int u = __ldg(a.in_idx + j);
+                    found = (vcur[u >> 5] >> (u & 31)) & 1u;
+                }
+            }
+            newbits = __ballot_sync(kFull, found);
+            if (found) {
+                a.dist[v] = step;
+                nf += 1;
+                mf += symmetric ? (ie - ib) : (__ldg(a.row_ptr + v + 1) - __ldg(a.row_ptr + v));
+            }
+        }
+        if (lane == 0) vnext[w] = cur | newbits;
+    }
+}
+
+// After a pull level: queue the vertices it reached (bits of vnow not in vold).
+__device__ void bitmap_to_queue(const SsspArgs& a, const uint32_t* __restrict__ vnow,
+                                const uint32_t* __restrict__ vold, int2* qout, unsigned long long* qtail) {
+    const int lane = threadIdx.x & 31;
+    const int gw = blockIdx.x * kWarps + (threadIdx.x >> 5);
+    const int nw = gridDim.x * kWarps;
+    for (int base = gw << 5; base < a.nwords; base += nw << 5) {
+        const int w = base + lane;
+        uint32_t nb = w < a.nwords ? (vnow[w] & ~vold[w]) : 0u;
+        int rounds = __popc(nb);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) rounds = max(rounds, __shfl_xor_sync(kFull, rounds, o));
+        for (int r = 0; r < rounds; ++r) {
+            const bool has = nb != 0;
+            int rb = 0, re = 0;
+            if (has) {
+                const int v = (w << 5) + (__ffs(nb) - 1);
+                nb &= nb - 1;
+                rb = __ldg(a.row_ptr + v);
+                re = __ldg(a.row_ptr + v + 1);
+            }
+            warp_enqueue(has, rb, re, lane, qout, qtail);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kThreads, 2) sssp_kernel(SsspArgs a) {
+    Ctl* ctl = a.ctl;
+    if (ld_relaxed_s32(&ctl->status) != DEV_OK) return;  // an earlier call failed: stay idle
+    const int lane = threadIdx.x & 31;
+    const long long gtid = (long long)blockIdx.x * kThreads + threadIdx.x;
+    const long long gthreads = (long long)gridDim.x * kThreads;
+
+    // ---- init: dist = -1 except dist[src] = 0; visited = excl + {src}; queue = {src}
+    const int32_t src = a.src;
+    if ((((uintptr_t)a.dist) & 15u) == 0) {
+        int4* d4 = reinterpret_cast<int4*>(a.dist);
+        const long long n4 = a.n >> 2;
+        for (long long i = gtid; i < n4; i += gthreads) d4[i] = make_int4(-1, -1, -1, -1);
+        for (long long i = (n4 << 2) + gtid; i < a.n; i += gthreads) a.dist[i] = -1;
+    } else {
+        for (long long i = gtid; i < a.n; i += gthreads) a.dist[i] = -1;
+    }
+    for (long long w = gtid; w < a.nwords; w += gthreads)
+        a.vis0[w] = a.excl[w] | (w == (src >> 5) ? (1u << (src & 31)) : 0u);
+    if (blockIdx.x == 0 && threadIdx.x < 32) {
+        if (lane < 3 * (int)(sizeof(CtrSlot) / 8)) {
+            reinterpret_cast<unsigned long long*>(ctl->ctr)[lane] = 0;
+        }
+        for (int i = lane + 32; i < 3 * (int)(sizeof(CtrSlot) / 8); i += 32)
+            reinterpret_cast<unsigned long long*>(ctl->ctr)[i] = 0;
+        __syncwarp();
+        const int rb = __ldg(a.row_ptr + src), re = __ldg(a.row_ptr + src + 1);
+        warp_enqueue(lane == 0, rb, re, lane, a.q0, &ctl->ctr[0].qtail);
+        if (lane == 0) {
+            ctl->ctr[0].nf = 1;
+            ctl->ctr[0].mf = (unsigned long long)(re - rb);
+        }
+    }
+    // dist[src] = 0 after the fill; the barrier orders it after every -1 store
+    if (!grid_barrier(ctl, a.spin_limit)) return;
+    if (gtid == 0) a.dist[src] = 0;
+
+    uint32_t* vcur = a.vis0;
+    uint32_t* vnext = a.vis1;
+    long long mu = a.m;         // arcs out of vertices not yet reached
+    long long prev_nf = 0;
+    long long reached = 0, edges = 0;
+    int pushes = 0, pulls = 0;
+    bool last_pull = false;
+    int step = 0;
+    while (true) {
+        CtrSlot* cur = &ctl->ctr[step % 3];
+        const long long nf_cur = (long long)ld_relaxed_u64(&cur->nf);
+        const long long mf_cur = (long long)ld_relaxed_u64(&cur->mf);
+        if (nf_cur == 0 || step >= a.n) break;
+        reached += nf_cur;
+        edges += mf_cur;
+        mu -= mf_cur;
+        bool pull;
+        if (a.mode == DAWN_MODE_PUSH) pull = false;
+        else if (a.mode == DAWN_MODE_PULL) pull = true;
+        else if (!last_pull) pull = mf_cur * a.alpha > mu;
+        else pull = !(nf_cur * a.beta < a.n && nf_cur < prev_nf);
+        prev_nf = nf_cur;
+        if (blockIdx.x == 0 && threadIdx.x < (int)(sizeof(CtrSlot) / 8))
+            reinterpret_cast<unsigned long long*>(&ctl->ctr[(step + 2) % 3])[threadIdx.x] = 0;
+
+        if (!pull && last_pull) {
+            // the frontier exists only as a bitmap difference: turn it into a queue
+            bitmap_to_queue(a, vcur, vnext, (step & 1) ? a.q1 : a.q0, &cur->qtail);
+            if (!grid_barrier(ctl, a.spin_limit)) return;
+        }
+        CtrSlot* out = &ctl->ctr[(step + 1) % 3];
+        long long nf = 0, mf = 0;
+        if (pull) {
+            pull_level(a, step + 1, vcur, vnext, nf, mf);
+            ++pulls;
+        } else {
+            const int qn = (int)ld_relaxed_u64(&cur->qtail);
+            push_level(a, step + 1, vcur, (step & 1) ? a.q1 : a.q0, qn, (step & 1) ? a.q0 : a.q1, out, nf, mf);
+            ++pushes;
+        }
+        flush_counts(nf, mf, out);
+        if (!grid_barrier(ctl, a.spin_limit)) return;
+        if (pull) {
+            uint32_t* t = vcur;
+            vcur = vnext;
+            vnext = t;
+        }
+        last_pull = pull;
+        ++step;
+    }
+    if (gtid == 0 && a.stats) {
+        dawn_sssp_stats s;
+        s.levels = step > 0 ? step - 1 : 0;
+        s.push_steps = pushes;
+        s.pull_steps = pulls;
+        s.reserved = 0;
+        s.reached = reached;
+        s.edges = edges;
+        *a.stats = s;
+    }
+}
+
+}  // namespace
+
+int sssp_occupancy(dawn_graph* g) {
+    int nb = 0;
+    DAWN_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sssp_kernel, kThreads, 0));
+    if (nb < 1) return fail(DAWN_E_CUDA, "persistent SSSP kernel cannot be resident on an SM");
+    g->sssp_blocks_per_sm = nb;
+    return DAWN_OK;
+}
+
+int sssp_launch(dawn_graph* g, int32_t src, int32_t* dist_dev, const dawn_sssp_opts* opts,
+                dawn_sssp_stats* stats_dev, cudaStream_t st) {
+    SsspArgs a;
+    a.row_ptr = g->row_ptr;
+    a.col_idx = g->col_idx;
+    a.in_ptr = g->in_ptr;
+    a.in_idx = g->in_idx;
+    a.excl = g->excl;
+    a.vis0 = g->vis[0];
+    a.vis1 = g->vis[1];
+    a.q0 = g->queue[0];
+    a.q1 = g->queue[1];
+    a.dist = dist_dev;
+    a.ctl = g->ctl;
+    a.stats = stats_dev;
+    a.m = g->m;
+    a.n = g->n;
+    a.nwords = g->nwords;
+    a.src = src;
+    a.mode = opts ? opts->mode : DAWN_MODE_AUTO;
+    a.alpha = (opts && opts->alpha > 0) ? opts->alpha : 15;
+    a.beta = (opts && opts->beta > 0) ? opts->beta : 18;
+    a.spin_limit = (opts && opts->spin_limit > 0) ? opts->spin_limit : kDefaultSpin;
+    if (a.mode < DAWN_MODE_AUTO || a.mode > DAWN_MODE_PULL)
+        return fail(DAWN_E_INVALID, "unknown mode %d", a.mode);
+    int bps = g->sssp_blocks_per_sm;
+    if (opts && opts->blocks_per_sm > 0 && opts->blocks_per_sm < bps) bps = opts->blocks_per_sm;
+    dim3 grid(g->sms * bps), block(kThreads);
+    void* args[] = {&a};
+    DAWN_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)sssp_kernel, grid, block, args, 0, st));
+    return DAWN_OK;
+}
+
+}  // namespace dawn
+
+extern "C" {
+
+DAWN_API int dawn_sssp_ex(dawn_graph_t g, int32_t src, int32_t* dist, const dawn_sssp_opts* opts,
+                          dawn_sssp_stats* stats, void* stream) {
+    if (!g) return dawn::fail(DAWN_E_INVALID, "graph is NULL");
+    if (!dist) return dawn::fail(DAWN_E_INVALID, "dist is NULL");
+    if (src < 0 || src >= g->n) return dawn::fail(DAWN_E_INVALID, "source %d outside [0, %d)", src, g->n);
+    cudaStream_t st = (cudaStream_t)stream;
+    const bool dev = dawn::is_device_ptr(dist);
+    int32_t* d = dev ? dist : g->dist_tmp;
+    int rc = dawn::sssp_launch(g, src, d, opts, g->stats_dev, st);
+    if (rc != DAWN_OK) return rc;
+    if (!dev) DAWN_CUDA_TRY(cudaMemcpyAsync(dist, d, sizeof(int32_t) * (size_t)g->n, cudaMemcpyDeviceToHost, st));
+    if (stats) DAWN_CUDA_TRY(cudaMemcpyAsync(g->stats_host, g->stats_dev, sizeof(dawn_sssp_stats), cudaMemcpyDeviceToHost, st));
+    rc = dawn::graph_sync_status(g, st);
+    if (rc != DAWN_OK) return rc;
+    if (stats) *stats = *g->stats_host;
+    return DAWN_OK;
+}
+
+DAWN_API int dawn_sssp(dawn_graph_t g, int32_t src, int32_t* dist, void* stream) {
+    return dawn_sssp_ex(g, src, dist, nullptr, nullptr, stream);
+}
+
+DAWN_API int dawn_sssp_async(dawn_graph_t g, int32_t src, int32_t* dist_dev, const dawn_sssp_opts* opts,
+                             dawn_sssp_stats* stats_dev, void* stream) {
+    if (!g) return dawn::fail(DAWN_E_INVALID, "graph is NULL");
+    if (!dist_dev || !dawn::is_device_ptr(dist_dev)) return dawn::fail(DAWN_E_INVALID, "dist_dev must be device memory");
+    if (stats_dev && !dawn::is_device_ptr(stats_dev)) return dawn::fail(DAWN_E_INVALID, "stats_dev must be device memory or NULL");
+    if (src < 0 || src >= g->n) return dawn::fail(DAWN_E_INVALID, "source %d outside [0, %d)", src, g->n);
+    return dawn::sssp_launch(g, src, dist_dev, opts, stats_dev, (cudaStream_t)stream);
+}
+
+}  // extern "C"

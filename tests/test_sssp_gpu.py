@@ -1,0 +1,270 @@
+"""Single-source parity: the CUDA path (through the C ABI) against the CPU
+oracle, element by element.  Distances are integers: the bar is bit-exact.
+
+Sizes: tiny hand-derived and random digraphs (all three traversal modes),
+the 1024-vertex directed ER graph with sources 0-3, RMAT graphs of growing
+scale with isolated and hub sources, ragged n (not a multiple of 32),
+and at full size the RMAT scale-20 graph (sampled sources against Alg. 3,
+all 64 against the certificate) and the 4096^2 lattice (against Alg. 2).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2208_04514_b300 import graphgen as gg
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+MODES = [0, 1, 2]  # auto, push only (Alg. 3), pull only (Alg. 1)
+
+
+def upload(dawn, g):
+    flags = dawn.DAWN_SYMMETRIC if g.symmetric else dawn.DAWN_DIRECTED
+    return dawn.dawn_graph_upload(g.row_ptr, g.col_idx, flags=flags)
+
+
+def gpu_sssp(dawn, h, n, src, mode=0, host=False):
+    if host:
+        d = np.full(n, -7, dtype=np.int32)
+        st = dawn.dawn_sssp_ex(h, src, d, {"mode": mode})
+        return d, st
+    d = torch.full((n,), -7, dtype=torch.int32, device="cuda")
+    st = dawn.dawn_sssp_ex(h, src, d, {"mode": mode})
+    return d.cpu().numpy(), st
+
+
+def check_stats(g, d, st):
+    deg = g.out_degree()
+    assert st["reached"] == int((d >= 0).sum())
+    assert st["edges"] == int(deg[d >= 0].sum())  # E_r, the SOVM cost of Sec. 3.3
+    assert st["levels"] == int(d.max())
+
+
+def test_golden_fixtures(dawn):
+    from test_oracle_pins import parse_golden
+    from pathlib import Path
+    for f in sorted((Path(__file__).parent / "golden").glob("hand_*.txt")):
+        n, arcs, cases = parse_golden(f)
+        g = gg.from_arcs(n, [a for a, _ in arcs], [b for _, b in arcs])
+        h = upload(dawn, g)
+        try:
+            for src, want in cases:
+                for mode in MODES:
+                    d, st = gpu_sssp(dawn, h, n, src, mode)
+                    np.testing.assert_array_equal(d, want, err_msg=f"{f.name} src={src} mode={mode}")
+        finally:
+            dawn.dawn_graph_free(h)
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_random_small_digraphs(dawn, seed):
+    from test_oracle_pins import random_digraph
+    g = random_digraph(5000 + seed, n=int(np.random.default_rng(seed).integers(1, 70)))
+    h = upload(dawn, g)
+    try:
+        for src in range(g.n):
+            want = oracle.sssp_sovm(g.row_ptr, g.col_idx, src)
+            for mode in MODES:
+                d, st = gpu_sssp(dawn, h, g.n, src, mode)
+                np.testing.assert_array_equal(d, want, err_msg=f"src={src} mode={mode}")
+                check_stats(g, d, st)
+    finally:
+        dawn.dawn_graph_free(h)
+
+
+def test_er_1024_sources_0_to_3(dawn):
+    g = gg.erdos_renyi(1024, 8.0, seed=1)
+    h = upload(dawn, g)
+    try:
+        for src in range(4):
+            want = oracle.sssp_sovm(g.row_ptr, g.col_idx, src)
+            for mode in MODES:
+                for host in (False, True):
+                    d, st = gpu_sssp(dawn, h, g.n, src, mode, host)
+                    np.testing.assert_array_equal(d, want)
+                    check_stats(g, d, st)
+    finally:
+        dawn.dawn_graph_free(h)
+
+
+@pytest.mark.parametrize("scale", [8, 12, 16])
+def test_rmat_scales(dawn, scale):
+    g = gg.rmat(scale, seed=2)
+    deg = g.out_degree()
+    h = upload(dawn, g)
+    try:
+        srcs = list(gg.sample_sources(g, 6, seed=scale))
+        srcs.append(int(np.argmax(deg)))                       # the largest hub
+        iso = np.nonzero(deg == 0)[0]
+        if iso.size:
+            srcs.append(int(iso[0]))                           # an isolated source
+        for src in srcs:
+            want = oracle.sssp_sovm(g.row_ptr, g.col_idx, src)
+            for mode in MODES:
+                d, st = gpu_sssp(dawn, h, g.n, src, mode)
+                np.testing.assert_array_equal(d, want, err_msg=f"src={src} mode={mode}")
+                check_stats(g, d, st)
+    finally:
+        dawn.dawn_graph_free(h)
+
+
+def test_directed_rmat_uses_in_adjacency(dawn):
+    g = gg.rmat(12, seed=9, symmetrise=False)
+    h = upload(dawn, g)
+    try:
+        deg = g.out_degree()
+        srcs = list(gg.sample_sources(g, 5, seed=1)) + [int(np.nonzero(deg == 0)[0][0])]
+        for src in srcs:
+            want = oracle.sssp_sovm(g.row_ptr, g.col_idx, src)
+            for mode in MODES:
+                d, _ = gpu_sssp(dawn, h, g.n, src, mode)
+                np.testing.assert_array_equal(d, want, err_msg=f"src={src} mode={mode}")
+    finally:
+        dawn.dawn_graph_free(h)
+
+
+@pytest.mark.parametrize("n", [1, 2, 31, 33, 63, 65, 1000, 4097])
+def test_ragged_sizes_paths_and_stars(dawn, n):
+    # undirected path: one vertex per level, the longest level chain for n
+    s = np.arange(max(n - 1, 0))
+    g = gg.from_arcs(n, np.r_[s, s + 1], np.r_[s + 1, s], symmetric=True)
+    h = upload(dawn, g)
+    try:
+        for src in {0, n // 2, n - 1}:
+            for mode in MODES:
+                d, st = gpu_sssp(dawn, h, n, src, mode)
+                np.testing.assert_array_equal(d, np.abs(np.arange(n) - src))
+                check_stats(g, d, st)
+    finally:
+        dawn.dawn_graph_free(h)
+
+
+def test_empty_graph_and_self_loops(dawn):
+    g = gg.from_arcs(5, [], [])
+    h = upload(dawn, g)
+    try:
+        for mode in MODES:
+            d, st = gpu_sssp(dawn, h, 5, 3, mode)
+            np.testing.assert_array_equal(d, [-1, -1, -1, 0, -1])
+            assert st["levels"] == 0 and st["reached"] == 1 and st["edges"] == 0
+    finally:
+        dawn.dawn_graph_free(h)
+    g = gg.from_arcs(4, [0, 0, 1, 1, 2, 3, 3], [0, 1, 1, 2, 2, 3, 0])  # loops + dup-free chain
+    h = upload(dawn, g)
+    try:
+        for mode in MODES:
+            d, _ = gpu_sssp(dawn, h, 4, 0, mode)
+            np.testing.assert_array_equal(d, [0, 1, 2, -1])
+            d, _ = gpu_sssp(dawn, h, 4, 3, mode)
+            np.testing.assert_array_equal(d, [1, 2, 3, 0])
+    finally:
+        dawn.dawn_graph_free(h)
+
+
+def test_invalid_inputs(dawn):
+    rp = np.array([0, 2, 1], dtype=np.int32)  # decreasing
+    ci = np.array([1, 0], dtype=np.int32)
+    with pytest.raises(dawn.DawnError) as ei:
+        dawn.dawn_graph_upload(rp, ci)
+    assert ei.value.code == dawn.DAWN_E_INVALID and "row_ptr[2]" in str(ei.value)
+    rp = np.array([0, 1, 2], dtype=np.int32)
+    ci = np.array([1, 5], dtype=np.int32)  # out of range
+    with pytest.raises(dawn.DawnError) as ei:
+        dawn.dawn_graph_upload(rp, ci)
+    assert "col_idx[1]" in str(ei.value)
+    g = gg.erdos_renyi(64, 2.0, seed=3)
+    h = upload(dawn, g)
+    try:
+        d = np.zeros(64, dtype=np.int32)
+        for bad in (-1, 64, 1 << 30):
+            with pytest.raises(dawn.DawnError) as ei:
+                dawn.dawn_sssp(h, bad, d)
+            assert ei.value.code == dawn.DAWN_E_INVALID
+        with pytest.raises(dawn.DawnError):
+            dawn.dawn_sssp_ex(h, 0, d, {"mode": 7})
+    finally:
+        dawn.dawn_graph_free(h)
+
+
+def test_barrier_timeout_is_reported_and_recoverable(dawn):
+    """A one-cycle spin budget makes the first grid-barrier wait run out: the
+    call must return DAWN_E_TIMEOUT, and the next call must work."""
+    g = gg.rmat(12, seed=2)
+    h = upload(dawn, g)
+    try:
+        d = torch.zeros(g.n, dtype=torch.int32, device="cuda")
+        with pytest.raises(dawn.DawnError) as ei:
+            dawn.dawn_sssp_ex(h, 0, d, {"spin_limit": 1})
+        assert ei.value.code == dawn.DAWN_E_TIMEOUT
+        src = int(gg.sample_sources(g, 1, seed=4)[0])
+        dawn.dawn_sssp(h, src, d)
+        np.testing.assert_array_equal(d.cpu().numpy(), oracle.sssp_sovm(g.row_ptr, g.col_idx, src))
+    finally:
+        dawn.dawn_graph_free(h)
+
+
+def test_async_queue_of_sources(dawn):
+    g = gg.rmat(14, seed=2)
+    h = upload(dawn, g)
+    try:
+        srcs = gg.sample_sources(g, 16, seed=3)
+        out = torch.zeros((len(srcs), g.n), dtype=torch.int32, device="cuda")
+        stats = torch.zeros((len(srcs), dawn.STATS_WORDS), dtype=torch.int64, device="cuda")
+        for i, s in enumerate(srcs):
+            dawn.dawn_sssp_async(h, int(s), out[i], None, stats[i])
+        dawn.dawn_graph_sync(h)
+        out = out.cpu().numpy()
+        stats = stats.cpu().numpy()
+        for i, s in enumerate(srcs):
+            d = out[i]
+            np.testing.assert_array_equal(d, oracle.sssp_sovm(g.row_ptr, g.col_idx, int(s)))
+            check_stats(g, d, dawn.stats_from_words(stats[i]))
+    finally:
+        dawn.dawn_graph_free(h)
+
+
+@pytest.fixture(scope="module")
+def rmat20():
+    return gg.rmat(20, seed=2)
+
+
+def test_rmat20_full_size(dawn, rmat20):
+    """Full-size RMAT scale 20: 8 sampled sources element by element against
+    Alg. 3, all 64 bench sources against the certificate (Thm 1 + Fact 1)."""
+    g = rmat20
+    h = upload(dawn, g)
+    try:
+        srcs = gg.sample_sources(g, 64, seed=5)
+        d = torch.zeros(g.n, dtype=torch.int32, device="cuda")
+        for i, s in enumerate(srcs):
+            st = dawn.dawn_sssp_ex(h, int(s), d)
+            dh = d.cpu().numpy()
+            assert oracle.certificate(g.row_ptr, g.col_idx, int(s), dh) == (0, -1)
+            check_stats(g, dh, st)
+            if i < 8:
+                np.testing.assert_array_equal(dh, oracle.sssp_sovm(g.row_ptr, g.col_idx, int(s)))
+        iso = int(np.nonzero(g.out_degree() == 0)[0][0])
+        st = dawn.dawn_sssp_ex(h, iso, d)
+        dh = d.cpu().numpy()
+        assert dh[iso] == 0 and (dh >= 0).sum() == 1 and st["levels"] == 0
+    finally:
+        dawn.dawn_graph_free(h)
+
+
+def test_lattice_4096_full_size(dawn):
+    """Full-size 4096^2 lattice (p = 0.1), ~10^4 levels: against Alg. 2 (the
+    oracle's queue BFS) and the certificate."""
+    g = gg.lattice(4096, 4096, 0.1, seed=3)
+    h = upload(dawn, g)
+    try:
+        d = torch.zeros(g.n, dtype=torch.int32, device="cuda")
+        for s in gg.uniform_vertices(g.n, 2, seed=7):
+            st = dawn.dawn_sssp_ex(h, int(s), d)
+            dh = d.cpu().numpy()
+            np.testing.assert_array_equal(dh, oracle.bfs_queue(g.row_ptr, g.col_idx, int(s)))
+            assert oracle.certificate(g.row_ptr, g.col_idx, int(s), dh) == (0, -1)
+            check_stats(g, dh, st)
+            assert st["levels"] > 4000
+    finally:
+        dawn.dawn_graph_free(h)
