@@ -39,6 +39,11 @@ constexpr int kThreads = 512;
 constexpr int kWarps = kThreads / 32;
 constexpr unsigned kFull = 0xffffffffu;
 
+// Only the graph arrays, which no launch writes, are marked __restrict__ (and
+// may take the read-only cache path).  The bitmaps and queues are rewritten
+// by other CTAs from level to level inside one launch, and an SM's L1 may
+// still hold a line of them from an earlier level, so every load of them is
+// ld.global.cg (cached in L2 only, the point of coherence).
 struct SsspArgs {
     const int32_t* __restrict__ row_ptr;
     const int32_t* __restrict__ col_idx;
@@ -167,7 +172,7 @@ __device__ __forceinline__ void flush_counts(long long nf, long long mf, CtrSlot
 }
 
 // SOVM push: expand the work entries of the frontier queue.
-__device__ void push_level(const SsspArgs& a, int step, uint32_t* vis, const int2* __restrict__ qin,
+__device__ void push_level(const SsspArgs& a, int step, uint32_t* vis, const int2* qin,
                            int qn, int2* qout, CtrSlot* out, long long& nf, long long& mf) {
     const int lane = threadIdx.x & 31;
     const int ngroups = (qn + 31) >> 5;
@@ -177,7 +182,7 @@ __device__ void push_level(const SsspArgs& a, int step, uint32_t* vis, const int
         g = __shfl_sync(kFull, g, 0);
         if (g >= ngroups) break;
         const int idx = (g << 5) + lane;
-        const int2 e = idx < qn ? qin[idx] : make_int2(0, 0);
+        const int2 e = idx < qn ? __ldcg(qin + idx) : make_int2(0, 0);
         const int incl = warp_inclusive_scan(e.y, lane);
         const int total = __shfl_sync(kFull, incl, 31);
         const int ex = incl - e.y;
@@ -198,7 +203,7 @@ __device__ void push_level(const SsspArgs& a, int step, uint32_t* vis, const int
             if (t < total) {
                 c = __ldg(a.col_idx + ostart + (t - oex));
                 const uint32_t bit = 1u << (c & 31);
-                if (!(vis[c >> 5] & bit)) {
+                if (!(__ldcg(vis + (c >> 5)) & bit)) {
                     const uint32_t old = atomicOr(&vis[c >> 5], bit);
                     claimed = !(old & bit);
                 }
@@ -218,33 +223,40 @@ __device__ void push_level(const SsspArgs& a, int step, uint32_t* vis, const int
 
 // BOVM pull: every unreached vertex tests its in-neighbours against the
 // step-start bitmap vcur, stopping at the first hit; results go to vnext.
-__device__ void pull_level(const SsspArgs& a, int step, const uint32_t* __restrict__ vcur,
-                           uint32_t* __restrict__ vnext, long long& nf, long long& mf) {
+__device__ void pull_level(const SsspArgs& a, int step, const uint32_t* vcur, uint32_t* vnext,
+                           long long& nf, long long& mf) {
     const int lane = threadIdx.x & 31;
     const int gw = blockIdx.x * kWarps + (threadIdx.x >> 5);
     const int nw = gridDim.x * kWarps;
     const bool symmetric = a.in_ptr == a.row_ptr;
     for (int w = gw; w < a.nwords; w += nw) {
-        const uint32_t cur = vcur[w];
+        const uint32_t cur = __ldcg(vcur + w);
+        // candidates: not reached, and with at least one in-arc (excl also
+        // covers the padding bits past n).  excl is kept out of the visited
+        // set itself: a vertex without in-arcs may still have out-arcs, and
+        // it must not look reached to its out-neighbours.
+        const uint32_t skip = cur | __ldg(a.excl + w);
         uint32_t newbits = 0;
-        if (cur != kFull) {
+        if (skip != kFull) {
             const int v = (w << 5) + lane;
             bool found = false;
             int ib = 0, ie = 0;
-            if (!((cur >> lane) & 1u)) {
+            if (!((skip >> lane) & 1u)) {
                 ib = __ldg(a.in_ptr + v);
                 ie = __ldg(a.in_ptr + v + 1);
                 int j = ib;
                 for (; j + 4 <= ie && !found; j += 4) {
                     const int u0 = __ldg(a.in_idx + j), u1 = __ldg(a.in_idx + j + 1);
                     const int u2 = __ldg(a.in_idx + j + 2), u3 = __ldg(a.in_idx + j + 3);
-                    const uint32_t h = ((vcur[u0 >> 5] >> (u0 & 31)) | (vcur[u1 >> 5] >> (u1 & 31)) |
-                                        (vcur[u2 >> 5] >> (u2 & 31)) | (vcur[u3 >> 5] >> (u3 & 31))) & 1u;
+                    const uint32_t h = ((__ldcg(vcur + (u0 >> 5)) >> (u0 & 31)) |
+                                        (__ldcg(vcur + (u1 >> 5)) >> (u1 & 31)) |
+                                        (__ldcg(vcur + (u2 >> 5)) >> (u2 & 31)) |
+                                        (__ldcg(vcur + (u3 >> 5)) >> (u3 & 31))) & 1u;
                     found = h != 0;
                 }
                 for (; j < ie && !found; ++j) {
                     const int u = __ldg(a.in_idx + j);
-                    found = (vcur[u >> 5] >> (u & 31)) & 1u;
+                    found = (__ldcg(vcur + (u >> 5)) >> (u & 31)) & 1u;
                 }
             }
             newbits = __ballot_sync(kFull, found);
@@ -259,14 +271,14 @@ __device__ void pull_level(const SsspArgs& a, int step, const uint32_t* __restri
 }
 
 // After a pull level: queue the vertices it reached (bits of vnow not in vold).
-__device__ void bitmap_to_queue(const SsspArgs& a, const uint32_t* __restrict__ vnow,
-                                const uint32_t* __restrict__ vold, int2* qout, unsigned long long* qtail) {
+__device__ void bitmap_to_queue(const SsspArgs& a, const uint32_t* vnow, const uint32_t* vold,
+                                int2* qout, unsigned long long* qtail) {
     const int lane = threadIdx.x & 31;
     const int gw = blockIdx.x * kWarps + (threadIdx.x >> 5);
     const int nw = gridDim.x * kWarps;
     for (int base = gw << 5; base < a.nwords; base += nw << 5) {
         const int w = base + lane;
-        uint32_t nb = w < a.nwords ? (vnow[w] & ~vold[w]) : 0u;
+        uint32_t nb = w < a.nwords ? (__ldcg(vnow + w) & ~__ldcg(vold + w)) : 0u;
         int rounds = __popc(nb);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) rounds = max(rounds, __shfl_xor_sync(kFull, rounds, o));
@@ -291,7 +303,7 @@ __global__ void __launch_bounds__(kThreads, 2) sssp_kernel(SsspArgs a) {
     const long long gtid = (long long)blockIdx.x * kThreads + threadIdx.x;
     const long long gthreads = (long long)gridDim.x * kThreads;
 
-    // ---- init: dist = -1 except dist[src] = 0; visited = excl + {src}; queue = {src}
+    // ---- init: dist = -1 except dist[src] = 0; visited = {src}; queue = {src}
     const int32_t src = a.src;
     if ((((uintptr_t)a.dist) & 15u) == 0) {
         int4* d4 = reinterpret_cast<int4*>(a.dist);
@@ -302,7 +314,7 @@ __global__ void __launch_bounds__(kThreads, 2) sssp_kernel(SsspArgs a) {
         for (long long i = gtid; i < a.n; i += gthreads) a.dist[i] = -1;
     }
     for (long long w = gtid; w < a.nwords; w += gthreads)
-        a.vis0[w] = a.excl[w] | (w == (src >> 5) ? (1u << (src & 31)) : 0u);
+        a.vis0[w] = (w == (src >> 5)) ? (1u << (src & 31)) : 0u;
     if (blockIdx.x == 0 && threadIdx.x < 32) {
         if (lane < 3 * (int)(sizeof(CtrSlot) / 8)) {
             reinterpret_cast<unsigned long long*>(ctl->ctr)[lane] = 0;
