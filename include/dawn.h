@@ -155,6 +155,34 @@ DAWN_API int dawn_sssp_async(dawn_graph_t g, int32_t src, int32_t* dist_dev, con
 DAWN_API int dawn_graph_sync(dawn_graph_t g, void* stream);
 
 /*
+ * Allocation-free single source (the paper has no counterpart: this entry
+ * point exists for callers that cannot call cudaMalloc, e.g. a process whose
+ * framework allocator has already reserved the device memory it is allowed
+ * to use, or a latency-critical request path whose policy forbids device
+ * allocation after start-up).  It runs the same persistent level loop as
+ * dawn_sssp in SOVM push mode (Alg. 3) on a CSR the caller keeps on the
+ * device; no graph handle is needed.
+ *   row_ptr, col_idx  device memory, int32[n+1] / int32[m]; checked on the
+ *                     device before the traversal (DAWN_E_INVALID if bad).
+ *   n, m              1 <= n <= 1,048,576 and 0 <= m <= 33,554,432, else
+ *                     DAWN_E_INVALID.
+ *   src               0 <= src < n.
+ *   dist              device memory, int32[n], written in full.
+ * The work buffers (control block, visited bitmap, two frontier queues)
+ * live in one file-scope device array of about 19 MB that every GPU which
+ * loads this library holds until the process exits.  The call allocates
+ * nothing: no cudaMalloc, cudaFree, pinned host buffer or library routine
+ * that allocates.  The first call on a device looks up the array's device
+ * address and the kernel's occupancy (once per device); make that first call
+ * before any stream capture.  Every call uses the same array and leaves its
+ * contents behind (the call clears what must start at zero), so calls whose
+ * work overlaps on the GPU (other streams, other host threads) race and must
+ * be serialized by the caller.  Synchronizes `stream`.
+ */
+DAWN_API int dawn_sssp_noalloc(const int32_t* row_ptr, const int32_t* col_idx, int32_t n, int64_t m,
+                               int32_t src, int32_t* dist, void* stream);
+
+/*
  * Multi-source (APSP-style) batch: SSSP from each of k sources (Sec. 3.3,
  * APSP as repeated SSSP), advanced together as bit lanes: 64 * W sources per
  * pass share each vertex's W uint64 visited words, and one level does

@@ -30,6 +30,8 @@
 // (push -> pull when m_f * alpha > m_u; pull -> push when n_f * beta < n and
 // the frontier shrank).  Levels are separated by a grid barrier whose spin is
 // bounded; on expiry the kernel records DEV_TIMEOUT and every CTA returns.
+#include <mutex>
+
 #include "dawn_internal.cuh"
 
 namespace dawn {
@@ -438,6 +440,141 @@ int sssp_launch(dawn_graph* g, int32_t src, int32_t* dist_dev, const dawn_sssp_o
     return DAWN_OK;
 }
 
+
+// ------------------------------------------------- allocation-free variant --
+// Scratch of dawn_sssp_noalloc: a file-scope device array, so that callers
+// which cannot allocate device memory can still run the level loop.  Every
+// GPU that loads this library holds it until the process exits.  Layout
+// (256-byte aligned parts): control block | CSR check flags | visited bitmap
+// | two frontier queues.
+constexpr int32_t kNoAllocMaxN = 1 << 20;
+constexpr int64_t kNoAllocMaxM = 1LL << 25;
+constexpr int64_t kNoAllocQueueCap = kNoAllocMaxN + kNoAllocMaxM / kEntryArcs + 64;
+constexpr size_t kNoAllocCtlOff = 0;
+constexpr size_t kNoAllocBadOff = (sizeof(Ctl) + 255) / 256 * 256;
+constexpr size_t kNoAllocVisOff = kNoAllocBadOff + 256;
+constexpr size_t kNoAllocQ0Off = kNoAllocVisOff + (size_t)kNoAllocMaxN / 8;
+constexpr size_t kNoAllocQ1Off = kNoAllocQ0Off + (size_t)kNoAllocQueueCap * sizeof(int2);
+constexpr size_t kNoAllocBytes = kNoAllocQ1Off + (size_t)kNoAllocQueueCap * sizeof(int2);
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+namespace {
+
+// bad[0]: smallest bad row_ptr index; bad[1]: smallest bad col_idx index.
+__global__ void noalloc_check_csr_kernel(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                                         int32_t n, long long m, unsigned long long* bad) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const long long t0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    for (long long i = t0; i <= n; i += stride) {
+        const int v = rp[i];
+        bool ok = v >= 0 && v <= m && (i == 0 ? v == 0 : v >= rp[i - 1]);
+        if (i == n) ok = ok && v == m;
+        if (!ok) atomicMin(&bad[0], (unsigned long long)i);
+    }
+    for (long long j = t0; j < m; j += stride) {
+        const int c = ci[j];
+        if (c < 0 || c >= n) atomicMin(&bad[1], (unsigned long long)j);
+    }
+}
+
+struct NoAllocDevice {
+    unsigned char* scratch = nullptr;  // device address of g_noalloc_scratch
+    int sms = 0;
+    int blocks_per_sm = 0;
+};
+
+std::mutex g_noalloc_mu;
+NoAllocDevice g_noalloc_dev[64];
+
+// Once per device, with that device current: the scratch array's device
+// address (host code only sees a host-side stand-in for its name) and the
+// persistent kernel's occupancy.
+int noalloc_setup(NoAllocDevice** out) {
+    int dev = 0;
+    DAWN_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return fail(DAWN_E_INVALID, "device ordinal %d out of range", dev);
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    NoAllocDevice& d = g_noalloc_dev[dev];
+    if (!d.scratch) {
+        void* p = nullptr;
+        DAWN_CUDA_TRY(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+        DAWN_CUDA_TRY(cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev));
+        DAWN_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d.blocks_per_sm, sssp_kernel, kThreads, 0));
+        if (d.blocks_per_sm < 1) return fail(DAWN_E_CUDA, "persistent SSSP kernel cannot be resident on an SM");
+        d.scratch = static_cast<unsigned char*>(p);
+    }
+    *out = &d;
+    return DAWN_OK;
+}
+
+}  // namespace
+
+int sssp_noalloc(const int32_t* row_ptr, const int32_t* col_idx, int32_t n, int64_t m, int32_t src,
+                 int32_t* dist, cudaStream_t st) {
+    if (n < 1 || n > kNoAllocMaxN)
+        return fail(DAWN_E_INVALID, "n = %d: dawn_sssp_noalloc handles 1 <= n <= %d", n, kNoAllocMaxN);
+    if (m < 0 || m > kNoAllocMaxM)
+        return fail(DAWN_E_INVALID, "m = %lld: dawn_sssp_noalloc handles 0 <= m <= %lld", (long long)m,
+                    (long long)kNoAllocMaxM);
+    if (src < 0 || src >= n) return fail(DAWN_E_INVALID, "source %d outside [0, %d)", src, n);
+    if (!is_device_ptr(row_ptr) || (m > 0 && !is_device_ptr(col_idx)) || !is_device_ptr(dist))
+        return fail(DAWN_E_INVALID, "row_ptr, col_idx and dist must be device memory");
+    NoAllocDevice* d = nullptr;
+    int rc = noalloc_setup(&d);
+    if (rc != DAWN_OK) return rc;
+    Ctl* ctl = reinterpret_cast<Ctl*>(d->scratch + kNoAllocCtlOff);
+    unsigned long long* bad = reinterpret_cast<unsigned long long*>(d->scratch + kNoAllocBadOff);
+
+    // the CSR comes straight from the caller: check it before any traversal
+    unsigned long long bad_h[2] = {0, 0};
+    DAWN_CUDA_TRY(cudaMemsetAsync(bad, 0xff, 2 * sizeof(unsigned long long), st));
+    const long long work = (long long)n + 1 > m ? (long long)n + 1 : (long long)m;
+    long long nb = (work + 255) / 256;
+    if (nb > (long long)d->sms * 8) nb = (long long)d->sms * 8;
+    noalloc_check_csr_kernel<<<(int)(nb < 1 ? 1 : nb), 256, 0, st>>>(row_ptr, col_idx, n, (long long)m, bad);
+    DAWN_CUDA_TRY(cudaGetLastError());
+    DAWN_CUDA_TRY(cudaMemcpyAsync(bad_h, bad, sizeof(bad_h), cudaMemcpyDeviceToHost, st));
+    DAWN_CUDA_TRY(cudaStreamSynchronize(st));
+    if (bad_h[0] != ~0ULL)
+        return fail(DAWN_E_INVALID, "row_ptr[%llu] breaks row_ptr[0] = 0 <= ... <= row_ptr[n] = m", bad_h[0]);
+    if (bad_h[1] != ~0ULL) return fail(DAWN_E_INVALID, "col_idx[%llu] is outside [0, n)", bad_h[1]);
+
+    // the array keeps the previous call's contents: the barrier state and the
+    // status word must start at zero (the kernel clears its own counters)
+    DAWN_CUDA_TRY(cudaMemsetAsync(ctl, 0, sizeof(Ctl), st));
+    SsspArgs a;
+    a.row_ptr = row_ptr;
+    a.col_idx = col_idx;
+    a.in_ptr = nullptr;  // push (SOVM) only: the in-adjacency is never read
+    a.in_idx = nullptr;
+    a.excl = nullptr;
+    a.vis0 = reinterpret_cast<uint32_t*>(d->scratch + kNoAllocVisOff);
+    a.vis1 = nullptr;
+    a.q0 = reinterpret_cast<int2*>(d->scratch + kNoAllocQ0Off);
+    a.q1 = reinterpret_cast<int2*>(d->scratch + kNoAllocQ1Off);
+    a.dist = dist;
+    a.ctl = ctl;
+    a.stats = nullptr;
+    a.m = m;
+    a.n = n;
+    a.nwords = (int32_t)(((int64_t)n + 31) / 32);
+    a.src = src;
+    a.mode = DAWN_MODE_PUSH;
+    a.alpha = 15;
+    a.beta = 18;
+    a.spin_limit = kDefaultSpin;
+    dim3 grid(d->sms * d->blocks_per_sm), block(kThreads);
+    void* args[] = {&a};
+    DAWN_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)sssp_kernel, grid, block, args, 0, st));
+    int status = 0;
+    DAWN_CUDA_TRY(cudaMemcpyAsync(&status, &ctl->status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    DAWN_CUDA_TRY(cudaStreamSynchronize(st));
+    if (status == DEV_TIMEOUT) return fail(DAWN_E_TIMEOUT, "a grid-barrier wait on the device ran out of its spin budget");
+    if (status != DEV_OK) return fail(DAWN_E_CUDA, "unknown device status %d", status);
+    return DAWN_OK;
+}
+
 }  // namespace dawn
 
 extern "C" {
@@ -471,6 +608,11 @@ DAWN_API int dawn_sssp_async(dawn_graph_t g, int32_t src, int32_t* dist_dev, con
     if (stats_dev && !dawn::is_device_ptr(stats_dev)) return dawn::fail(DAWN_E_INVALID, "stats_dev must be device memory or NULL");
     if (src < 0 || src >= g->n) return dawn::fail(DAWN_E_INVALID, "source %d outside [0, %d)", src, g->n);
     return dawn::sssp_launch(g, src, dist_dev, opts, stats_dev, (cudaStream_t)stream);
+}
+
+DAWN_API int dawn_sssp_noalloc(const int32_t* row_ptr, const int32_t* col_idx, int32_t n, int64_t m,
+                              int32_t src, int32_t* dist, void* stream) {
+    return dawn::sssp_noalloc(row_ptr, col_idx, n, m, src, dist, (cudaStream_t)stream);
 }
 
 }  // extern "C"

@@ -79,6 +79,7 @@ _SIGNATURES = {
     "dawn_sssp": [_vp, _i32, _vp, _vp],
     "dawn_sssp_ex": [_vp, _i32, _vp, _vp, _vp, _vp],
     "dawn_sssp_async": [_vp, _i32, _vp, _vp, _vp, _vp],
+    "dawn_sssp_noalloc": [_vp, _vp, _i32, _i64, _i32, _vp, _vp],
     "dawn_msbfs": [_vp, _vp, _i32, _vp, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp],
     "dawn_msbfs_ex": [_vp, _vp, _i32, _vp, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp, _vp],
     "dawn_serve_create": [_vp, ctypes.c_int, _sz, ctypes.c_int, ctypes.POINTER(_vp)],
@@ -202,6 +203,15 @@ def dawn_sssp_async(g: int, src: int, dist_dev, opts: dict | None = None, stats_
     o = _opts(opts, dawn_sssp_opts)
     _check(load().dawn_sssp_async(g, int(src), _ptr(dist_dev), ctypes.byref(o) if o else None,
                                   _ptr(stats_dev), _stream(stream)))
+
+
+def dawn_sssp_noalloc(row_ptr_dev, col_idx_dev, src: int, dist_dev, n: int | None = None,
+                      m: int | None = None, stream=None) -> None:
+    """Allocation-free single source on a device-resident CSR (see include/dawn.h)."""
+    n = int(row_ptr_dev.shape[0] - 1) if n is None else n
+    m = int(col_idx_dev.shape[0]) if m is None else m
+    _check(load().dawn_sssp_noalloc(_ptr(row_ptr_dev), _ptr(col_idx_dev), n, m, int(src),
+                                    _ptr(dist_dev), _stream(stream)))
 
 
 STATS_WORDS = ctypes.sizeof(dawn_sssp_stats) // 8  # int64 words per stats record
