@@ -122,6 +122,13 @@ typedef struct {
     int32_t beta;          /* pull -> push when n_f * beta < n and n_f shrank; 0 = default (18) */
     int32_t blocks_per_sm; /* CTAs per SM of the persistent grid; 0 = occupancy-derived */
     int64_t spin_limit;    /* grid-barrier spin budget in SM clock cycles; 0 = default (~2 s) */
+    int64_t* trace;        /* device memory or NULL: one record of 4 int64 per grid barrier,
+                              {kind, step, count, globaltimer ns}; kind 0 = kernel entry,
+                              1 = init done, 2 = push level, 3 = pull level, 4 = bitmap-to-queue
+                              conversion; count = vertices the level reached (entries queued
+                              for kind 4); records past trace_cap are dropped */
+    int32_t trace_cap;     /* records that fit in trace */
+    int32_t reserved;
 } dawn_sssp_opts;
 
 typedef struct {
@@ -169,7 +176,7 @@ DAWN_API int dawn_graph_sync(dawn_graph_t g, void* stream);
  *   src               0 <= src < n.
  *   dist              device memory, int32[n], written in full.
  * The work buffers (control block, visited bitmap, two frontier queues)
- * live in one file-scope device array of about 19 MB that every GPU which
+ * live in one file-scope device array of about 27 MB that every GPU which
  * loads this library holds until the process exits.  The call allocates
  * nothing: no cudaMalloc, cudaFree, pinned host buffer or library routine
  * that allocates.  The first call on a device looks up the array's device

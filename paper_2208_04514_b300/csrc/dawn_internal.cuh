@@ -40,11 +40,10 @@ constexpr int kEntryArcs = 256;
 // slots (step % 3): written during step s, read after the barrier that ends
 // step s, reset during step s + 1 (see the level loop in sssp.cu).
 struct alignas(128) CtrSlot {
-    unsigned long long qtail;  // work entries appended to the level's queue
+    unsigned long long qpack;  // queue size: entries (high 32 bits) | arcs (low 32 bits)
     unsigned long long nf;     // vertices first reached at this level
     unsigned long long mf;     // sum of their out-degrees
-    unsigned long long grab;   // next 32-entry group of the input queue to take
-    unsigned long long pad[12];
+    unsigned long long pad[13];
 };
 
 struct alignas(128) Ctl {
@@ -77,7 +76,8 @@ struct dawn_graph {
     uint32_t* excl = nullptr;         // bit v set: v has no in-arc (or v >= n)
     // single-source work buffers
     uint32_t* vis[2] = {nullptr, nullptr};
-    int2* queue[2] = {nullptr, nullptr};
+    int2* queue[2] = {nullptr, nullptr};        // frontier entries {first arc, arc count}
+    int32_t* queue_off[2] = {nullptr, nullptr}; // each entry's arc offset within its level
     int64_t queue_cap = 0;
     int32_t* dist_tmp = nullptr;      // result staging for host outputs
     dawn::Ctl* ctl = nullptr;         // device control block

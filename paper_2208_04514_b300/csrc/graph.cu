@@ -169,6 +169,8 @@ void release(dawn_graph* g) {
     f(g->vis[1]);
     f(g->queue[0]);
     f(g->queue[1]);
+    f(g->queue_off[0]);
+    f(g->queue_off[1]);
     f(g->dist_tmp);
     f(g->ctl);
     f(g->stats_dev);
@@ -269,6 +271,8 @@ int upload(const int32_t* row_ptr, const int32_t* col_idx, int32_t n, int64_t m,
         (e = alloc((void**)&g->vis[1], wb)) != cudaSuccess ||
         (e = alloc((void**)&g->queue[0], sizeof(int2) * (size_t)g->queue_cap)) != cudaSuccess ||
         (e = alloc((void**)&g->queue[1], sizeof(int2) * (size_t)g->queue_cap)) != cudaSuccess ||
+        (e = alloc((void**)&g->queue_off[0], sizeof(int32_t) * (size_t)g->queue_cap)) != cudaSuccess ||
+        (e = alloc((void**)&g->queue_off[1], sizeof(int32_t) * (size_t)g->queue_cap)) != cudaSuccess ||
         (e = alloc((void**)&g->dist_tmp, sizeof(int32_t) * (size_t)n)) != cudaSuccess ||
         (e = alloc((void**)&g->ctl, sizeof(Ctl))) != cudaSuccess ||
         (e = alloc((void**)&g->stats_dev, sizeof(dawn_sssp_stats))) != cudaSuccess ||

@@ -30,6 +30,7 @@
 // (push -> pull when m_f * alpha > m_u; pull -> push when n_f * beta < n and
 // the frontier shrank).  Levels are separated by a grid barrier whose spin is
 // bounded; on expiry the kernel records DEV_TIMEOUT and every CTA returns.
+#include <climits>
 #include <mutex>
 
 #include "dawn_internal.cuh"
@@ -56,9 +57,12 @@ struct SsspArgs {
     uint32_t* vis1;
     int2* q0;
     int2* q1;
+    int32_t* q0off;          // arc offset of each entry of q0 / q1
+    int32_t* q1off;
     int32_t* dist;
     Ctl* ctl;
     dawn_sssp_stats* stats;  // device, may be null
+    long long* trace;        // device, may be null: 4 int64 per grid barrier
     long long m;
     long long spin_limit;
     int32_t n;
@@ -67,6 +71,14 @@ struct SsspArgs {
     int32_t mode;
     int32_t alpha;
     int32_t beta;
+    int32_t trace_cap;
+};
+
+// A frontier queue: entries {first arc, arc count} and, in a parallel array,
+// each entry's offset in the level's concatenated arc list.
+struct Queue {
+    int2* ent;
+    int32_t* off;
 };
 
 __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
@@ -89,6 +101,25 @@ __device__ __forceinline__ int ld_relaxed_s32(const int* p) {
     int v;
     asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
+}
+
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// One trace record {kind, step, count, time}; called by one thread.
+__device__ __forceinline__ void trace_rec(const SsspArgs& a, int& slot, long long kind, long long step,
+                                          long long count) {
+    if (a.trace && slot < a.trace_cap) {
+        long long* r = a.trace + 4 * (long long)slot;
+        r[0] = kind;
+        r[1] = step;
+        r[2] = count;
+        r[3] = (long long)globaltimer_ns();
+    }
+    ++slot;
 }
 
 // Grid-wide barrier with a bounded spin.  Returns false (in every thread of
@@ -136,21 +167,29 @@ __device__ __forceinline__ int warp_inclusive_scan(int x, int lane) {
 }
 
 // Append the CSR row [rb, re) of each lane with `has` set to the queue, split
-// into entries of at most kEntryArcs arcs.  Must be reached by the full warp.
-__device__ __forceinline__ void warp_enqueue(bool has, int rb, int re, int lane, int2* q,
-                                             unsigned long long* qtail) {
+// into entries of at most kEntryArcs arcs.  One 64-bit atomic reserves the
+// warp's entries (high word) and arcs (low word) together, so each entry's
+// offset in the level's concatenated arc list grows with its slot index.
+// The low word cannot carry into the high one: a level's arcs total at most
+// m < 2^31.  Must be reached by the full warp.
+__device__ __forceinline__ void warp_enqueue(bool has, int rb, int re, int lane, Queue q,
+                                             unsigned long long* qpack) {
     const int deg = has ? re - rb : 0;
     const int cnt = (deg + kEntryArcs - 1) / kEntryArcs;
-    const int incl = warp_inclusive_scan(cnt, lane);
-    const int total = __shfl_sync(kFull, incl, 31);
-    if (total == 0) return;
+    const int cincl = warp_inclusive_scan(cnt, lane);
+    const int ctot = __shfl_sync(kFull, cincl, 31);
+    if (ctot == 0) return;
+    const int dincl = warp_inclusive_scan(deg, lane);
+    const int dtot = __shfl_sync(kFull, dincl, 31);
     unsigned long long base = 0;
-    if (lane == 31) base = atomicAdd(qtail, (unsigned long long)total);
+    if (lane == 31) base = atomicAdd(qpack, ((unsigned long long)ctot << 32) | (unsigned)dtot);
     base = __shfl_sync(kFull, base, 31);
-    int pos = (int)base + incl - cnt;
+    const int pos = (int)(base >> 32) + cincl - cnt;
+    const int aoff = (int)(base & 0xffffffffu) + dincl - deg;
     for (int k = 0; k < cnt; ++k) {
         const int s = rb + k * kEntryArcs;
-        q[pos + k] = make_int2(s, min(kEntryArcs, re - s));
+        q.ent[pos + k] = make_int2(s, min(kEntryArcs, re - s));
+        q.off[pos + k] = aoff + k * kEntryArcs;
     }
 }
 
@@ -173,58 +212,98 @@ __device__ __forceinline__ void flush_counts(long long nf, long long mf, CtrSlot
     }
 }
 
-// SOVM push: expand the work entries of the frontier queue.
-__device__ void push_level(const SsspArgs& a, int step, uint32_t* vis, const int2* qin,
-                           int qn, int2* qout, CtrSlot* out, long long& nf, long long& mf) {
+// Load the 32 queue entries starting at slot b (one per lane).
+__device__ __forceinline__ void load_batch(const Queue& q, int qn, int b, int lane, int2& e, int& eoff) {
+    const int i = b + lane;
+    e = i < qn ? __ldcg(q.ent + i) : make_int2(0, 0);
+    eoff = i < qn ? __ldcg(q.off + i) : INT_MAX;
+}
+
+// SOVM push: expand the frontier's rows (Eq. 7: the new vector is the union
+// of the CSR rows of the frontier).  The level's E arcs are cut into equal
+// ranges, a multiple of 32 long, one per warp of the grid; a warp finds the
+// entry holding its first arc with a 32-ary search over the sorted entry
+// offsets, then walks its range 32 consecutive arcs at a time.
+__device__ void push_level(const SsspArgs& a, int step, uint32_t* vis, Queue qin, unsigned long long pack,
+                           Queue qout, CtrSlot* out, long long& nf, long long& mf) {
     const int lane = threadIdx.x & 31;
-    const int ngroups = (qn + 31) >> 5;
-    while (true) {
-        int g = 0;
-        if (lane == 0) g = (int)atomicAdd(&out->grab, 1ull);
-        g = __shfl_sync(kFull, g, 0);
-        if (g >= ngroups) break;
-        const int idx = (g << 5) + lane;
-        const int2 e = idx < qn ? __ldcg(qin + idx) : make_int2(0, 0);
-        const int incl = warp_inclusive_scan(e.y, lane);
-        const int total = __shfl_sync(kFull, incl, 31);
-        const int ex = incl - e.y;
-        for (int off = 0; off < total; off += 32) {
-            const int t = off + lane;
-            // owner entry of arc t: the largest lane whose exclusive prefix is <= t
-            int lo = 0;
-#pragma unroll
-            for (int b = 16; b > 0; b >>= 1) {
-                const int cand = lo + b;
-                const int pv = __shfl_sync(kFull, ex, cand);
-                if (pv <= t) lo = cand;
-            }
-            const int ostart = __shfl_sync(kFull, e.x, lo);
-            const int oex = __shfl_sync(kFull, ex, lo);
-            bool claimed = false;
-            int c = 0;
-            if (t < total) {
-                c = __ldg(a.col_idx + ostart + (t - oex));
-                const uint32_t bit = 1u << (c & 31);
-                if (!(__ldcg(vis + (c >> 5)) & bit)) {
-                    const uint32_t old = atomicOr(&vis[c >> 5], bit);
-                    claimed = !(old & bit);
-                }
-            }
-            int rb = 0, re = 0;
-            if (claimed) {
-                a.dist[c] = step;
-                rb = __ldg(a.row_ptr + c);
-                re = __ldg(a.row_ptr + c + 1);
-                nf += 1;
-                mf += re - rb;
-            }
-            warp_enqueue(claimed, rb, re, lane, qout, &out->qtail);
+    const int qn = (int)(pack >> 32);
+    const long long E = (long long)(pack & 0xffffffffull);
+    const long long nw = (long long)gridDim.x * kWarps;
+    const long long gw = (long long)blockIdx.x * kWarps + (threadIdx.x >> 5);
+    long long chunk = (E + nw - 1) / nw;
+    chunk = (chunk + 31) & ~31LL;
+    const long long a0 = gw * chunk;
+    if (E == 0 || a0 >= E) return;
+    const long long a1 = min(E, a0 + chunk);
+    // largest slot i with off[i] <= a0 (off[0] = 0, so one exists)
+    int lo = 0, hi = qn;
+    while (hi - lo > 32) {
+        const int stp = (hi - lo + 31) >> 5;
+        const int p = lo + lane * stp;
+        const int v = p < hi ? __ldcg(qin.off + p) : INT_MAX;
+        const unsigned b = __ballot_sync(kFull, (long long)v <= a0);
+        const int k = 31 - __clz(b);
+        lo += k * stp;
+        hi = min(hi, lo + stp);
+    }
+    int bstart = lo;
+    int2 e;
+    int eoff;
+    load_batch(qin, qn, bstart, lane, e, eoff);
+    for (long long wb = a0; wb < a1; wb += 32) {
+        // keep the batch covering this window: if its last arc lies past the
+        // batch's last entry, restart the batch at the entry holding wb
+        const long long last = min(wb + 31, a1 - 1);
+        const int off31 = __shfl_sync(kFull, eoff, 31);
+        const int len31 = __shfl_sync(kFull, e.y, 31);
+        if (bstart + 32 < qn && last >= (long long)off31 + len31) {
+            int k;
+            if (wb >= (long long)off31 + len31) k = 32;
+            else k = 31 - __clz(__ballot_sync(kFull, (long long)eoff <= wb));
+            bstart += k;
+            load_batch(qin, qn, bstart, lane, e, eoff);
         }
+        const long long t = wb + lane;
+        int o = 0;
+#pragma unroll
+        for (int b = 16; b > 0; b >>= 1) {
+            const int cand = o + b;
+            const int pv = __shfl_sync(kFull, eoff, cand);
+            if ((long long)pv <= t) o = cand;
+        }
+        const int ostart = __shfl_sync(kFull, e.x, o);
+        const int ooff = __shfl_sync(kFull, eoff, o);
+        bool claimed = false;
+        int c = 0;
+        if (t < a1) {
+            c = __ldg(a.col_idx + ostart + (int)(t - ooff));
+            const uint32_t bit = 1u << (c & 31);
+            if (!(__ldcg(vis + (c >> 5)) & bit)) {
+                const uint32_t old = atomicOr(&vis[c >> 5], bit);
+                claimed = !(old & bit);
+            }
+        }
+        int rb = 0, re = 0;
+        if (claimed) {
+            a.dist[c] = step;
+            rb = __ldg(a.row_ptr + c);
+            re = __ldg(a.row_ptr + c + 1);
+            nf += 1;
+            mf += re - rb;
+        }
+        warp_enqueue(claimed, rb, re, lane, qout, &out->qpack);
     }
 }
 
 // BOVM pull: every unreached vertex tests its in-neighbours against the
-// step-start bitmap vcur, stopping at the first hit; results go to vnext.
+// step-start bitmap vcur, stopping at the first hit (Eq. 4); results go to
+// vnext.  A lane first tests up to kPullSerial in-neighbours of its own
+// vertex; vertices with in-arcs left are then taken one at a time by the
+// whole warp, 32 in-neighbours per round, so that one long row does not
+// hold 31 idle lanes.
+constexpr int kPullSerial = 8;
+
 __device__ void pull_level(const SsspArgs& a, int step, const uint32_t* vcur, uint32_t* vnext,
                            long long& nf, long long& mf) {
     const int lane = threadIdx.x & 31;
@@ -241,13 +320,15 @@ __device__ void pull_level(const SsspArgs& a, int step, const uint32_t* vcur, ui
         uint32_t newbits = 0;
         if (skip != kFull) {
             const int v = (w << 5) + lane;
+            const bool cand = !((skip >> lane) & 1u);
             bool found = false;
-            int ib = 0, ie = 0;
-            if (!((skip >> lane) & 1u)) {
+            int ib = 0, ie = 0, j = 0;
+            if (cand) {
                 ib = __ldg(a.in_ptr + v);
                 ie = __ldg(a.in_ptr + v + 1);
-                int j = ib;
-                for (; j + 4 <= ie && !found; j += 4) {
+                j = ib;
+                const int jl = min(ie, ib + kPullSerial);
+                for (; j + 4 <= jl && !found; j += 4) {
                     const int u0 = __ldg(a.in_idx + j), u1 = __ldg(a.in_idx + j + 1);
                     const int u2 = __ldg(a.in_idx + j + 2), u3 = __ldg(a.in_idx + j + 3);
                     const uint32_t h = ((__ldcg(vcur + (u0 >> 5)) >> (u0 & 31)) |
@@ -256,10 +337,27 @@ __device__ void pull_level(const SsspArgs& a, int step, const uint32_t* vcur, ui
                                         (__ldcg(vcur + (u3 >> 5)) >> (u3 & 31))) & 1u;
                     found = h != 0;
                 }
-                for (; j < ie && !found; ++j) {
+                for (; j < jl && !found; ++j) {
                     const int u = __ldg(a.in_idx + j);
                     found = (__ldcg(vcur + (u >> 5)) >> (u & 31)) & 1u;
                 }
+            }
+            unsigned rest = __ballot_sync(kFull, cand && !found && j < ie);
+            while (rest) {
+                const int L = __ffs(rest) - 1;
+                rest &= rest - 1;
+                const int jb = __shfl_sync(kFull, j, L);
+                const int je = __shfl_sync(kFull, ie, L);
+                bool hit = false;
+                for (int base = jb; base < je; base += 32) {
+                    bool h = false;
+                    if (base + lane < je) {
+                        const int u = __ldg(a.in_idx + base + lane);
+                        h = (__ldcg(vcur + (u >> 5)) >> (u & 31)) & 1u;
+                    }
+                    if (__any_sync(kFull, h)) { hit = true; break; }
+                }
+                if (lane == L) found = hit;
             }
             newbits = __ballot_sync(kFull, found);
             if (found) {
@@ -274,7 +372,7 @@ __device__ void pull_level(const SsspArgs& a, int step, const uint32_t* vcur, ui
 
 // After a pull level: queue the vertices it reached (bits of vnow not in vold).
 __device__ void bitmap_to_queue(const SsspArgs& a, const uint32_t* vnow, const uint32_t* vold,
-                                int2* qout, unsigned long long* qtail) {
+                                Queue qout, unsigned long long* qpack) {
     const int lane = threadIdx.x & 31;
     const int gw = blockIdx.x * kWarps + (threadIdx.x >> 5);
     const int nw = gridDim.x * kWarps;
@@ -293,7 +391,7 @@ __device__ void bitmap_to_queue(const SsspArgs& a, const uint32_t* vnow, const u
                 rb = __ldg(a.row_ptr + v);
                 re = __ldg(a.row_ptr + v + 1);
             }
-            warp_enqueue(has, rb, re, lane, qout, qtail);
+            warp_enqueue(has, rb, re, lane, qout, qpack);
         }
     }
 }
@@ -302,6 +400,9 @@ __global__ void __launch_bounds__(kThreads, 2) sssp_kernel(SsspArgs a) {
     Ctl* ctl = a.ctl;
     if (ld_relaxed_s32(&ctl->status) != DEV_OK) return;  // an earlier call failed: stay idle
     const int lane = threadIdx.x & 31;
+    const bool tracer = blockIdx.x == 0 && threadIdx.x == 0;
+    int tslot = 0;
+    if (tracer) trace_rec(a, tslot, 0, 0, 1);
     const long long gtid = (long long)blockIdx.x * kThreads + threadIdx.x;
     const long long gthreads = (long long)gridDim.x * kThreads;
 
@@ -325,7 +426,7 @@ __global__ void __launch_bounds__(kThreads, 2) sssp_kernel(SsspArgs a) {
             reinterpret_cast<unsigned long long*>(ctl->ctr)[i] = 0;
         __syncwarp();
         const int rb = __ldg(a.row_ptr + src), re = __ldg(a.row_ptr + src + 1);
-        warp_enqueue(lane == 0, rb, re, lane, a.q0, &ctl->ctr[0].qtail);
+        warp_enqueue(lane == 0, rb, re, lane, Queue{a.q0, a.q0off}, &ctl->ctr[0].qpack);
         if (lane == 0) {
             ctl->ctr[0].nf = 1;
             ctl->ctr[0].mf = (unsigned long long)(re - rb);
@@ -334,6 +435,7 @@ __global__ void __launch_bounds__(kThreads, 2) sssp_kernel(SsspArgs a) {
     // dist[src] = 0 after the fill; the barrier orders it after every -1 store
     if (!grid_barrier(ctl, a.spin_limit)) return;
     if (gtid == 0) a.dist[src] = 0;
+    if (tracer) trace_rec(a, tslot, 1, 0, 1);
 
     uint32_t* vcur = a.vis0;
     uint32_t* vnext = a.vis1;
@@ -345,6 +447,9 @@ __global__ void __launch_bounds__(kThreads, 2) sssp_kernel(SsspArgs a) {
     int step = 0;
     while (true) {
         CtrSlot* cur = &ctl->ctr[step % 3];
+        // the frontier found at step s lives in queue (s & 1)
+        const Queue qcur = (step & 1) ? Queue{a.q1, a.q1off} : Queue{a.q0, a.q0off};
+        const Queue qnext = (step & 1) ? Queue{a.q0, a.q0off} : Queue{a.q1, a.q1off};
         const long long nf_cur = (long long)ld_relaxed_u64(&cur->nf);
         const long long mf_cur = (long long)ld_relaxed_u64(&cur->mf);
         if (nf_cur == 0 || step >= a.n) break;
@@ -362,8 +467,9 @@ __global__ void __launch_bounds__(kThreads, 2) sssp_kernel(SsspArgs a) {
 
         if (!pull && last_pull) {
             // the frontier exists only as a bitmap difference: turn it into a queue
-            bitmap_to_queue(a, vcur, vnext, (step & 1) ? a.q1 : a.q0, &cur->qtail);
+            bitmap_to_queue(a, vcur, vnext, qcur, &cur->qpack);
             if (!grid_barrier(ctl, a.spin_limit)) return;
+            if (tracer) trace_rec(a, tslot, 4, step, (long long)(ld_relaxed_u64(&cur->qpack) >> 32));
         }
         CtrSlot* out = &ctl->ctr[(step + 1) % 3];
         long long nf = 0, mf = 0;
@@ -371,12 +477,12 @@ __global__ void __launch_bounds__(kThreads, 2) sssp_kernel(SsspArgs a) {
             pull_level(a, step + 1, vcur, vnext, nf, mf);
             ++pulls;
         } else {
-            const int qn = (int)ld_relaxed_u64(&cur->qtail);
-            push_level(a, step + 1, vcur, (step & 1) ? a.q1 : a.q0, qn, (step & 1) ? a.q0 : a.q1, out, nf, mf);
+            push_level(a, step + 1, vcur, qcur, ld_relaxed_u64(&cur->qpack), qnext, out, nf, mf);
             ++pushes;
         }
         flush_counts(nf, mf, out);
         if (!grid_barrier(ctl, a.spin_limit)) return;
+        if (tracer) trace_rec(a, tslot, pull ? 3 : 2, step + 1, (long long)ld_relaxed_u64(&out->nf));
         if (pull) {
             uint32_t* t = vcur;
             vcur = vnext;
@@ -419,6 +525,8 @@ int sssp_launch(dawn_graph* g, int32_t src, int32_t* dist_dev, const dawn_sssp_o
     a.vis1 = g->vis[1];
     a.q0 = g->queue[0];
     a.q1 = g->queue[1];
+    a.q0off = g->queue_off[0];
+    a.q1off = g->queue_off[1];
     a.dist = dist_dev;
     a.ctl = g->ctl;
     a.stats = stats_dev;
@@ -430,6 +538,10 @@ int sssp_launch(dawn_graph* g, int32_t src, int32_t* dist_dev, const dawn_sssp_o
     a.alpha = (opts && opts->alpha > 0) ? opts->alpha : 15;
     a.beta = (opts && opts->beta > 0) ? opts->beta : 18;
     a.spin_limit = (opts && opts->spin_limit > 0) ? opts->spin_limit : kDefaultSpin;
+    a.trace = opts ? reinterpret_cast<long long*>(opts->trace) : nullptr;
+    a.trace_cap = (opts && opts->trace) ? opts->trace_cap : 0;
+    if (a.trace && (a.trace_cap < 0 || !is_device_ptr(a.trace)))
+        return fail(DAWN_E_INVALID, "trace must be device memory with trace_cap >= 0");
     if (a.mode < DAWN_MODE_AUTO || a.mode > DAWN_MODE_PULL)
         return fail(DAWN_E_INVALID, "unknown mode %d", a.mode);
     int bps = g->sssp_blocks_per_sm;
@@ -446,7 +558,7 @@ int sssp_launch(dawn_graph* g, int32_t src, int32_t* dist_dev, const dawn_sssp_o
 // which cannot allocate device memory can still run the level loop.  Every
 // GPU that loads this library holds it until the process exits.  Layout
 // (256-byte aligned parts): control block | CSR check flags | visited bitmap
-// | two frontier queues.
+// | two frontier queues | their arc-offset arrays.
 constexpr int32_t kNoAllocMaxN = 1 << 20;
 constexpr int64_t kNoAllocMaxM = 1LL << 25;
 constexpr int64_t kNoAllocQueueCap = kNoAllocMaxN + kNoAllocMaxM / kEntryArcs + 64;
@@ -455,7 +567,9 @@ constexpr size_t kNoAllocBadOff = (sizeof(Ctl) + 255) / 256 * 256;
 constexpr size_t kNoAllocVisOff = kNoAllocBadOff + 256;
 constexpr size_t kNoAllocQ0Off = kNoAllocVisOff + (size_t)kNoAllocMaxN / 8;
 constexpr size_t kNoAllocQ1Off = kNoAllocQ0Off + (size_t)kNoAllocQueueCap * sizeof(int2);
-constexpr size_t kNoAllocBytes = kNoAllocQ1Off + (size_t)kNoAllocQueueCap * sizeof(int2);
+constexpr size_t kNoAllocQ0OffOff = kNoAllocQ1Off + (size_t)kNoAllocQueueCap * sizeof(int2);
+constexpr size_t kNoAllocQ1OffOff = kNoAllocQ0OffOff + ((size_t)kNoAllocQueueCap * sizeof(int32_t) + 255) / 256 * 256;
+constexpr size_t kNoAllocBytes = kNoAllocQ1OffOff + (size_t)kNoAllocQueueCap * sizeof(int32_t);
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
@@ -553,9 +667,13 @@ int sssp_noalloc(const int32_t* row_ptr, const int32_t* col_idx, int32_t n, int6
     a.vis1 = nullptr;
     a.q0 = reinterpret_cast<int2*>(d->scratch + kNoAllocQ0Off);
     a.q1 = reinterpret_cast<int2*>(d->scratch + kNoAllocQ1Off);
+    a.q0off = reinterpret_cast<int32_t*>(d->scratch + kNoAllocQ0OffOff);
+    a.q1off = reinterpret_cast<int32_t*>(d->scratch + kNoAllocQ1OffOff);
     a.dist = dist;
     a.ctl = ctl;
     a.stats = nullptr;
+    a.trace = nullptr;
+    a.trace_cap = 0;
     a.m = m;
     a.n = n;
     a.nwords = (int32_t)(((int64_t)n + 31) / 32);

@@ -52,7 +52,8 @@ class DawnError(RuntimeError):
 
 class dawn_sssp_opts(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int32), ("alpha", ctypes.c_int32), ("beta", ctypes.c_int32),
-                ("blocks_per_sm", ctypes.c_int32), ("spin_limit", ctypes.c_int64)]
+                ("blocks_per_sm", ctypes.c_int32), ("spin_limit", ctypes.c_int64),
+                ("trace", ctypes.c_void_p), ("trace_cap", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class dawn_sssp_stats(ctypes.Structure):
