@@ -46,11 +46,17 @@ struct alignas(128) CtrSlot {
     unsigned long long pad[13];
 };
 
+// Arrival counter of the grid barrier, on its own 128-byte line.
+struct alignas(128) BarCounter {
+    unsigned int count;
+    unsigned int pad[31];
+};
+
 struct alignas(128) Ctl {
-    unsigned int bar_count;    // arrivals at the current grid barrier
-    unsigned int pad0[31];
-    unsigned int bar_gen;      // barrier generation
-    unsigned int pad1[31];
+    // Launches alternate between the two counters: a launch counts its
+    // barrier arrivals on bar[parity] from zero and zeroes bar[parity ^ 1]
+    // for the next launch, so no host-side reset sits between launches.
+    BarCounter bar[2];
     int status;                // sticky DeviceStatus
     int pad2[31];
     CtrSlot ctr[3];
@@ -85,6 +91,8 @@ struct dawn_graph {
     dawn_sssp_stats* stats_host = nullptr;  // pinned
     int* status_host = nullptr;              // pinned
     int sssp_blocks_per_sm = 0;       // occupancy of the persistent kernel
+    int sssp_smem_bytes = 0;          // dynamic shared memory: the pull levels' bitmap copy
+    unsigned sssp_launches = 0;       // picks the barrier counter of the next launch
     // multi-source work buffers (allocated on first use)
     uint64_t* ms_vis[2] = {nullptr, nullptr};
     int ms_words_cap = 0;             // W capacity of ms_vis

@@ -38,7 +38,7 @@
 namespace dawn {
 namespace {
 
-constexpr int kThreads = 512;
+constexpr int kThreads = 1024;
 constexpr int kWarps = kThreads / 32;
 constexpr unsigned kFull = 0xffffffffu;
 
@@ -72,6 +72,8 @@ struct SsspArgs {
     int32_t alpha;
     int32_t beta;
     int32_t trace_cap;
+    int32_t bar_parity;      // which of the two barrier counters this launch uses
+    int32_t smem_words;      // > 0: pull levels copy the bitmap (this many words) to shared memory
 };
 
 // A frontier queue: entries {first arc, arc count} and, in a parallel array,
@@ -122,35 +124,32 @@ __device__ __forceinline__ void trace_rec(const SsspArgs& a, int& slot, long lon
     ++slot;
 }
 
-// Grid-wide barrier with a bounded spin.  Returns false (in every thread of
-// the CTA) when the wait ran out or another CTA already reported a failure.
-__device__ bool grid_barrier(Ctl* ctl, long long spin_limit) {
+__device__ __forceinline__ void red_release_add(unsigned* p, unsigned v) {
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Grid-wide barrier with a bounded spin.  Every CTA adds one to the launch's
+// arrival counter with a release reduction and spins (acquire loads) until
+// the counter reaches its own running target, gridDim.x more per barrier.
+// Returns false (in every thread of the CTA) when the wait ran out or
+// another CTA reported a failure.  `target` lives in thread 0.
+__device__ bool grid_barrier(Ctl* ctl, unsigned* count, unsigned& target, long long spin_limit) {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
         int ok = 1;
-        const unsigned gen = ld_acquire(&ctl->bar_gen);
-        __threadfence();
-        const unsigned arrived = atomicAdd(&ctl->bar_count, 1u);
-        if (arrived == gridDim.x - 1) {
-            ctl->bar_count = 0;
-            st_release(&ctl->bar_gen, gen + 1);
-        } else {
-            const long long t0 = clock64();
-            unsigned polls = 0;
-            while (ld_acquire(&ctl->bar_gen) == gen) {
-                if ((++polls & 63u) == 0) {
-                    if (ld_relaxed_s32(&ctl->status) != DEV_OK) { ok = 0; break; }
-                    if (clock64() - t0 > spin_limit) {
-                        atomicCAS(&ctl->status, DEV_OK, DEV_TIMEOUT);
-                        ok = 0;
-                        break;
-                    }
-                }
+        target += gridDim.x;
+        red_release_add(count, 1u);
+        const long long t0 = clock64();
+        unsigned polls = 0;
+        while ((int)(ld_acquire(count) - target) < 0) {
+            if (clock64() - t0 > spin_limit) {
+                atomicCAS(&ctl->status, DEV_OK, DEV_TIMEOUT);
+                ok = 0;
+                break;
             }
+            if ((++polls & 15u) == 0 && ld_relaxed_s32(&ctl->status) != DEV_OK) { ok = 0; break; }
         }
-        __threadfence();
-        if (ok && ld_relaxed_s32(&ctl->status) != DEV_OK) ok = 0;
         s_ok = ok;
     }
     __syncthreads();
@@ -304,14 +303,31 @@ __device__ void push_level(const SsspArgs& a, int step, uint32_t* vis, Queue qin
 // hold 31 idle lanes.
 constexpr int kPullSerial = 8;
 
+// kSmem: the CTA first copies the whole step-start bitmap into shared memory
+// (it is read-only for the level), so every in-neighbour test is a shared
+// memory load instead of an L2 round trip.
+extern __shared__ uint4 s_bitmap4[];
+
+template <bool kSmem>
+__device__ __forceinline__ uint32_t bm_word(const uint32_t* vcur, int w) {
+    if (kSmem) return reinterpret_cast<const uint32_t*>(s_bitmap4)[w];
+    return __ldcg(vcur + w);
+}
+
+template <bool kSmem>
 __device__ void pull_level(const SsspArgs& a, int step, const uint32_t* vcur, uint32_t* vnext,
                            long long& nf, long long& mf) {
     const int lane = threadIdx.x & 31;
     const int gw = blockIdx.x * kWarps + (threadIdx.x >> 5);
     const int nw = gridDim.x * kWarps;
     const bool symmetric = a.in_ptr == a.row_ptr;
+    if (kSmem) {
+        const uint4* src4 = reinterpret_cast<const uint4*>(vcur);
+        for (int i = threadIdx.x; i < (a.smem_words >> 2); i += kThreads) s_bitmap4[i] = __ldcg(src4 + i);
+        __syncthreads();
+    }
     for (int w = gw; w < a.nwords; w += nw) {
-        const uint32_t cur = __ldcg(vcur + w);
+        const uint32_t cur = bm_word<kSmem>(vcur, w);
         // candidates: not reached, and with at least one in-arc (excl also
         // covers the padding bits past n).  excl is kept out of the visited
         // set itself: a vertex without in-arcs may still have out-arcs, and
@@ -331,15 +347,15 @@ __device__ void pull_level(const SsspArgs& a, int step, const uint32_t* vcur, ui
                 for (; j + 4 <= jl && !found; j += 4) {
                     const int u0 = __ldg(a.in_idx + j), u1 = __ldg(a.in_idx + j + 1);
                     const int u2 = __ldg(a.in_idx + j + 2), u3 = __ldg(a.in_idx + j + 3);
-                    const uint32_t h = ((__ldcg(vcur + (u0 >> 5)) >> (u0 & 31)) |
-                                        (__ldcg(vcur + (u1 >> 5)) >> (u1 & 31)) |
-                                        (__ldcg(vcur + (u2 >> 5)) >> (u2 & 31)) |
-                                        (__ldcg(vcur + (u3 >> 5)) >> (u3 & 31))) & 1u;
+                    const uint32_t h = ((bm_word<kSmem>(vcur, u0 >> 5) >> (u0 & 31)) |
+                                        (bm_word<kSmem>(vcur, u1 >> 5) >> (u1 & 31)) |
+                                        (bm_word<kSmem>(vcur, u2 >> 5) >> (u2 & 31)) |
+                                        (bm_word<kSmem>(vcur, u3 >> 5) >> (u3 & 31))) & 1u;
                     found = h != 0;
                 }
                 for (; j < jl && !found; ++j) {
                     const int u = __ldg(a.in_idx + j);
-                    found = (__ldcg(vcur + (u >> 5)) >> (u & 31)) & 1u;
+                    found = (bm_word<kSmem>(vcur, u >> 5) >> (u & 31)) & 1u;
                 }
             }
             unsigned rest = __ballot_sync(kFull, cand && !found && j < ie);
@@ -353,7 +369,7 @@ __device__ void pull_level(const SsspArgs& a, int step, const uint32_t* vcur, ui
                     bool h = false;
                     if (base + lane < je) {
                         const int u = __ldg(a.in_idx + base + lane);
-                        h = (__ldcg(vcur + (u >> 5)) >> (u & 31)) & 1u;
+                        h = (bm_word<kSmem>(vcur, u >> 5) >> (u & 31)) & 1u;
                     }
                     if (__any_sync(kFull, h)) { hit = true; break; }
                 }
@@ -396,12 +412,14 @@ __device__ void bitmap_to_queue(const SsspArgs& a, const uint32_t* vnow, const u
     }
 }
 
-__global__ void __launch_bounds__(kThreads, 2) sssp_kernel(SsspArgs a) {
+__global__ void __launch_bounds__(kThreads, 1) sssp_kernel(SsspArgs a) {
     Ctl* ctl = a.ctl;
     if (ld_relaxed_s32(&ctl->status) != DEV_OK) return;  // an earlier call failed: stay idle
     const int lane = threadIdx.x & 31;
     const bool tracer = blockIdx.x == 0 && threadIdx.x == 0;
     int tslot = 0;
+    unsigned* bar = &ctl->bar[a.bar_parity].count;
+    unsigned bar_target = 0;
     if (tracer) trace_rec(a, tslot, 0, 0, 1);
     const long long gtid = (long long)blockIdx.x * kThreads + threadIdx.x;
     const long long gthreads = (long long)gridDim.x * kThreads;
@@ -433,8 +451,11 @@ __global__ void __launch_bounds__(kThreads, 2) sssp_kernel(SsspArgs a) {
         }
     }
     // dist[src] = 0 after the fill; the barrier orders it after every -1 store
-    if (!grid_barrier(ctl, a.spin_limit)) return;
-    if (gtid == 0) a.dist[src] = 0;
+    if (!grid_barrier(ctl, bar, bar_target, a.spin_limit)) return;
+    if (gtid == 0) {
+        a.dist[src] = 0;
+        ctl->bar[a.bar_parity ^ 1].count = 0;  // the next launch's counter
+    }
     if (tracer) trace_rec(a, tslot, 1, 0, 1);
 
     uint32_t* vcur = a.vis0;
@@ -468,20 +489,21 @@ __global__ void __launch_bounds__(kThreads, 2) sssp_kernel(SsspArgs a) {
         if (!pull && last_pull) {
             // the frontier exists only as a bitmap difference: turn it into a queue
             bitmap_to_queue(a, vcur, vnext, qcur, &cur->qpack);
-            if (!grid_barrier(ctl, a.spin_limit)) return;
+            if (!grid_barrier(ctl, bar, bar_target, a.spin_limit)) return;
             if (tracer) trace_rec(a, tslot, 4, step, (long long)(ld_relaxed_u64(&cur->qpack) >> 32));
         }
         CtrSlot* out = &ctl->ctr[(step + 1) % 3];
         long long nf = 0, mf = 0;
         if (pull) {
-            pull_level(a, step + 1, vcur, vnext, nf, mf);
+            if (a.smem_words > 0) pull_level<true>(a, step + 1, vcur, vnext, nf, mf);
+            else pull_level<false>(a, step + 1, vcur, vnext, nf, mf);
             ++pulls;
         } else {
             push_level(a, step + 1, vcur, qcur, ld_relaxed_u64(&cur->qpack), qnext, out, nf, mf);
             ++pushes;
         }
         flush_counts(nf, mf, out);
-        if (!grid_barrier(ctl, a.spin_limit)) return;
+        if (!grid_barrier(ctl, bar, bar_target, a.spin_limit)) return;
         if (tracer) trace_rec(a, tslot, pull ? 3 : 2, step + 1, (long long)ld_relaxed_u64(&out->nf));
         if (pull) {
             uint32_t* t = vcur;
@@ -505,9 +527,15 @@ __global__ void __launch_bounds__(kThreads, 2) sssp_kernel(SsspArgs a) {
 
 }  // namespace
 
+// Largest bitmap the pull levels copy into shared memory (n up to 1,638,400).
+constexpr int kSmemBitmapMax = 200 * 1024;
+
 int sssp_occupancy(dawn_graph* g) {
     int nb = 0;
-    DAWN_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sssp_kernel, kThreads, 0));
+    DAWN_CUDA_TRY(cudaFuncSetAttribute(sssp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBitmapMax));
+    const size_t words4 = (size_t)(g->nwords + 3) / 4 * 4;
+    g->sssp_smem_bytes = words4 * 4 <= (size_t)kSmemBitmapMax ? (int)(words4 * 4) : 0;
+    DAWN_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sssp_kernel, kThreads, g->sssp_smem_bytes));
     if (nb < 1) return fail(DAWN_E_CUDA, "persistent SSSP kernel cannot be resident on an SM");
     g->sssp_blocks_per_sm = nb;
     return DAWN_OK;
@@ -546,9 +574,13 @@ int sssp_launch(dawn_graph* g, int32_t src, int32_t* dist_dev, const dawn_sssp_o
         return fail(DAWN_E_INVALID, "unknown mode %d", a.mode);
     int bps = g->sssp_blocks_per_sm;
     if (opts && opts->blocks_per_sm > 0 && opts->blocks_per_sm < bps) bps = opts->blocks_per_sm;
+    a.smem_words = g->sssp_smem_bytes / 4;
+    a.bar_parity = (int32_t)(g->sssp_launches & 1u);
     dim3 grid(g->sms * bps), block(kThreads);
     void* args[] = {&a};
-    DAWN_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)sssp_kernel, grid, block, args, 0, st));
+    DAWN_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)sssp_kernel, grid, block, args,
+                                              (size_t)g->sssp_smem_bytes, st));
+    g->sssp_launches += 1;  // only a launch that was accepted zeroes the other counter
     return DAWN_OK;
 }
 
@@ -679,6 +711,8 @@ int sssp_noalloc(const int32_t* row_ptr, const int32_t* col_idx, int32_t n, int6
     a.nwords = (int32_t)(((int64_t)n + 31) / 32);
     a.src = src;
     a.mode = DAWN_MODE_PUSH;
+    a.bar_parity = 0;  // the whole control block was just zeroed
+    a.smem_words = 0;
     a.alpha = 15;
     a.beta = 18;
     a.spin_limit = kDefaultSpin;
