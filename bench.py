@@ -225,6 +225,8 @@ def run_gpu(args):
             distrib.barrier()
 
     g, srcs = build_workload()
+    if args.sources:
+        srcs = srcs[: args.sources]
     n = g.n
     stream = torch.cuda.current_stream()
     h = dawn.dawn_graph_upload(g.row_ptr, g.col_idx, flags=dawn.DAWN_SYMMETRIC, stream=stream)
@@ -283,18 +285,20 @@ def run_gpu(args):
     traffic = recorded_traffic(SSSP_SRC, ROOT / "profiles" / "sssp_kernel_rmat20.md")
 
     # end to end through the public call with a pinned host result buffer
-    host_dist = torch.empty(n, dtype=torch.int32, pin_memory=True)
-    barrier()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        for s in srcs:
-            dawn.dawn_sssp(h, int(s), host_dist, stream)
-    torch.cuda.synchronize()
-    e2e_s = (time.perf_counter() - t0) / args.steps
-    e2e = {"value": world * edges_per_step / e2e_s / 1e9, "unit": "GTEPS",
-           "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 4 * n * len(srcs),
-           "note": "dawn_sssp with a pinned host dist buffer per source (synchronous call, D2H inside); no L2 flush"}
+    e2e = None
+    if not args.no_e2e:
+        host_dist = torch.empty(n, dtype=torch.int32, pin_memory=True)
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            for s in srcs:
+                dawn.dawn_sssp(h, int(s), host_dist, stream)
+        torch.cuda.synchronize()
+        e2e_s = (time.perf_counter() - t0) / args.steps
+        e2e = {"value": world * edges_per_step / e2e_s / 1e9, "unit": "GTEPS",
+               "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 4 * n * len(srcs),
+               "note": "dawn_sssp with a pinned host dist buffer per source (synchronous call, D2H inside); no L2 flush"}
 
     dawn.dawn_graph_free(h)
     if rank != 0:
@@ -335,6 +339,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget-s", type=float, default=15.0)
     ap.add_argument("--ref-budget-s", type=float, default=10.0)
+    ap.add_argument("--sources", type=int, default=0,
+                    help="use only the first N of the 64 sources (small profiling runs; not a bench value)")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end host-buffer pass")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("at least 3 warm-up steps")
