@@ -101,6 +101,7 @@ struct dawn_graph {
     int32_t* ms_counts = nullptr;     // per-lane per-level new-vertex counts
     size_t ms_counts_cap = 0;
     int ms_blocks_per_sm = 0;
+    unsigned ms_launches = 0;         // picks the barrier counter of the next batched launch
 };
 
 namespace dawn {
