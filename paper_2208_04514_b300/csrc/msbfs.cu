@@ -32,6 +32,11 @@ constexpr int kMsThreads = 1024;
 constexpr int kMsWarps = kMsThreads / 32;
 constexpr int kMsMaxLanes = 256;
 constexpr int kMsSerial = 8;  // in-neighbours a lane tests before the warp takes over
+// In-lists longer than this (after the lane's own tests) are deferred to the
+// end of the level and scanned by the whole CTA: a hub's row is split over
+// 1024 threads instead of one warp walking it 32 arcs at a time.
+constexpr int kMsHeavy = 512;
+constexpr int kMsHeavyMax = 32;  // deferred vertices per CTA per level
 constexpr unsigned kFull = 0xffffffffu;
 
 struct alignas(128) MsCtl {
@@ -158,6 +163,9 @@ __global__ void __launch_bounds__(kMsThreads, 1) msbfs_kernel(MsArgs a) {
     __shared__ int s_ecc[kMsMaxLanes];
     __shared__ long long s_dsum[kMsMaxLanes];
     __shared__ unsigned long long s_newmask[4];
+    __shared__ int s_hcount;
+    __shared__ int s_hv[kMsHeavyMax], s_hj[kMsHeavyMax], s_hie[kMsHeavyMax];
+    __shared__ unsigned long long s_hvv[kMsHeavyMax][W], s_hacc[kMsHeavyMax][W];
 
     MsCtl* ctl = a.ctl;
     if (ms_ld_relaxed_s32(&ctl->status) != DEV_OK) return;
@@ -179,6 +187,7 @@ __global__ void __launch_bounds__(kMsThreads, 1) msbfs_kernel(MsArgs a) {
         s_dsum[i] = 0;
     }
     if (threadIdx.x < 4) s_newmask[threadIdx.x] = 0;
+    if (threadIdx.x == 0) s_hcount = 0;
 
     for (int b = 0; b < nbatches; ++b) {
         const int s0 = b * L;
@@ -241,7 +250,22 @@ __global__ void __launch_bounds__(kMsThreads, 1) msbfs_kernel(MsArgs a) {
                         if (all) { j = ie; break; }
                     }
                 }
-                unsigned rest = __ballot_sync(kFull, need && j < ie);
+                bool deferred = false;
+                if (need && ie - j > kMsHeavy) {
+                    const int slot = atomicAdd(&s_hcount, 1);
+                    if (slot < kMsHeavyMax) {
+                        deferred = true;
+                        s_hv[slot] = v;
+                        s_hj[slot] = j;
+                        s_hie[slot] = ie;
+#pragma unroll
+                        for (int w = 0; w < W; ++w) {
+                            s_hvv[slot][w] = vv[w];
+                            s_hacc[slot][w] = acc[w];
+                        }
+                    }
+                }
+                unsigned rest = __ballot_sync(kFull, need && !deferred && j < ie);
                 while (rest) {
                     const int src_lane = __ffs(rest) - 1;
                     rest &= rest - 1;
@@ -273,8 +297,8 @@ __global__ void __launch_bounds__(kMsThreads, 1) msbfs_kernel(MsArgs a) {
                 // new bits, next visited words, distances, counts
 #pragma unroll
                 for (int w = 0; w < W; ++w) {
-                    const unsigned long long nb = need ? (acc[w] & ~vv[w] & ~fin[w]) : 0ull;
-                    if (valid) vnext[(long long)v * W + w] = vv[w] | nb;
+                    const unsigned long long nb = (need && !deferred) ? (acc[w] & ~vv[w] & ~fin[w]) : 0ull;
+                    if (valid && !deferred) vnext[(long long)v * W + w] = vv[w] | nb;
                     unsigned long long uni = warp_or64(nb);
                     if (lane == 0 && uni) atomicOr(&s_newmask[w], uni);
                     while (uni) {
@@ -289,6 +313,43 @@ __global__ void __launch_bounds__(kMsThreads, 1) msbfs_kernel(MsArgs a) {
                 }
             }
             __syncthreads();
+            // deferred long in-lists: the whole CTA scans each one
+            const int nh = min(s_hcount, kMsHeavyMax);
+            for (int h = 0; h < nh; ++h) {
+                unsigned long long part[W];
+#pragma unroll
+                for (int w = 0; w < W; ++w) part[w] = 0ull;
+                const int hie = s_hie[h];
+                for (int jj = s_hj[h] + threadIdx.x; jj < hie; jj += kMsThreads) {
+                    const int u = __ldg(a.in_idx + jj);
+#pragma unroll
+                    for (int w = 0; w < W; ++w) part[w] |= __ldcg(vcur + (long long)u * W + w);
+                }
+#pragma unroll
+                for (int w = 0; w < W; ++w) {
+                    part[w] = warp_or64(part[w]);
+                    if (lane == 0 && part[w]) atomicOr(&s_hacc[h][w], part[w]);
+                }
+            }
+            __syncthreads();
+            for (int h = threadIdx.x >> 5; h < nh; h += kMsWarps) {
+                const int v = s_hv[h];
+                unsigned long long nbw[W];
+#pragma unroll
+                for (int w = 0; w < W; ++w) {
+                    nbw[w] = s_hacc[h][w] & ~s_hvv[h][w] & ~fin[w];
+                    if (lane == w) vnext[(long long)v * W + w] = s_hvv[h][w] | nbw[w];
+                    if (lane == 0 && nbw[w]) atomicOr(&s_newmask[w], nbw[w]);
+                }
+                for (int i = lane; i < L; i += 32) {
+                    if ((nbw[i >> 6] >> (i & 63)) & 1ull) {
+                        store_dist(a, s0, i, v, t);
+                        atomicAdd(&s_cnt[i], 1);
+                    }
+                }
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) s_hcount = 0;
             // fold this level's counts into the batch accumulators
             for (int s = threadIdx.x; s < L; s += kMsThreads) {
                 const int c = s_cnt[s];
