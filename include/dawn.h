@@ -222,15 +222,23 @@ DAWN_API int dawn_msbfs_ex(dawn_graph_t g, const int32_t* sources, int32_t k, vo
                            const dawn_msbfs_opts* opts, void* stream);
 
 /*
- * Continuous-batching server over several resident graphs.  Requests name a
- * graph and k sources; their sources are packed into free bit lanes of that
- * graph's running batch as lanes free up, so requests that arrive while
- * others run share the device.  Every lane advances one level per device
- * iteration; a lane's distance is (iteration - its start iteration), so the
- * result of a request is identical alone and in any mix.
+ * Continuous-batching server over several resident graphs (APSP-style
+ * batching of Sec. 3.3 applied to a request stream; the paper has no
+ * serving layer).  Requests name a graph and k sources; each source becomes
+ * one bit lane of that graph, admitted as lanes free up, so requests that
+ * arrive while others run share the device.  One persistent kernel advances
+ * every occupied lane one level per iteration (bit-lane Alg. 1 pull); a
+ * lane's distance is (iteration - its start iteration), so a request's
+ * result is identical alone and in any mix.  A host thread owned by the
+ * server admits requests and collects completions; while work is queued the
+ * server's kernel occupies every SM (other kernels wait), and it exits
+ * after about 2 ms without work.
  *   graphs          ngraphs handles (borrowed; must outlive the server).
- *   mem_budget_bytes  device bytes available to admitted requests' distance
- *                   blocks (k * n * dist_bytes each); 0 = no limit.
+ *   mem_budget_bytes  device bytes for the distance blocks of admitted
+ *                   requests whose dist_out is host memory (k * n * dist_bytes
+ *                   each, held from admission until the block is copied out);
+ *                   a request waits in the queue until its block fits; 0 =
+ *                   1 GiB.  Requests with device dist_out write in place.
  *   max_lanes       lanes per graph batch: 64, 128 or 256.
  */
 DAWN_API int dawn_serve_create(const dawn_graph_t* graphs, int ngraphs, size_t mem_budget_bytes,
@@ -249,6 +257,11 @@ DAWN_API int dawn_serve_submit(dawn_server_t s, int graph_idx, const int32_t* so
 /* State of a request (DAWN_REQ_*).  Returns the request's error code once it
  * has failed (e.g. DAWN_E_OVERFLOW), DAWN_E_STATE for an unknown id. */
 DAWN_API int dawn_serve_poll(dawn_server_t s, uint64_t req_id, int* state);
+
+/* Host clock (seconds, steady clock) at which the request was submitted and
+ * at which it became DONE or FAILED (0 while open): its latency is the
+ * difference.  DAWN_E_STATE for an unknown id. */
+DAWN_API int dawn_serve_times(dawn_server_t s, uint64_t req_id, double* submit_s, double* done_s);
 
 /* Block until every submitted request is done or failed (timeout_ms < 0:
  * no limit).  DAWN_E_TIMEOUT if the time ran out first. */

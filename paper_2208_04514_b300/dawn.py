@@ -86,6 +86,7 @@ _SIGNATURES = {
     "dawn_serve_create": [_vp, ctypes.c_int, _sz, ctypes.c_int, ctypes.POINTER(_vp)],
     "dawn_serve_submit": [_vp, ctypes.c_int, _vp, _i32, ctypes.c_int, _vp, ctypes.POINTER(_u64)],
     "dawn_serve_poll": [_vp, _u64, ctypes.POINTER(ctypes.c_int)],
+    "dawn_serve_times": [_vp, _u64, _vp, _vp],
     "dawn_serve_drain": [_vp, _i64],
     "dawn_serve_destroy": [_vp],
     "dawn_last_error": [],
@@ -265,6 +266,13 @@ def dawn_serve_poll(s: int, req_id: int) -> int:
     st = ctypes.c_int()
     _check(load().dawn_serve_poll(s, req_id, ctypes.byref(st)))
     return st.value
+
+
+def dawn_serve_times(s: int, req_id: int) -> tuple[float, float]:
+    """(submit, done) host steady-clock seconds of a request (done = 0 while open)."""
+    a, b = ctypes.c_double(), ctypes.c_double()
+    _check(load().dawn_serve_times(s, req_id, ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
 
 
 def dawn_serve_drain(s: int, timeout_ms: int = -1) -> None:

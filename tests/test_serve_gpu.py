@@ -1,0 +1,139 @@
+"""Continuous-batching server: every request's distance rows against the CPU
+oracle, bit-exact, and the same request alone and inside a mix of requests
+of uneven source counts on several resident graphs.  Also admission by the
+device-memory budget, device outputs, the int16 overflow report and bad
+arguments."""
+import time
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2208_04514_b300 import graphgen as gg
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def graphs():
+    return [gg.rmat(10, seed=21), gg.erdos_renyi(1024, 8.0, seed=1), gg.lattice(32, 32, 0.1, seed=3),
+            gg.rmat(12, seed=22, symmetrise=False)]
+
+
+@pytest.fixture(scope="module")
+def handles(dawn, graphs):
+    hs = [dawn.dawn_graph_upload(g.row_ptr, g.col_idx, flags=dawn.DAWN_SYMMETRIC if g.symmetric else dawn.DAWN_DIRECTED)
+          for g in graphs]
+    yield hs
+    for h in hs:
+        dawn.dawn_graph_free(h)
+
+
+def want_rows(g, srcs):
+    return oracle.msbfs(g.row_ptr, g.col_idx, np.asarray(srcs, dtype=np.int32))[0]
+
+
+def wait_done(dawn, s, rid, timeout=60.0):
+    t0 = time.time()
+    while time.time() - t0 < timeout:
+        if dawn.dawn_serve_poll(s, rid) == dawn.DAWN_REQ_DONE:
+            return
+        time.sleep(0.001)
+    raise AssertionError(f"request {rid} not done after {timeout} s")
+
+
+def test_alone_and_in_the_mix(dawn, graphs, handles):
+    s = dawn.dawn_serve_create(handles, 0, 256)
+    try:
+        probe_srcs = np.array([3, 17, 200, 511, 1000], dtype=np.int32)
+        alone = np.full((5, graphs[0].n), 99, dtype=np.int16)
+        rid = dawn.dawn_serve_submit(s, 0, probe_srcs, dist_bytes=2, dist_out=alone)
+        wait_done(dawn, s, rid)
+        np.testing.assert_array_equal(alone, want_rows(graphs[0], probe_srcs))
+
+        rng = np.random.default_rng(7)
+        reqs = []
+        for i in range(120):
+            gi = int(rng.integers(0, len(graphs)))
+            k = int(min(300, max(1, np.floor(256 ** rng.random()))))
+            srcs = rng.integers(0, graphs[gi].n, k).astype(np.int32)
+            db = 2 if rng.random() < 0.5 else 4
+            out = np.full((k, graphs[gi].n), 99, dtype=np.int16 if db == 2 else np.int32)
+            reqs.append((dawn.dawn_serve_submit(s, gi, srcs, dist_bytes=db, dist_out=out), gi, srcs, out))
+            if i == 60:  # the probe again, in the middle of the stream
+                mixed = np.full((5, graphs[0].n), 99, dtype=np.int16)
+                mid = dawn.dawn_serve_submit(s, 0, probe_srcs, dist_bytes=2, dist_out=mixed)
+            if i % 10 == 0:
+                time.sleep(0.002)  # arrivals spread while earlier requests run
+        dawn.dawn_serve_drain(s, 120000)
+        wait_done(dawn, s, mid)
+        np.testing.assert_array_equal(mixed, alone)
+        for rid, gi, srcs, out in reqs:
+            assert dawn.dawn_serve_poll(s, rid) == dawn.DAWN_REQ_DONE
+            np.testing.assert_array_equal(out.astype(np.int64), want_rows(graphs[gi], srcs), err_msg=f"request {rid}")
+            t_sub, t_done = dawn.dawn_serve_times(s, rid)
+            assert t_done >= t_sub > 0
+    finally:
+        dawn.dawn_serve_destroy(s)
+
+
+def test_memory_budget_admission_and_device_outputs(dawn, graphs, handles):
+    g = graphs[1]
+    block = 64 * g.n * 4
+    s = dawn.dawn_serve_create(handles, block + 1024, 64)  # room for one 64-source int32 block at a time
+    try:
+        with pytest.raises(dawn.DawnError) as ei:
+            dawn.dawn_serve_submit(s, 1, np.arange(65, dtype=np.int32), dist_bytes=4,
+                                   dist_out=np.zeros((65, g.n), dtype=np.int32))
+        assert ei.value.code == dawn.DAWN_E_NOMEM
+        outs = []
+        for r in range(6):
+            srcs = np.arange(r, r + 64, dtype=np.int32)
+            out = np.zeros((64, g.n), dtype=np.int32)
+            outs.append((dawn.dawn_serve_submit(s, 1, srcs, dist_bytes=4, dist_out=out), srcs, out))
+        dev_srcs = np.array([5, 6, 7], dtype=np.int32)
+        dev_out = torch.full((3, graphs[2].n), 99, dtype=torch.int32, device="cuda")
+        rd = dawn.dawn_serve_submit(s, 2, dev_srcs, dist_bytes=4, dist_out=dev_out)
+        dawn.dawn_serve_drain(s, 60000)
+        for rid, srcs, out in outs:
+            np.testing.assert_array_equal(out, want_rows(g, srcs))
+        assert dawn.dawn_serve_poll(s, rd) == dawn.DAWN_REQ_DONE
+        np.testing.assert_array_equal(dev_out.cpu().numpy(), want_rows(graphs[2], dev_srcs))
+    finally:
+        dawn.dawn_serve_destroy(s)
+
+
+def test_overflow_and_bad_arguments(dawn):
+    n = 40000
+    s_ = np.arange(n - 1)
+    path = gg.from_arcs(n, np.r_[s_, s_ + 1], np.r_[s_ + 1, s_], symmetric=True)
+    h = dawn.dawn_graph_upload(path.row_ptr, path.col_idx, flags=dawn.DAWN_SYMMETRIC)
+    s = dawn.dawn_serve_create([h], 0, 64)
+    try:
+        out16 = np.zeros((1, n), dtype=np.int16)
+        r16 = dawn.dawn_serve_submit(s, 0, np.array([0], dtype=np.int32), dist_bytes=2, dist_out=out16)
+        out32 = np.zeros((1, n), dtype=np.int32)
+        r32 = dawn.dawn_serve_submit(s, 0, np.array([0], dtype=np.int32), dist_bytes=4, dist_out=out32)
+        with pytest.raises(dawn.DawnError):
+            dawn.dawn_serve_drain(s, 120000)  # the int16 request fails
+        with pytest.raises(dawn.DawnError) as ei:
+            dawn.dawn_serve_poll(s, r16)
+        assert ei.value.code == dawn.DAWN_E_OVERFLOW
+        assert dawn.dawn_serve_poll(s, r32) == dawn.DAWN_REQ_DONE
+        np.testing.assert_array_equal(out32[0], np.arange(n))
+        with pytest.raises(dawn.DawnError) as ei:
+            dawn.dawn_serve_poll(s, 987654)
+        assert ei.value.code == dawn.DAWN_E_STATE
+        for bad in [dict(graph_idx=1), dict(sources=np.array([n], dtype=np.int32)), dict(dist_bytes=3)]:
+            args = dict(graph_idx=0, sources=np.array([0], dtype=np.int32), dist_bytes=4)
+            args.update(bad)
+            with pytest.raises(dawn.DawnError) as ei:
+                dawn.dawn_serve_submit(s, args["graph_idx"], args["sources"], dist_bytes=args["dist_bytes"],
+                                       dist_out=np.zeros((1, n), dtype=np.int32))
+            assert ei.value.code == dawn.DAWN_E_INVALID
+    finally:
+        dawn.dawn_serve_destroy(s)
+        dawn.dawn_graph_free(h)
+    with pytest.raises(dawn.DawnError):
+        dawn.dawn_serve_create([h], 0, 100)
