@@ -115,8 +115,7 @@ def test_overflow_and_bad_arguments(dawn):
         r16 = dawn.dawn_serve_submit(s, 0, np.array([0], dtype=np.int32), dist_bytes=2, dist_out=out16)
         out32 = np.zeros((1, n), dtype=np.int32)
         r32 = dawn.dawn_serve_submit(s, 0, np.array([0], dtype=np.int32), dist_bytes=4, dist_out=out32)
-        with pytest.raises(dawn.DawnError):
-            dawn.dawn_serve_drain(s, 120000)  # the int16 request fails
+        dawn.dawn_serve_drain(s, 120000)  # returns once every request is done or failed
         with pytest.raises(dawn.DawnError) as ei:
             dawn.dawn_serve_poll(s, r16)
         assert ei.value.code == dawn.DAWN_E_OVERFLOW
