@@ -74,7 +74,7 @@ def build_graphgen(force: bool = False) -> Path:
         return GRAPHGEN_SO
     LIB_DIR.mkdir(parents=True, exist_ok=True)
     tmp = GRAPHGEN_SO.with_suffix(".so.tmp")
-    _run(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", str(tmp), str(src), "-lm"])
+    _run(["gcc", "-O2", "-std=c11", "-fPIC", "-fopenmp", "-shared", "-o", str(tmp), str(src), "-lm"])
     tmp.replace(GRAPHGEN_SO)
     return GRAPHGEN_SO
 

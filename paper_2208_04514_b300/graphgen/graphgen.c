@@ -123,21 +123,31 @@ static gg_csr* csr_from_arcs(int32_t n, int64_t na, int32_t* src, int32_t* dst) 
     for (int64_t i = 0; i < na; ++i)
         if (src[i] != dst[i]) col[pos[src[i]]++] = dst[i];
     free(pos);
-    /* sort + dedup each row, compacting in place */
+    /* sort + dedup each row (rows are independent: in parallel), then
+     * compact the rows in order */
     int32_t* rp = (int32_t*)malloc(((size_t)n + 1) * sizeof(int32_t));
-    if (!rp) { free(col); free(cnt); free(g); return NULL; }
-    int64_t w = 0;
-    rp[0] = 0;
+    int64_t* keep = (int64_t*)malloc((size_t)n * sizeof(int64_t));
+    if (!rp || !keep) { free(rp); free(keep); free(col); free(cnt); free(g); return NULL; }
+#pragma omp parallel for schedule(dynamic, 1024)
     for (int32_t v = 0; v < n; ++v) {
         int64_t b = cnt[v], e = cnt[v + 1];
         sort_row(col + b, e - b);
-        int64_t row_start = w;
+        int64_t w = b;
         for (int64_t i = b; i < e; ++i) {
-            if (w > row_start && col[w - 1] == col[i]) continue;
+            if (w > b && col[w - 1] == col[i]) continue;
             col[w++] = col[i];
         }
+        keep[v] = w - b;
+    }
+    int64_t w = 0;
+    rp[0] = 0;
+    for (int32_t v = 0; v < n; ++v) {
+        const int64_t b = cnt[v], k = keep[v];
+        if (w != b) memmove(col + w, col + b, (size_t)k * sizeof(int32_t));
+        w += k;
         rp[v + 1] = (int32_t)w;
     }
+    free(keep);
     free(cnt);
     g->m = w;
     g->row_ptr = rp;
