@@ -287,6 +287,102 @@ def bench_batched(dawn, torch, flush, plain_sample=4096):
     return out
 
 
+def bench_serving(dawn, torch, nreq=48, seed=6):
+    """Continuous-batching server on 8 resident graphs: RMAT scales 14, 16, 18,
+    20, 22 (edge factor 16, symmetrised) and 1024^2, 2048^2, 4096^2 lattices
+    (bonds deleted with p = 0.1).  Requests: graph uniform over the 8, k =
+    floor(256^U) sources in [1, 256] (log-uniform), sources uniform, int16
+    rows written in place into device buffers.  Saturated throughput is
+    measured first (all requests at once); then Poisson arrival streams at
+    0.3x, 0.7x and 1.0x of it.  The plain path serves the 1.0x stream FIFO,
+    one dawn_sssp launch per source (int32 rows): its per-request service
+    times are measured back to back and its latencies follow from the FIFO
+    single-server recursion start = max(arrival, previous done)."""
+    from paper_2208_04514_b300 import graphgen as gg
+    specs = [("rmat14", lambda: gg.rmat(14, seed=114)), ("rmat16", lambda: gg.rmat(16, seed=116)),
+             ("rmat18", lambda: gg.rmat(18, seed=118)), ("rmat20", lambda: gg.rmat(20, seed=120)),
+             ("rmat22", lambda: gg.rmat(22, seed=122)), ("lattice1024", lambda: gg.lattice(1024, 1024, 0.1, seed=3)),
+             ("lattice2048", lambda: gg.lattice(2048, 2048, 0.1, seed=3)),
+             ("lattice4096", lambda: gg.lattice(4096, 4096, 0.1, seed=3))]
+    handles, ns = [], []
+    for name, make in specs:
+        g = make()
+        handles.append(dawn.dawn_graph_upload(g.row_ptr, g.col_idx, flags=dawn.DAWN_SYMMETRIC))
+        ns.append(g.n)
+        del g
+    rng = np.random.default_rng(seed)
+
+    def draw(count):
+        reqs = []
+        for _ in range(count):
+            gi = int(rng.integers(0, len(specs)))
+            k = int(min(256, max(1, np.floor(256 ** rng.random()))))
+            reqs.append((gi, rng.integers(0, ns[gi], k).astype(np.int32)))
+        return reqs
+
+    def serve(reqs, arrivals):
+        s = dawn.dawn_serve_create(handles, 0, 256)
+        outs, ids = [], []
+        t0 = time.perf_counter()
+        for (gi, srcs), at in zip(reqs, arrivals):
+            while time.perf_counter() - t0 < at:
+                pass
+            out = torch.empty((len(srcs), ns[gi]), dtype=torch.int16, device="cuda")
+            outs.append(out)
+            ids.append(dawn.dawn_serve_submit(s, gi, srcs, dist_bytes=2, dist_out=out))
+        dawn.dawn_serve_drain(s, 600000)
+        t_end = time.perf_counter()
+        times = [dawn.dawn_serve_times(s, r) for r in ids]
+        dawn.dawn_serve_destroy(s)
+        lat = np.array([d - a for a, d in times])
+        span = max(d for _, d in times) - min(a for a, _ in times)
+        del outs
+        return lat, len(reqs) / span, t_end - t0
+
+    out = {"workload": "serve_8graphs", "graphs": [n for n, _ in specs], "requests_per_rate": nreq,
+           "dist": "int16 rows written in place into device buffers", "rates": {}}
+    cal = draw(nreq)
+    lat, qps_sat, _ = serve(cal, np.zeros(nreq))
+    out["saturated_queries_per_s"] = qps_sat
+    out["saturated_sources_per_s"] = sum(len(x[1]) for x in cal) * qps_sat / nreq
+    stream_10 = None
+    for frac in (0.3, 0.7, 1.0):
+        reqs = draw(nreq)
+        arrivals = np.cumsum(rng.exponential(1.0 / (frac * qps_sat), nreq))
+        lat, qps, _ = serve(reqs, arrivals)
+        out["rates"][f"{frac:.1f}x"] = {"offered_queries_per_s": frac * qps_sat, "queries_per_s": qps,
+                                       "p50_ms": 1e3 * float(np.percentile(lat, 50)),
+                                       "p99_ms": 1e3 * float(np.percentile(lat, 99))}
+        if frac == 1.0:
+            stream_10 = (reqs, arrivals)
+    # plain path on the 1.0x stream
+    reqs, arrivals = stream_10
+    stream = torch.cuda.current_stream()
+    service = []
+    for gi, srcs in reqs:
+        rows = torch.empty((len(srcs), ns[gi]), dtype=torch.int32, device="cuda")
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for i, sv in enumerate(srcs):
+            dawn.dawn_sssp_async(handles[gi], int(sv), rows[i], None, None, stream)
+        e1.record(stream)
+        dawn.dawn_graph_sync(handles[gi], stream)
+        service.append(e0.elapsed_time(e1) * 1e-3)
+        del rows
+    done_prev, lat = 0.0, []
+    for at, sv in zip(arrivals, service):
+        start = max(at, done_prev)
+        done_prev = start + sv
+        lat.append(done_prev - at)
+    lat = np.array(lat)
+    out["plain_1.0x"] = {"queries_per_s": len(reqs) / (done_prev - arrivals[0]),
+                         "p50_ms": 1e3 * float(np.percentile(lat, 50)), "p99_ms": 1e3 * float(np.percentile(lat, 99)),
+                         "busy_s": float(sum(service))}
+    for h in handles:
+        dawn.dawn_graph_free(h)
+    return out
+
+
 def run_gpu(args):
     import torch
     import torch.distributed as distrib
@@ -401,6 +497,9 @@ def run_gpu(args):
     if world == 1 and not args.no_secondary:
         line["secondary"] = {"lattice": bench_lattice(dawn, torch, flush),
                              "batched": bench_batched(dawn, torch, flush)}
+        del flush
+        torch.cuda.empty_cache()
+        line["secondary"]["serving"] = bench_serving(dawn, torch, nreq=args.serve_requests)
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(g, srcs, args.cpu_budget_s)
     print(json.dumps(line), flush=True)
@@ -422,6 +521,7 @@ def main():
     ap.add_argument("--sources", type=int, default=0,
                     help="use only the first N of the 64 sources (small profiling runs; not a bench value)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end host-buffer pass")
+    ap.add_argument("--serve-requests", type=int, default=48, help="requests per arrival rate in the serving mix")
     ap.add_argument("--no-secondary", action="store_true",
                     help="skip the lattice, batched and serving workloads reported beside the headline")
     args = ap.parse_args()
