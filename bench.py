@@ -138,6 +138,20 @@ def algorithmic_bytes(n, stats):
     return 4 * stats["edges"] + 16 * stats["reached"] + 4 * n + stats["pull_steps"] * ((n + 7) // 8)
 
 
+def aggregate_replicas(ms_step: float, edges_per_step: int, world: int, device: str = "cpu"):
+    """Whole-job figures of independent replicas: the step time is the MAX
+    over ranks, the work is the SUM over ranks (each rank runs its own copy of
+    the workload; no collective touches the data path)."""
+    import torch
+    import torch.distributed as distrib
+    t = torch.tensor([ms_step], dtype=torch.float64, device=device)
+    e = torch.tensor([edges_per_step], dtype=torch.int64, device=device)
+    if world > 1:
+        distrib.all_reduce(t, op=distrib.ReduceOp.MAX)
+        distrib.all_reduce(e, op=distrib.ReduceOp.SUM)
+    return float(t.item()), int(e.item())
+
+
 def build_workload():
     from paper_2208_04514_b300 import graphgen as gg
     g = gg.rmat(20, 16, 0.57, 0.19, 0.19, seed=2, symmetrise=True)
@@ -444,11 +458,8 @@ def run_gpu(args):
     edges_per_step = sum(x["edges"] for x in st)
     ms_step = kernel_ms / args.steps
     # max over ranks of the device time
-    t_ms = torch.tensor([ms_step], dtype=torch.float64, device="cuda")
-    if world > 1:
-        distrib.all_reduce(t_ms, op=distrib.ReduceOp.MAX)
-    ms_step_max = float(t_ms.item())
-    value = world * edges_per_step / (ms_step_max * 1e-3) / 1e9
+    ms_step_max, edges_all = aggregate_replicas(ms_step, edges_per_step, world, device="cuda")
+    value = edges_all / (ms_step_max * 1e-3) / 1e9
 
     # roofline of the persistent SSSP kernel (one launch = one source)
     peak, peak_kind = measured_peaks()
