@@ -118,8 +118,8 @@ DAWN_API int dawn_sssp(dawn_graph_t g, int32_t src, int32_t* dist, void* stream)
 
 typedef struct {
     int32_t mode;          /* DAWN_MODE_*; 0 = AUTO */
-    int32_t alpha;         /* push -> pull when m_f * alpha > m_u; 0 = default (15) */
-    int32_t beta;          /* pull -> push when n_f * beta < n and n_f shrank; 0 = default (18) */
+    int32_t alpha;         /* push -> pull when m_f * alpha > m_u; 0 = tuned or 15 */
+    int32_t beta;          /* pull -> push when n_f * beta < n and n_f shrank; 0 = tuned or 18 */
     int32_t blocks_per_sm; /* CTAs per SM of the persistent grid; 0 = occupancy-derived */
     int64_t spin_limit;    /* grid-barrier spin budget in SM clock cycles; 0 = default (~2 s) */
     int64_t* trace;        /* device memory or NULL: one record of 4 int64 per grid barrier,
@@ -128,7 +128,8 @@ typedef struct {
                               conversion; count = vertices the level reached (entries queued
                               for kind 4); records past trace_cap are dropped */
     int32_t trace_cap;     /* records that fit in trace */
-    int32_t reserved;
+    int32_t pull_serial;   /* in-neighbours a lane tests on its own in a pull level before
+                              the warp takes the rest of the row; 0 = tuned or 8 */
 } dawn_sssp_opts;
 
 typedef struct {
@@ -188,6 +189,32 @@ DAWN_API int dawn_graph_sync(dawn_graph_t g, void* stream);
  */
 DAWN_API int dawn_sssp_noalloc(const int32_t* row_ptr, const int32_t* col_idx, int32_t n, int64_t m,
                                int32_t src, int32_t* dist, void* stream);
+
+/*
+ * Autotuner (the paper fixes one block size and has no tuner; Sec. 4.1).
+ * Times short trials of dawn_sssp on `sample` (up to 16 sources) for a grid
+ * of push/pull switch thresholds (alpha, beta) and per-lane pull lengths,
+ * and of dawn_msbfs for 64 / 128 / 256 lanes (the sample repeated to 1024
+ * sources), then stores the fastest settings in g: later calls whose options
+ * leave these fields at 0 use them.  Results are bit-identical whatever the
+ * settings; only time changes.  sample: host or device int32[k], k >= 1.
+ * out (nullable) receives the choice and the times measured with it.
+ * Synchronizes `stream`.
+ */
+typedef struct {
+    int32_t alpha;
+    int32_t beta;
+    int32_t pull_serial;
+    int32_t lanes;
+    double sssp_us;            /* mean device time per source with the chosen settings */
+    double msbfs_sources_per_s;
+} dawn_tuning;
+
+DAWN_API int dawn_autotune(dawn_graph_t g, const int32_t* sample, int32_t k, dawn_tuning* out, void* stream);
+
+/* Store settings in g as dawn_autotune does (e.g. read back from a cache);
+ * fields at 0 keep the built-in defaults. */
+DAWN_API int dawn_set_tuning(dawn_graph_t g, const dawn_tuning* t);
 
 /*
  * Multi-source (APSP-style) batch: SSSP from each of k sources (Sec. 3.3,

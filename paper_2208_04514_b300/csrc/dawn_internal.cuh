@@ -93,6 +93,7 @@ struct dawn_graph {
     int sssp_blocks_per_sm = 0;       // occupancy of the persistent kernel
     int sssp_smem_bytes = 0;          // dynamic shared memory: the pull levels' bitmap copy
     unsigned sssp_launches = 0;       // picks the barrier counter of the next launch
+    dawn_tuning tuning = {0, 0, 0, 0, 0.0, 0.0};  // 0 fields: built-in defaults
     // multi-source work buffers (allocated on first use)
     uint64_t* ms_vis[2] = {nullptr, nullptr};
     int ms_words_cap = 0;             // W capacity of ms_vis

@@ -446,6 +446,7 @@ int msbfs_run(dawn_graph* g, const int32_t* sources, int32_t k, void* dist_block
     int lanes = opts && opts->lanes ? opts->lanes : 0;
     if (lanes != 0 && lanes != 64 && lanes != 128 && lanes != 256)
         return fail(DAWN_E_INVALID, "lanes = %d: need 64, 128 or 256", lanes);
+    if (lanes == 0 && g->tuning.lanes > 0) lanes = g->tuning.lanes;
     if (lanes == 0) lanes = k <= 64 ? 64 : (k <= 128 ? 128 : 256);
     const int W = lanes / 64;
     const long long spin = (opts && opts->spin_limit > 0) ? opts->spin_limit : kDefaultSpin;

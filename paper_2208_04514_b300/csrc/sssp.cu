@@ -72,6 +72,7 @@ struct SsspArgs {
     int32_t alpha;
     int32_t beta;
     int32_t trace_cap;
+    int32_t pull_serial;     // in-neighbours a lane tests alone in a pull level
     int32_t bar_parity;      // which of the two barrier counters this launch uses
     int32_t smem_words;      // > 0: pull levels copy the bitmap (this many words) to shared memory
 };
@@ -297,11 +298,10 @@ __device__ void push_level(const SsspArgs& a, int step, uint32_t* vis, Queue qin
 
 // BOVM pull: every unreached vertex tests its in-neighbours against the
 // step-start bitmap vcur, stopping at the first hit (Eq. 4); results go to
-// vnext.  A lane first tests up to kPullSerial in-neighbours of its own
+// vnext.  A lane first tests up to pull_serial in-neighbours of its own
 // vertex; vertices with in-arcs left are then taken one at a time by the
 // whole warp, 32 in-neighbours per round, so that one long row does not
 // hold 31 idle lanes.
-constexpr int kPullSerial = 8;
 
 // kSmem: the CTA first copies the whole step-start bitmap into shared memory
 // (it is read-only for the level), so every in-neighbour test is a shared
@@ -343,7 +343,7 @@ __device__ void pull_level(const SsspArgs& a, int step, const uint32_t* vcur, ui
                 ib = __ldg(a.in_ptr + v);
                 ie = __ldg(a.in_ptr + v + 1);
                 j = ib;
-                const int jl = min(ie, ib + kPullSerial);
+                const int jl = min(ie, ib + a.pull_serial);
                 for (; j + 4 <= jl && !found; j += 4) {
                     const int u0 = __ldg(a.in_idx + j), u1 = __ldg(a.in_idx + j + 1);
                     const int u2 = __ldg(a.in_idx + j + 2), u3 = __ldg(a.in_idx + j + 3);
@@ -563,8 +563,10 @@ int sssp_launch(dawn_graph* g, int32_t src, int32_t* dist_dev, const dawn_sssp_o
     a.nwords = g->nwords;
     a.src = src;
     a.mode = opts ? opts->mode : DAWN_MODE_AUTO;
-    a.alpha = (opts && opts->alpha > 0) ? opts->alpha : 15;
-    a.beta = (opts && opts->beta > 0) ? opts->beta : 18;
+    a.alpha = (opts && opts->alpha > 0) ? opts->alpha : (g->tuning.alpha > 0 ? g->tuning.alpha : 15);
+    a.beta = (opts && opts->beta > 0) ? opts->beta : (g->tuning.beta > 0 ? g->tuning.beta : 18);
+    a.pull_serial = (opts && opts->pull_serial > 0) ? opts->pull_serial
+                                                    : (g->tuning.pull_serial > 0 ? g->tuning.pull_serial : 8);
     a.spin_limit = (opts && opts->spin_limit > 0) ? opts->spin_limit : kDefaultSpin;
     a.trace = opts ? reinterpret_cast<long long*>(opts->trace) : nullptr;
     a.trace_cap = (opts && opts->trace) ? opts->trace_cap : 0;
@@ -715,6 +717,7 @@ int sssp_noalloc(const int32_t* row_ptr, const int32_t* col_idx, int32_t n, int6
     a.smem_words = 0;
     a.alpha = 15;
     a.beta = 18;
+    a.pull_serial = 8;
     a.spin_limit = kDefaultSpin;
     dim3 grid(d->sms * d->blocks_per_sm), block(kThreads);
     void* args[] = {&a};

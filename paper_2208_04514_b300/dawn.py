@@ -53,7 +53,7 @@ class DawnError(RuntimeError):
 class dawn_sssp_opts(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int32), ("alpha", ctypes.c_int32), ("beta", ctypes.c_int32),
                 ("blocks_per_sm", ctypes.c_int32), ("spin_limit", ctypes.c_int64),
-                ("trace", ctypes.c_void_p), ("trace_cap", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("trace", ctypes.c_void_p), ("trace_cap", ctypes.c_int32), ("pull_serial", ctypes.c_int32)]
 
 
 class dawn_sssp_stats(ctypes.Structure):
@@ -62,6 +62,14 @@ class dawn_sssp_stats(ctypes.Structure):
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+
+
+class dawn_tuning(ctypes.Structure):
+    _fields_ = [("alpha", ctypes.c_int32), ("beta", ctypes.c_int32), ("pull_serial", ctypes.c_int32),
+                ("lanes", ctypes.c_int32), ("sssp_us", ctypes.c_double), ("msbfs_sources_per_s", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
 
 
 class dawn_msbfs_opts(ctypes.Structure):
@@ -83,6 +91,8 @@ _SIGNATURES = {
     "dawn_sssp_noalloc": [_vp, _vp, _i32, _i64, _i32, _vp, _vp],
     "dawn_msbfs": [_vp, _vp, _i32, _vp, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp],
     "dawn_msbfs_ex": [_vp, _vp, _i32, _vp, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp, _vp],
+    "dawn_autotune": [_vp, _vp, _i32, _vp, _vp],
+    "dawn_set_tuning": [_vp, _vp],
     "dawn_serve_create": [_vp, ctypes.c_int, _sz, ctypes.c_int, ctypes.POINTER(_vp)],
     "dawn_serve_submit": [_vp, ctypes.c_int, _vp, _i32, ctypes.c_int, _vp, ctypes.POINTER(_u64)],
     "dawn_serve_poll": [_vp, _u64, ctypes.POINTER(ctypes.c_int)],
@@ -242,6 +252,23 @@ def dawn_msbfs_ex(g: int, sources, k: int | None = None, dist_block=None, dist_b
     _check(load().dawn_msbfs_ex(g, _ptr(sources), k, _ptr(dist_block), dist_bytes, layout,
                                 _ptr(ecc), _ptr(dsum), _ptr(reached), ctypes.byref(o) if o else None,
                                 _stream(stream)))
+
+
+# -------------------------------------------------------------- autotune --
+
+def dawn_autotune(g: int, sample, k: int | None = None, stream=None) -> dict:
+    """Time short trials on g and keep the fastest settings in g; returns them."""
+    k = int(sample.shape[0]) if k is None else k
+    t = dawn_tuning()
+    _check(load().dawn_autotune(g, _ptr(sample), k, ctypes.byref(t), _stream(stream)))
+    return t.as_dict()
+
+
+def dawn_set_tuning(g: int, tuning: dict) -> None:
+    t = dawn_tuning()
+    for f, _ in dawn_tuning._fields_:
+        setattr(t, f, tuning.get(f, 0))
+    _check(load().dawn_set_tuning(g, ctypes.byref(t)))
 
 
 # --------------------------------------------------------------- serving --
