@@ -219,11 +219,52 @@ __device__ __forceinline__ void load_batch(const Queue& q, int qn, int b, int la
     eoff = i < qn ? __ldcg(q.off + i) : INT_MAX;
 }
 
+// Append up to kPushGroup claimed rows per lane with one reservation per warp
+// (same layout rules as warp_enqueue; a lane's rows keep their order).
+constexpr int kPushGroup = 4;
+
+__device__ __forceinline__ void warp_enqueue_group(unsigned has, const int* rb, const int* re, int lane, Queue q,
+                                                   unsigned long long* qpack) {
+    int cnt = 0, deg = 0;
+#pragma unroll
+    for (int i = 0; i < kPushGroup; ++i) {
+        if ((has >> i) & 1u) {
+            const int d = re[i] - rb[i];
+            deg += d;
+            cnt += (d + kEntryArcs - 1) / kEntryArcs;
+        }
+    }
+    const int cincl = warp_inclusive_scan(cnt, lane);
+    const int ctot = __shfl_sync(kFull, cincl, 31);
+    if (ctot == 0) return;
+    const int dincl = warp_inclusive_scan(deg, lane);
+    const int dtot = __shfl_sync(kFull, dincl, 31);
+    unsigned long long base = 0;
+    if (lane == 31) base = atomicAdd(qpack, ((unsigned long long)ctot << 32) | (unsigned)dtot);
+    base = __shfl_sync(kFull, base, 31);
+    int pos = (int)(base >> 32) + cincl - cnt;
+    int aoff = (int)(base & 0xffffffffu) + dincl - deg;
+#pragma unroll
+    for (int i = 0; i < kPushGroup; ++i) {
+        if (!((has >> i) & 1u)) continue;
+        for (int s = rb[i]; s < re[i]; s += kEntryArcs) {
+            q.ent[pos] = make_int2(s, min(kEntryArcs, re[i] - s));
+            q.off[pos] = aoff + (s - rb[i]);
+            ++pos;
+        }
+        aoff += re[i] - rb[i];
+    }
+}
+
 // SOVM push: expand the frontier's rows (Eq. 7: the new vector is the union
 // of the CSR rows of the frontier).  The level's E arcs are cut into equal
 // ranges, a multiple of 32 long, one per warp of the grid; a warp finds the
 // entry holding its first arc with a 32-ary search over the sorted entry
-// offsets, then walks its range 32 consecutive arcs at a time.
+// offsets, then walks its range in groups of kPushGroup windows of 32
+// consecutive arcs.  Within a group the col_idx loads, the bitmap tests, the
+// atomicOr claims and the row_ptr loads of all windows are issued back to back,
+// so a warp waits for one chain of memory round trips per group, not per
+// window.
 __device__ void push_level(const SsspArgs& a, int step, uint32_t* vis, Queue qin, unsigned long long pack,
                            Queue qout, CtrSlot* out, long long& nf, long long& mf) {
     const int lane = threadIdx.x & 31;
@@ -251,48 +292,73 @@ __device__ void push_level(const SsspArgs& a, int step, uint32_t* vis, Queue qin
     int2 e;
     int eoff;
     load_batch(qin, qn, bstart, lane, e, eoff);
-    for (long long wb = a0; wb < a1; wb += 32) {
-        // keep the batch covering this window: if its last arc lies past the
-        // batch's last entry, restart the batch at the entry holding wb
-        const long long last = min(wb + 31, a1 - 1);
-        const int off31 = __shfl_sync(kFull, eoff, 31);
-        const int len31 = __shfl_sync(kFull, e.y, 31);
-        if (bstart + 32 < qn && last >= (long long)off31 + len31) {
-            int k;
-            if (wb >= (long long)off31 + len31) k = 32;
-            else k = 31 - __clz(__ballot_sync(kFull, (long long)eoff <= wb));
-            bstart += k;
-            load_batch(qin, qn, bstart, lane, e, eoff);
-        }
-        const long long t = wb + lane;
-        int o = 0;
+    for (long long gb = a0; gb < a1; gb += 32 * kPushGroup) {
+        int cidx[kPushGroup];
 #pragma unroll
-        for (int b = 16; b > 0; b >>= 1) {
-            const int cand = o + b;
-            const int pv = __shfl_sync(kFull, eoff, cand);
-            if ((long long)pv <= t) o = cand;
+        for (int q = 0; q < kPushGroup; ++q) {
+            const long long wb = gb + 32 * q;
+            cidx[q] = -1;
+            if (wb >= a1) continue;  // warp-uniform
+            // keep the batch covering this window: if its last arc lies past
+            // the batch's last entry, restart the batch at the entry holding wb
+            const long long last = min(wb + 31, a1 - 1);
+            const int off31 = __shfl_sync(kFull, eoff, 31);
+            const int len31 = __shfl_sync(kFull, e.y, 31);
+            if (bstart + 32 < qn && last >= (long long)off31 + len31) {
+                int k;
+                if (wb >= (long long)off31 + len31) k = 32;
+                else k = 31 - __clz(__ballot_sync(kFull, (long long)eoff <= wb));
+                bstart += k;
+                load_batch(qin, qn, bstart, lane, e, eoff);
+            }
+            const long long t = wb + lane;
+            int o = 0;
+#pragma unroll
+            for (int b = 16; b > 0; b >>= 1) {
+                const int cand = o + b;
+                const int pv = __shfl_sync(kFull, eoff, cand);
+                if ((long long)pv <= t) o = cand;
+            }
+            const int ostart = __shfl_sync(kFull, e.x, o);
+            const int ooff = __shfl_sync(kFull, eoff, o);
+            if (t < a1) cidx[q] = ostart + (int)(t - ooff);
         }
-        const int ostart = __shfl_sync(kFull, e.x, o);
-        const int ooff = __shfl_sync(kFull, eoff, o);
-        bool claimed = false;
-        int c = 0;
-        if (t < a1) {
-            c = __ldg(a.col_idx + ostart + (int)(t - ooff));
-            const uint32_t bit = 1u << (c & 31);
-            if (!(__ldcg(vis + (c >> 5)) & bit)) {
-                const uint32_t old = atomicOr(&vis[c >> 5], bit);
-                claimed = !(old & bit);
+        int c[kPushGroup];
+#pragma unroll
+        for (int q = 0; q < kPushGroup; ++q) c[q] = cidx[q] >= 0 ? __ldg(a.col_idx + cidx[q]) : -1;
+        uint32_t wv[kPushGroup];
+#pragma unroll
+        for (int q = 0; q < kPushGroup; ++q) wv[q] = c[q] >= 0 ? __ldcg(vis + (c[q] >> 5)) : kFull;
+        // targets that look unreached: claim them and fetch their rows together
+        int rb[kPushGroup], re[kPushGroup];
+        unsigned cand = 0;
+#pragma unroll
+        for (int q = 0; q < kPushGroup; ++q) {
+            rb[q] = re[q] = 0;
+            if (c[q] >= 0 && !((wv[q] >> (c[q] & 31)) & 1u)) {
+                cand |= 1u << q;
+                rb[q] = __ldg(a.row_ptr + c[q]);
+                re[q] = __ldg(a.row_ptr + c[q] + 1);
             }
         }
-        int rb = 0, re = 0;
-        if (claimed) {
-            a.dist[c] = step;
-            rb = __ldg(a.row_ptr + c);
-            re = __ldg(a.row_ptr + c + 1);
-            nf += 1;
-            mf += re - rb;
+        unsigned claimed = 0;
+#pragma unroll
+        for (int q = 0; q < kPushGroup; ++q) {
+            if ((cand >> q) & 1u) {
+                const uint32_t bit = 1u << (c[q] & 31);
+                const uint32_t old = atomicOr(&vis[c[q] >> 5], bit);
+                if (!(old & bit)) claimed |= 1u << q;
+            }
         }
-        warp_enqueue(claimed, rb, re, lane, qout, &out->qpack);
+#pragma unroll
+        for (int q = 0; q < kPushGroup; ++q) {
+            if ((claimed >> q) & 1u) {
+                a.dist[c[q]] = step;
+                nf += 1;
+                mf += re[q] - rb[q];
+            }
+        }
+        warp_enqueue_group(claimed, rb, re, lane, qout, &out->qpack);
     }
 }
 
@@ -317,6 +383,7 @@ __device__ __forceinline__ uint32_t bm_word(const uint32_t* vcur, int w) {
 template <bool kSmem>
 __device__ void pull_level(const SsspArgs& a, int step, const uint32_t* vcur, uint32_t* vnext,
                            long long& nf, long long& mf) {
+    constexpr int U = 2;  // bitmap words per warp per round
     const int lane = threadIdx.x & 31;
     const int gw = blockIdx.x * kWarps + (threadIdx.x >> 5);
     const int nw = gridDim.x * kWarps;
@@ -326,63 +393,91 @@ __device__ void pull_level(const SsspArgs& a, int step, const uint32_t* vcur, ui
         for (int i = threadIdx.x; i < (a.smem_words >> 2); i += kThreads) s_bitmap4[i] = __ldcg(src4 + i);
         __syncthreads();
     }
-    for (int w = gw; w < a.nwords; w += nw) {
-        const uint32_t cur = bm_word<kSmem>(vcur, w);
-        // candidates: not reached, and with at least one in-arc (excl also
-        // covers the padding bits past n).  excl is kept out of the visited
-        // set itself: a vertex without in-arcs may still have out-arcs, and
-        // it must not look reached to its out-neighbours.
-        const uint32_t skip = cur | __ldg(a.excl + w);
-        uint32_t newbits = 0;
-        if (skip != kFull) {
-            const int v = (w << 5) + lane;
-            const bool cand = !((skip >> lane) & 1u);
-            bool found = false;
-            int ib = 0, ie = 0, j = 0;
-            if (cand) {
-                ib = __ldg(a.in_ptr + v);
-                ie = __ldg(a.in_ptr + v + 1);
-                j = ib;
-                const int jl = min(ie, ib + a.pull_serial);
-                for (; j + 4 <= jl && !found; j += 4) {
-                    const int u0 = __ldg(a.in_idx + j), u1 = __ldg(a.in_idx + j + 1);
-                    const int u2 = __ldg(a.in_idx + j + 2), u3 = __ldg(a.in_idx + j + 3);
-                    const uint32_t h = ((bm_word<kSmem>(vcur, u0 >> 5) >> (u0 & 31)) |
-                                        (bm_word<kSmem>(vcur, u1 >> 5) >> (u1 & 31)) |
-                                        (bm_word<kSmem>(vcur, u2 >> 5) >> (u2 & 31)) |
-                                        (bm_word<kSmem>(vcur, u3 >> 5) >> (u3 & 31))) & 1u;
-                    found = h != 0;
-                }
-                for (; j < jl && !found; ++j) {
-                    const int u = __ldg(a.in_idx + j);
-                    found = (bm_word<kSmem>(vcur, u >> 5) >> (u & 31)) & 1u;
+    for (int w0 = gw; w0 < a.nwords; w0 += U * nw) {
+        uint32_t cur[U];
+        bool cand[U], found[U];
+        int ib[U], ie[U], j[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int w = w0 + u * nw;
+            cur[u] = kFull;
+            cand[u] = false;
+            found[u] = false;
+            ib[u] = ie[u] = j[u] = 0;
+            if (w < a.nwords) {
+                cur[u] = bm_word<kSmem>(vcur, w);
+                // candidates: not reached, and with at least one in-arc (excl
+                // also covers the padding bits past n).  excl is kept out of
+                // the visited set itself: a vertex without in-arcs may still
+                // have out-arcs, and it must not look reached to them.
+                const uint32_t skip = cur[u] | __ldg(a.excl + w);
+                cand[u] = !((skip >> lane) & 1u);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if (cand[u]) {
+                const int v = ((w0 + u * nw) << 5) + lane;
+                ib[u] = __ldg(a.in_ptr + v);
+                ie[u] = __ldg(a.in_ptr + v + 1);
+                j[u] = ib[u];
+            }
+        }
+        // own tests, 4 in-neighbours at a time, both words' loads in flight
+        bool more = true;
+        for (int r = 0; more; ++r) {
+            more = false;
+            int uu[U][4];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int jl = min(ie[u], ib[u] + a.pull_serial);
+#pragma unroll
+                for (int x = 0; x < 4; ++x) uu[u][x] = (cand[u] && !found[u] && j[u] + x < jl) ? __ldg(a.in_idx + j[u] + x) : -1;
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int jl = min(ie[u], ib[u] + a.pull_serial);
+                uint32_t h = 0;
+#pragma unroll
+                for (int x = 0; x < 4; ++x)
+                    if (uu[u][x] >= 0) h |= (bm_word<kSmem>(vcur, uu[u][x] >> 5) >> (uu[u][x] & 31)) & 1u;
+                if (cand[u] && !found[u] && j[u] < jl) {
+                    found[u] = h != 0;
+                    j[u] = min(j[u] + 4, jl);
+                    more |= !found[u] && j[u] < jl;
                 }
             }
-            unsigned rest = __ballot_sync(kFull, cand && !found && j < ie);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int w = w0 + u * nw;
+            if (w >= a.nwords) continue;  // warp-uniform
+            unsigned rest = __ballot_sync(kFull, cand[u] && !found[u] && j[u] < ie[u]);
             while (rest) {
                 const int L = __ffs(rest) - 1;
                 rest &= rest - 1;
-                const int jb = __shfl_sync(kFull, j, L);
-                const int je = __shfl_sync(kFull, ie, L);
+                const int jb = __shfl_sync(kFull, j[u], L);
+                const int je = __shfl_sync(kFull, ie[u], L);
                 bool hit = false;
                 for (int base = jb; base < je; base += 32) {
-                    bool h = false;
+                    bool hh = false;
                     if (base + lane < je) {
-                        const int u = __ldg(a.in_idx + base + lane);
-                        h = (bm_word<kSmem>(vcur, u >> 5) >> (u & 31)) & 1u;
+                        const int x = __ldg(a.in_idx + base + lane);
+                        hh = (bm_word<kSmem>(vcur, x >> 5) >> (x & 31)) & 1u;
                     }
-                    if (__any_sync(kFull, h)) { hit = true; break; }
+                    if (__any_sync(kFull, hh)) { hit = true; break; }
                 }
-                if (lane == L) found = hit;
+                if (lane == L) found[u] = hit;
             }
-            newbits = __ballot_sync(kFull, found);
-            if (found) {
+            const uint32_t newbits = __ballot_sync(kFull, found[u]);
+            if (found[u]) {
+                const int v = (w << 5) + lane;
                 a.dist[v] = step;
                 nf += 1;
-                mf += symmetric ? (ie - ib) : (__ldg(a.row_ptr + v + 1) - __ldg(a.row_ptr + v));
+                mf += symmetric ? (ie[u] - ib[u]) : (__ldg(a.row_ptr + v + 1) - __ldg(a.row_ptr + v));
             }
+            if (lane == 0) vnext[w] = cur[u] | newbits;
         }
-        if (lane == 0) vnext[w] = cur | newbits;
     }
 }
 
