@@ -272,26 +272,46 @@ __device__ void push_level(const SsspArgs& a, int step, uint32_t* vis, Queue qin
     const long long E = (long long)(pack & 0xffffffffull);
     const long long nw = (long long)gridDim.x * kWarps;
     const long long gw = (long long)blockIdx.x * kWarps + (threadIdx.x >> 5);
-    long long chunk = (E + nw - 1) / nw;
-    chunk = (chunk + 31) & ~31LL;
-    const long long a0 = gw * chunk;
-    if (E == 0 || a0 >= E) return;
-    const long long a1 = min(E, a0 + chunk);
-    // largest slot i with off[i] <= a0 (off[0] = 0, so one exists)
-    int lo = 0, hi = qn;
-    while (hi - lo > 32) {
-        const int stp = (hi - lo + 31) >> 5;
-        const int p = lo + lane * stp;
-        const int v = p < hi ? __ldcg(qin.off + p) : INT_MAX;
-        const unsigned b = __ballot_sync(kFull, (long long)v <= a0);
-        const int k = 31 - __clz(b);
-        lo += k * stp;
-        hi = min(hi, lo + stp);
-    }
-    int bstart = lo;
+    if (E == 0) return;
+    // Light levels (entries of at most 8 arcs on average, e.g. a lattice
+    // frontier): each warp takes whole entries by index, so its first entry
+    // is known without a search, and claims without a read-only pre-test.
+    // Heavy levels (hub rows): equal arc ranges found by a 32-ary search.
+    const bool light = E <= 8LL * qn;
+    long long a0, a1;
+    int bstart;
     int2 e;
     int eoff;
-    load_batch(qin, qn, bstart, lane, e, eoff);
+    if (light) {
+        const long long per = (qn + nw - 1) / nw;
+        const long long s0 = gw * per;
+        if (s0 >= qn) return;
+        const long long s1 = min((long long)qn, s0 + per);
+        bstart = (int)s0;
+        load_batch(qin, qn, bstart, lane, e, eoff);
+        const int end_off = s1 < qn ? __ldcg(qin.off + s1) : (int)E;
+        a0 = __shfl_sync(kFull, eoff, 0);
+        a1 = end_off;
+    } else {
+        long long chunk = (E + nw - 1) / nw;
+        chunk = (chunk + 31) & ~31LL;
+        a0 = gw * chunk;
+        if (a0 >= E) return;
+        a1 = min(E, a0 + chunk);
+        // largest slot i with off[i] <= a0 (off[0] = 0, so one exists)
+        int lo = 0, hi = qn;
+        while (hi - lo > 32) {
+            const int stp = (hi - lo + 31) >> 5;
+            const int p = lo + lane * stp;
+            const int v = p < hi ? __ldcg(qin.off + p) : INT_MAX;
+            const unsigned b = __ballot_sync(kFull, (long long)v <= a0);
+            const int k = 31 - __clz(b);
+            lo += k * stp;
+            hi = min(hi, lo + stp);
+        }
+        bstart = lo;
+        load_batch(qin, qn, bstart, lane, e, eoff);
+    }
     for (long long gb = a0; gb < a1; gb += 32 * kPushGroup) {
         int cidx[kPushGroup];
 #pragma unroll
@@ -328,7 +348,7 @@ __device__ void push_level(const SsspArgs& a, int step, uint32_t* vis, Queue qin
         for (int q = 0; q < kPushGroup; ++q) c[q] = cidx[q] >= 0 ? __ldg(a.col_idx + cidx[q]) : -1;
         uint32_t wv[kPushGroup];
 #pragma unroll
-        for (int q = 0; q < kPushGroup; ++q) wv[q] = c[q] >= 0 ? __ldcg(vis + (c[q] >> 5)) : kFull;
+        for (int q = 0; q < kPushGroup; ++q) wv[q] = (c[q] >= 0 && !light) ? __ldcg(vis + (c[q] >> 5)) : (c[q] >= 0 ? 0u : kFull);
         // targets that look unreached: claim them and fetch their rows together
         int rb[kPushGroup], re[kPushGroup];
         unsigned cand = 0;
