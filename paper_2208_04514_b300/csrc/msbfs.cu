@@ -89,8 +89,12 @@ __device__ __forceinline__ unsigned long long ms_ld_relaxed_u64(const unsigned l
 }
 
 // Same protocol as the single-source barrier: release-add on the launch's
-// arrival counter, acquire polls up to a running target, bounded spin.
-__device__ bool ms_barrier(MsCtl* ctl, unsigned* count, unsigned& target, long long spin_limit) {
+// arrival counter, acquire polls up to a running target, bounded spin.  With
+// `snap`, thread 0 copies nsnap words after the acquire into s_snap for the
+// whole CTA (one L2 request per CTA, not one per warp on a hot line).
+__device__ bool ms_barrier(MsCtl* ctl, unsigned* count, unsigned& target, long long spin_limit,
+                           const unsigned long long* snap = nullptr, int nsnap = 0,
+                           unsigned long long* s_snap = nullptr) {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -107,6 +111,8 @@ __device__ bool ms_barrier(MsCtl* ctl, unsigned* count, unsigned& target, long l
             }
             if ((++polls & 15u) == 0 && ms_ld_relaxed_s32(&ctl->status) != DEV_OK) { ok = 0; break; }
         }
+        if (ok)
+            for (int i = 0; i < nsnap; ++i) s_snap[i] = ms_ld_relaxed_u64(snap + i);
         s_ok = ok;
     }
     __syncthreads();
@@ -168,7 +174,11 @@ __global__ void __launch_bounds__(kMsThreads, 1) msbfs_kernel(MsArgs a) {
     __shared__ unsigned long long s_hvv[kMsHeavyMax][W], s_hacc[kMsHeavyMax][W];
 
     MsCtl* ctl = a.ctl;
-    if (ms_ld_relaxed_s32(&ctl->status) != DEV_OK) return;
+    __shared__ unsigned long long s_lanes[4];
+    __shared__ int s_status;
+    if (threadIdx.x == 0) s_status = ms_ld_relaxed_s32(&ctl->status);
+    __syncthreads();
+    if (s_status != DEV_OK) return;
     unsigned* bar = &ctl->bar[a.bar_parity].count;
     unsigned bar_target = 0;
     constexpr int L = 64 * W;
@@ -366,11 +376,11 @@ __global__ void __launch_bounds__(kMsThreads, 1) msbfs_kernel(MsArgs a) {
             }
             if (blockIdx.x == 0 && threadIdx.x >= 32 && threadIdx.x < 32 + W)
                 ctl->lanes_new[(t + 1) % 3][threadIdx.x - 32] = 0ull;
-            if (!ms_barrier(ctl, bar, bar_target, a.spin_limit)) return;
+            if (!ms_barrier(ctl, bar, bar_target, a.spin_limit, ctl->lanes_new[t % 3], W, s_lanes)) return;
             bool done = true;
 #pragma unroll
             for (int w = 0; w < W; ++w) {
-                fin[w] |= ~ms_ld_relaxed_u64(&ctl->lanes_new[t % 3][w]);
+                fin[w] |= ~s_lanes[w];
                 done &= fin[w] == ~0ull;
             }
             uint64_t* tmp = vcur;

@@ -97,11 +97,11 @@ struct SvGraph {
 struct alignas(128) SvCtl {
     BarCounter bar[2];
     int status;
-    int exit_flag;
-    int pad[30];
+    int pad[31];
     unsigned long long lanes_new[3][kSvMaxGraphs][4];
-    int admit_count[2];                   // entries of the batch for iteration (t & 1)
-    int pad2[30];
+    // published by CTA 0 for iteration t into pub[t & 1]: {admitted entries,
+    // exit flag, first entry of each graph (kSvMaxGraphs + 1 values)}
+    int pub[2][32];
     AdmitEntry admit[2][kSvMaxAdmit];     // sorted by (graph, src)
     long long seg_prefix[2][kSvMaxAdmit + 1];  // row-fill work items before each entry
 };
@@ -157,7 +157,10 @@ __device__ __forceinline__ AdmitEntry ld_entry(const AdmitEntry* p) {
     return e;
 }
 
-__device__ bool sv_barrier(SvCtl* ctl, unsigned* count, unsigned& target, long long spin_limit) {
+// With `snap`, thread 0 copies nsnap ints after the acquire into s_snap
+// for the whole CTA (one L2 request per CTA, not one per warp).
+__device__ bool sv_barrier(SvCtl* ctl, unsigned* count, unsigned& target, long long spin_limit,
+                           const int* snap = nullptr, int nsnap = 0, int* s_snap = nullptr) {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -174,6 +177,8 @@ __device__ bool sv_barrier(SvCtl* ctl, unsigned* count, unsigned& target, long l
             }
             if ((++polls & 15u) == 0 && sv_ld_relaxed_s32(&ctl->status) != DEV_OK) { ok = 0; break; }
         }
+        if (ok)
+            for (int i = 0; i < nsnap; ++i) s_snap[i] = sv_ld_relaxed_s32(snap + i);
         s_ok = ok;
     }
     __syncthreads();
@@ -207,7 +212,11 @@ __global__ void __launch_bounds__(kSvThreads, 1) serve_kernel(SvArgs a) {
 
     SvCtl* ctl = a.ctl;
     HostShared* hs = a.hs;
-    if (sv_ld_relaxed_s32(&ctl->status) != DEV_OK) return;
+    __shared__ int s_pub[32];  // this iteration's {entries, exit flag, first entry per graph}
+    __shared__ int s_status;
+    if (threadIdx.x == 0) s_status = sv_ld_relaxed_s32(&ctl->status);
+    __syncthreads();
+    if (s_status != DEV_OK) return;
     unsigned* bar = &ctl->bar[a.bar_parity].count;
     unsigned bar_target = 0;
     const int lane = threadIdx.x & 31;
@@ -233,9 +242,7 @@ __global__ void __launch_bounds__(kSvThreads, 1) serve_kernel(SvArgs a) {
             const unsigned seq = sv_ld_acquire_sys(&hs->batch_seq);
             s_take = seq != seen_seq ? (int)min(hs->count, (unsigned)kSvMaxAdmit) : -1;
             if (s_take >= 0) seen_seq = seq;
-            ctl->admit_count[0] = 0;
-            ctl->admit_count[1] = 0;
-            ctl->exit_flag = 0;
+            for (int i = 0; i < 32; ++i) ctl->pub[0][i] = ctl->pub[1][i] = 0;
         }
         __syncthreads();
         const int take = s_take;
@@ -256,18 +263,23 @@ __global__ void __launch_bounds__(kSvThreads, 1) serve_kernel(SvArgs a) {
                     G->lane_token[e.lane] = e.token;
                 }
                 ctl->seg_prefix[0][take] = acc;
-                ctl->admit_count[0] = take;
+                ctl->pub[0][0] = take;
+                int gi = 0;
+                for (int g = 0; g <= kSvMaxGraphs; ++g) {
+                    while (gi < take && ctl->admit[0][gi].graph < g) ++gi;
+                    ctl->pub[0][2 + g] = gi;
+                }
                 __threadfence_system();
                 *(volatile unsigned*)&hs->batch_ack = seen_seq;
             }
         }
         if (threadIdx.x < 3 * kSvMaxGraphs * 4) (&ctl->lanes_new[0][0][0])[threadIdx.x] = 0ull;
     }
-    if (!sv_barrier(ctl, bar, bar_target, a.spin_limit)) return;
+    if (!sv_barrier(ctl, bar, bar_target, a.spin_limit, ctl->pub[0], 2 + kSvMaxGraphs + 1, s_pub)) return;
 
     for (int t = 0;; ++t) {
         const int par = t & 1;
-        const int na = sv_ld_relaxed_s32(&ctl->admit_count[par]);
+        const int na = s_pub[0];
         const long long* seg = ctl->seg_prefix[par];
         // ---- (1) fill the rows of lanes admitted now: -1, and 0 at the source
         if (na > 0) {
@@ -296,10 +308,9 @@ __global__ void __launch_bounds__(kSvThreads, 1) serve_kernel(SvArgs a) {
             }
         }
         // ---- (2) one level for every graph with occupied or admitted lanes
-        int ai = 0;  // admitted entries are sorted by graph
         for (int g = 0; g < a.ngraphs; ++g) {
-            int a0 = ai;
-            while (ai < na && ld_entry(&ctl->admit[par][ai]).graph == g) ++ai;
+            const int a0 = s_pub[2 + g];  // admitted entries are sorted by graph
+            const int ai = s_pub[2 + g + 1];
             const int nag = ai - a0;
             unsigned long long adm[W];
             bool any = false;
@@ -500,7 +511,12 @@ __global__ void __launch_bounds__(kSvThreads, 1) serve_kernel(SvArgs a) {
                     G->lane_token[e.lane] = e.token;
                 }
                 ctl->seg_prefix[npar][take] = acc;
-                ctl->admit_count[npar] = take;
+                ctl->pub[npar][0] = take;
+                int gi = 0;
+                for (int g = 0; g <= kSvMaxGraphs; ++g) {
+                    while (gi < take && ctl->admit[npar][gi].graph < g) ++gi;
+                    ctl->pub[npar][2 + g] = gi;
+                }
                 if (take > 0) {
                     __threadfence_system();
                     *(volatile unsigned*)&hs->batch_ack = seen_seq;
@@ -510,11 +526,11 @@ __global__ void __launch_bounds__(kSvThreads, 1) serve_kernel(SvArgs a) {
                     for (int w = 0; w < W; ++w) busy |= occ[g][w] != 0ull;
                 const unsigned long long now = sv_globaltimer();
                 if (busy) last_busy = now;
-                ctl->exit_flag = (*(volatile unsigned*)&hs->stop != 0u) ||
-                                 (!busy && (long long)(now - last_busy) > a.idle_ns);
+                ctl->pub[npar][1] = (*(volatile unsigned*)&hs->stop != 0u) ||
+                                    (!busy && (long long)(now - last_busy) > a.idle_ns);
             }
         }
-        if (!sv_barrier(ctl, bar, bar_target, a.spin_limit)) return;
+        if (!sv_barrier(ctl, bar, bar_target, a.spin_limit, ctl->pub[par ^ 1], 2 + kSvMaxGraphs + 1, s_pub)) return;
         // ---- (4) lanes whose level reached nothing are done (thread 0 of every
         //      CTA computes the same masks; CTA 0 reports them to the host)
         if (threadIdx.x == 0) {
@@ -555,7 +571,7 @@ __global__ void __launch_bounds__(kSvThreads, 1) serve_kernel(SvArgs a) {
             }
         }
         __syncthreads();
-        if (sv_ld_relaxed_s32(&ctl->exit_flag)) break;
+        if (s_pub[1]) break;
     }
     if (gtid == 0) ctl->bar[a.bar_parity ^ 1].count = 0;
 }

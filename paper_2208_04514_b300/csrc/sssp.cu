@@ -133,8 +133,12 @@ __device__ __forceinline__ void red_release_add(unsigned* p, unsigned v) {
 // arrival counter with a release reduction and spins (acquire loads) until
 // the counter reaches its own running target, gridDim.x more per barrier.
 // Returns false (in every thread of the CTA) when the wait ran out or
-// another CTA reported a failure.  `target` lives in thread 0.
-__device__ bool grid_barrier(Ctl* ctl, unsigned* count, unsigned& target, long long spin_limit) {
+// another CTA reported a failure.  `target` lives in thread 0.  With `snap`,
+// thread 0 also reads that counter slot after the acquire and leaves
+// {qpack, nf, mf} in s_snap for the whole CTA: one L2 request per CTA
+// instead of one per warp on a single hot line.
+__device__ bool grid_barrier(Ctl* ctl, unsigned* count, unsigned& target, long long spin_limit,
+                             const CtrSlot* snap = nullptr, unsigned long long* s_snap = nullptr) {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -150,6 +154,11 @@ __device__ bool grid_barrier(Ctl* ctl, unsigned* count, unsigned& target, long l
                 break;
             }
             if ((++polls & 15u) == 0 && ld_relaxed_s32(&ctl->status) != DEV_OK) { ok = 0; break; }
+        }
+        if (ok && snap) {
+            s_snap[0] = ld_relaxed_u64(&snap->qpack);
+            s_snap[1] = ld_relaxed_u64(&snap->nf);
+            s_snap[2] = ld_relaxed_u64(&snap->mf);
         }
         s_ok = ok;
     }
@@ -529,7 +538,11 @@ __device__ void bitmap_to_queue(const SsspArgs& a, const uint32_t* vnow, const u
 
 __global__ void __launch_bounds__(kThreads, 1) sssp_kernel(SsspArgs a) {
     Ctl* ctl = a.ctl;
-    if (ld_relaxed_s32(&ctl->status) != DEV_OK) return;  // an earlier call failed: stay idle
+    __shared__ unsigned long long s_snap[3];  // {qpack, nf, mf} of the level just finished
+    __shared__ int s_status;
+    if (threadIdx.x == 0) s_status = ld_relaxed_s32(&ctl->status);
+    __syncthreads();
+    if (s_status != DEV_OK) return;  // an earlier call failed: stay idle
     const int lane = threadIdx.x & 31;
     const bool tracer = blockIdx.x == 0 && threadIdx.x == 0;
     int tslot = 0;
@@ -566,7 +579,7 @@ __global__ void __launch_bounds__(kThreads, 1) sssp_kernel(SsspArgs a) {
         }
     }
     // dist[src] = 0 after the fill; the barrier orders it after every -1 store
-    if (!grid_barrier(ctl, bar, bar_target, a.spin_limit)) return;
+    if (!grid_barrier(ctl, bar, bar_target, a.spin_limit, &ctl->ctr[0], s_snap)) return;
     if (gtid == 0) {
         a.dist[src] = 0;
         ctl->bar[a.bar_parity ^ 1].count = 0;  // the next launch's counter
@@ -586,8 +599,9 @@ __global__ void __launch_bounds__(kThreads, 1) sssp_kernel(SsspArgs a) {
         // the frontier found at step s lives in queue (s & 1)
         const Queue qcur = (step & 1) ? Queue{a.q1, a.q1off} : Queue{a.q0, a.q0off};
         const Queue qnext = (step & 1) ? Queue{a.q0, a.q0off} : Queue{a.q1, a.q1off};
-        const long long nf_cur = (long long)ld_relaxed_u64(&cur->nf);
-        const long long mf_cur = (long long)ld_relaxed_u64(&cur->mf);
+        unsigned long long qpack = s_snap[0];
+        const long long nf_cur = (long long)s_snap[1];
+        const long long mf_cur = (long long)s_snap[2];
         if (nf_cur == 0 || step >= a.n) break;
         reached += nf_cur;
         edges += mf_cur;
@@ -604,8 +618,9 @@ __global__ void __launch_bounds__(kThreads, 1) sssp_kernel(SsspArgs a) {
         if (!pull && last_pull) {
             // the frontier exists only as a bitmap difference: turn it into a queue
             bitmap_to_queue(a, vcur, vnext, qcur, &cur->qpack);
-            if (!grid_barrier(ctl, bar, bar_target, a.spin_limit)) return;
-            if (tracer) trace_rec(a, tslot, 4, step, (long long)(ld_relaxed_u64(&cur->qpack) >> 32));
+            if (!grid_barrier(ctl, bar, bar_target, a.spin_limit, cur, s_snap)) return;
+            qpack = s_snap[0];
+            if (tracer) trace_rec(a, tslot, 4, step, (long long)(qpack >> 32));
         }
         CtrSlot* out = &ctl->ctr[(step + 1) % 3];
         long long nf = 0, mf = 0;
@@ -614,12 +629,12 @@ __global__ void __launch_bounds__(kThreads, 1) sssp_kernel(SsspArgs a) {
             else pull_level<false>(a, step + 1, vcur, vnext, nf, mf);
             ++pulls;
         } else {
-            push_level(a, step + 1, vcur, qcur, ld_relaxed_u64(&cur->qpack), qnext, out, nf, mf);
+            push_level(a, step + 1, vcur, qcur, qpack, qnext, out, nf, mf);
             ++pushes;
         }
         flush_counts(nf, mf, out);
-        if (!grid_barrier(ctl, bar, bar_target, a.spin_limit)) return;
-        if (tracer) trace_rec(a, tslot, pull ? 3 : 2, step + 1, (long long)ld_relaxed_u64(&out->nf));
+        if (!grid_barrier(ctl, bar, bar_target, a.spin_limit, out, s_snap)) return;
+        if (tracer) trace_rec(a, tslot, pull ? 3 : 2, step + 1, (long long)s_snap[1]);
         if (pull) {
             uint32_t* t = vcur;
             vcur = vnext;
