@@ -238,9 +238,11 @@ DAWN_API int dawn_msbfs(dawn_graph_t g, const int32_t* sources, int32_t k, void*
                         int dist_bytes, int layout, int32_t* ecc, int64_t* dsum, void* stream);
 
 typedef struct {
-    int32_t lanes;         /* sources per pass: 64, 128 or 256; 0 = autotuned */
-    int32_t reserved;
+    int32_t lanes;         /* sources per pass: 64, 128 or 256; 0 = tuned, else by k */
+    int32_t trace_cap;     /* records that fit in trace */
     int64_t spin_limit;    /* as in dawn_sssp_opts */
+    int64_t* trace;        /* device memory or NULL: one record of 4 int64 per level,
+                              {pass, level, vertices reached in the level, globaltimer ns} */
 } dawn_msbfs_opts;
 
 /* dawn_msbfs with the reached counts and options (reached, opts may be NULL). */

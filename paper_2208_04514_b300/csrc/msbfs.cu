@@ -68,6 +68,8 @@ struct MsArgs {
     int32_t dist_bytes;
     int32_t per_pass;                     // 1: one block of 64*W rows reused by every pass (no caller block)
     int32_t bar_parity;
+    long long* trace;                     // device, may be null: 4 int64 per level
+    int32_t trace_cap;
 };
 
 __device__ __forceinline__ unsigned ms_ld_acquire(const unsigned* p) {
@@ -181,6 +183,7 @@ __global__ void __launch_bounds__(kMsThreads, 1) msbfs_kernel(MsArgs a) {
     if (s_status != DEV_OK) return;
     unsigned* bar = &ctl->bar[a.bar_parity].count;
     unsigned bar_target = 0;
+    int tslot = 0;
     constexpr int L = 64 * W;
     const int lane = threadIdx.x & 31;
     const int gw = blockIdx.x * kMsWarps + (threadIdx.x >> 5);
@@ -377,6 +380,17 @@ __global__ void __launch_bounds__(kMsThreads, 1) msbfs_kernel(MsArgs a) {
             if (blockIdx.x == 0 && threadIdx.x >= 32 && threadIdx.x < 32 + W)
                 ctl->lanes_new[(t + 1) % 3][threadIdx.x - 32] = 0ull;
             if (!ms_barrier(ctl, bar, bar_target, a.spin_limit, ctl->lanes_new[t % 3], W, s_lanes)) return;
+            if (a.trace && blockIdx.x == 0 && threadIdx.x == 0 && tslot < a.trace_cap) {
+                unsigned long long tnow;
+                asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(tnow));
+                long long* r = a.trace + 4 * (long long)tslot;
+                r[0] = b;
+                r[1] = t;
+                r[2] = 0;
+                for (int w = 0; w < W; ++w) r[2] += __popcll(s_lanes[w]);
+                r[3] = (long long)tnow;
+            }
+            ++tslot;
             bool done = true;
 #pragma unroll
             for (int w = 0; w < W; ++w) {
@@ -515,6 +529,12 @@ int msbfs_run(dawn_graph* g, const int32_t* sources, int32_t k, void* dist_block
     a.k = k;
     a.dist_bytes = dist_bytes;
     a.bar_parity = (int)(g->ms_launches & 1u);
+    a.trace = opts ? reinterpret_cast<long long*>(opts->trace) : nullptr;
+    a.trace_cap = (opts && opts->trace) ? opts->trace_cap : 0;
+    if (a.trace && (a.trace_cap < 0 || !is_device_ptr(a.trace))) {
+        cudaFreeAsync(tmp, st);
+        return fail(DAWN_E_INVALID, "trace must be device memory with trace_cap >= 0");
+    }
     a.out = d_out;
     if (!dist_block) {
         // no caller block: every pass writes its rows into one device block of `lanes` rows

@@ -102,8 +102,9 @@ DAWN_API int dawn_autotune(dawn_graph_t g, const int32_t* sample, int32_t k, daw
     for (int lanes : {256, 128, 64}) {
         dawn_msbfs_opts mo;
         mo.lanes = lanes;
-        mo.reserved = 0;
+        mo.trace_cap = 0;
         mo.spin_limit = 0;
+        mo.trace = nullptr;
         const auto t0 = std::chrono::steady_clock::now();
         rc = dawn_msbfs_ex(g, batch.data(), (int32_t)batch.size(), nullptr, 2, DAWN_SOURCE_MAJOR, nullptr, nullptr,
                            nullptr, &mo, stream);

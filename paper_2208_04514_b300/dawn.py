@@ -73,7 +73,8 @@ class dawn_tuning(ctypes.Structure):
 
 
 class dawn_msbfs_opts(ctypes.Structure):
-    _fields_ = [("lanes", ctypes.c_int32), ("reserved", ctypes.c_int32), ("spin_limit", ctypes.c_int64)]
+    _fields_ = [("lanes", ctypes.c_int32), ("trace_cap", ctypes.c_int32), ("spin_limit", ctypes.c_int64),
+                ("trace", ctypes.c_void_p)]
 
 
 _lib = None
