@@ -43,7 +43,9 @@ struct alignas(128) MsCtl {
     BarCounter bar[2];
     int status;
     int pad[31];
-    unsigned long long lanes_new[3][4];  // per level (t % 3): lanes that reached a vertex
+    // per level (t % 3): lanes that reached a vertex (words 0..3), vertices
+    // that needed a scan (4) and of those, vertices covered afterwards (5)
+    unsigned long long lanes_new[3][6];
 };
 
 struct MsArgs {
@@ -176,7 +178,9 @@ __global__ void __launch_bounds__(kMsThreads, 1) msbfs_kernel(MsArgs a) {
     __shared__ unsigned long long s_hvv[kMsHeavyMax][W], s_hacc[kMsHeavyMax][W];
 
     MsCtl* ctl = a.ctl;
-    __shared__ unsigned long long s_lanes[4];
+    __shared__ unsigned long long s_lanes[6];
+    __shared__ unsigned long long s_acc[kMsWarps][32][W];  // dense levels: per-vertex OR accumulators
+    __shared__ int s_need, s_cover;
     __shared__ int s_status;
     if (threadIdx.x == 0) s_status = ms_ld_relaxed_s32(&ctl->status);
     __syncthreads();
@@ -200,7 +204,7 @@ __global__ void __launch_bounds__(kMsThreads, 1) msbfs_kernel(MsArgs a) {
         s_dsum[i] = 0;
     }
     if (threadIdx.x < 4) s_newmask[threadIdx.x] = 0;
-    if (threadIdx.x == 0) s_hcount = 0;
+    if (threadIdx.x == 0) { s_hcount = 0; s_need = 0; s_cover = 0; }
 
     for (int b = 0; b < nbatches; ++b) {
         const int s0 = b * L;
@@ -210,7 +214,7 @@ __global__ void __launch_bounds__(kMsThreads, 1) msbfs_kernel(MsArgs a) {
         // ---- batch init: clear visited words and this batch's distances
         for (long long i = gtid; i < (long long)n * W; i += gthreads) vcur[i] = 0ull;
         fill_batch(a, s0, kb);
-        if (blockIdx.x == 0 && threadIdx.x < 12) (&ctl->lanes_new[0][0])[threadIdx.x] = 0ull;
+        if (blockIdx.x == 0 && threadIdx.x < 18) (&ctl->lanes_new[0][0])[threadIdx.x] = 0ull;
         if (!ms_barrier(ctl, bar, bar_target, a.spin_limit)) return;
         // ---- seeds: V[src_s] gets bit s, dist[s][src_s] = 0
         if (gtid < kb) {
@@ -228,6 +232,7 @@ __global__ void __launch_bounds__(kMsThreads, 1) msbfs_kernel(MsArgs a) {
             const int lo = w * 64;
             fin[w] = kb >= lo + 64 ? 0ull : (kb <= lo ? ~0ull : ~0ull << (kb - lo));
         }
+        bool dense = true;  // the first level covers almost nothing: arc-parallel
         for (int t = 1;; ++t) {
             if (a.dist_bytes == 2 && t > 32767) {
                 if (gtid == 0) atomicCAS(&ctl->status, DEV_OK, DEV_OVERFLOW);
@@ -246,65 +251,149 @@ __global__ void __launch_bounds__(kMsThreads, 1) msbfs_kernel(MsArgs a) {
                     need |= (vv[w] | fin[w]) != ~0ull;
                 }
                 if (valid && need && ((__ldg(a.excl + (v >> 5)) >> (v & 31)) & 1u)) need = false;
-                int j = 0, ie = 0;
-                if (need) {
-                    const int ib = __ldg(a.in_ptr + v);
-                    ie = __ldg(a.in_ptr + v + 1);
-                    j = ib;
-                    const int jl = min(ie, ib + kMsSerial);
-                    for (; j < jl; ++j) {
-                        const int u = __ldg(a.in_idx + j);
-                        bool all = true;
-#pragma unroll
-                        for (int w = 0; w < W; ++w) {
-                            acc[w] |= __ldcg(vcur + (long long)u * W + w);
-                            all &= (acc[w] | vv[w] | fin[w]) == ~0ull;
-                        }
-                        if (all) { j = ie; break; }
-                    }
-                }
                 bool deferred = false;
-                if (need && ie - j > kMsHeavy) {
-                    const int slot = atomicAdd(&s_hcount, 1);
-                    if (slot < kMsHeavyMax) {
-                        deferred = true;
-                        s_hv[slot] = v;
-                        s_hj[slot] = j;
-                        s_hie[slot] = ie;
+                if (dense) {
+                    // arc-parallel: the warp walks the concatenated in-lists of its
+                    // 32 vertices, 32 arcs per round, with a segmented OR scan
+                    // across the lanes of each round (no early exit)
+                    const int wib = threadIdx.x >> 5;
+                    int ib = 0, ie = 0;
+                    if (need) {
+                        ib = __ldg(a.in_ptr + v);
+                        ie = __ldg(a.in_ptr + v + 1);
+                    }
+                    if (need && ie - ib > kMsHeavy) {
+                        const int slot = atomicAdd(&s_hcount, 1);
+                        if (slot < kMsHeavyMax) {
+                            deferred = true;
+                            s_hv[slot] = v;
+                            s_hj[slot] = ib;
+                            s_hie[slot] = ie;
 #pragma unroll
+                            for (int w = 0; w < W; ++w) {
+                                s_hvv[slot][w] = vv[w];
+                                s_hacc[slot][w] = 0ull;
+                            }
+                        }
+                    }
+                    const int deg = (need && !deferred) ? ie - ib : 0;
+                    int incl = deg;
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const int y = __shfl_up_sync(kFull, incl, o);
+                        if (lane >= o) incl += y;
+                    }
+                    const int total = __shfl_sync(kFull, incl, 31);
+                    const int ex = incl - deg;
+#pragma unroll
+                    for (int w = 0; w < W; ++w) s_acc[wib][lane][w] = 0ull;
+                    __syncwarp();
+                    for (int base = 0; base < total; base += 32) {
+                        const int tt = base + lane;
+                        int o = 0;
+#pragma unroll
+                        for (int bb = 16; bb > 0; bb >>= 1) {
+                            const int cand = o + bb;
+                            const int pv = __shfl_sync(kFull, ex, cand);
+                            if (pv <= tt) o = cand;
+                        }
+                        const int oib = __shfl_sync(kFull, ib, o);
+                        const int oex = __shfl_sync(kFull, ex, o);
+                        const bool act = tt < total;
+                        if (!act) o = 32 + lane;  // lanes past the end form their own segments
+                        unsigned long long x[W];
+                        const int u = act ? __ldg(a.in_idx + oib + (tt - oex)) : 0;
+#pragma unroll
+                        for (int w = 0; w < W; ++w) x[w] = act ? __ldcg(vcur + (long long)u * W + w) : 0ull;
+#pragma unroll
+                        for (int d = 1; d < 32; d <<= 1) {
+                            const int o2 = __shfl_up_sync(kFull, o, d);
+#pragma unroll
+                            for (int w = 0; w < W; ++w) {
+                                const unsigned long long y = __shfl_up_sync(kFull, x[w], d);
+                                if (lane >= d && o2 == o) x[w] |= y;
+                            }
+                        }
+                        const int onext = __shfl_down_sync(kFull, o, 1);
+                        if (act && (lane == 31 || onext != o)) {
+#pragma unroll
+                            for (int w = 0; w < W; ++w) s_acc[wib][o][w] |= x[w];
+                        }
+                    }
+                    __syncwarp();
+#pragma unroll
+                    for (int w = 0; w < W; ++w) acc[w] = s_acc[wib][lane][w];
+                } else {
+                    int j = 0, ie = 0;
+                    if (need) {
+                        const int ib = __ldg(a.in_ptr + v);
+                        ie = __ldg(a.in_ptr + v + 1);
+                        j = ib;
+                        const int jl = min(ie, ib + kMsSerial);
+                        for (; j < jl; ++j) {
+                            const int u = __ldg(a.in_idx + j);
+                            bool all = true;
+    #pragma unroll
+                            for (int w = 0; w < W; ++w) {
+                                acc[w] |= __ldcg(vcur + (long long)u * W + w);
+                                all &= (acc[w] | vv[w] | fin[w]) == ~0ull;
+                            }
+                            if (all) { j = ie; break; }
+                        }
+                    }
+                    if (need && ie - j > kMsHeavy) {
+                        const int slot = atomicAdd(&s_hcount, 1);
+                        if (slot < kMsHeavyMax) {
+                            deferred = true;
+                            s_hv[slot] = v;
+                            s_hj[slot] = j;
+                            s_hie[slot] = ie;
+    #pragma unroll
+                            for (int w = 0; w < W; ++w) {
+                                s_hvv[slot][w] = vv[w];
+                                s_hacc[slot][w] = acc[w];
+                            }
+                        }
+                    }
+                    unsigned rest = __ballot_sync(kFull, need && !deferred && j < ie);
+                    while (rest) {
+                        const int src_lane = __ffs(rest) - 1;
+                        rest &= rest - 1;
+                        const int jb = __shfl_sync(kFull, j, src_lane);
+                        const int je = __shfl_sync(kFull, ie, src_lane);
+                        unsigned long long accL[W], vvL[W];
+    #pragma unroll
                         for (int w = 0; w < W; ++w) {
-                            s_hvv[slot][w] = vv[w];
-                            s_hacc[slot][w] = acc[w];
+                            accL[w] = __shfl_sync(kFull, acc[w], src_lane);
+                            vvL[w] = __shfl_sync(kFull, vv[w], src_lane);
+                        }
+                        for (int base = jb; base < je; base += 32) {
+                            const int jj = base + lane;
+                            const int u = jj < je ? __ldg(a.in_idx + jj) : -1;
+                            bool all = true;
+    #pragma unroll
+                            for (int w = 0; w < W; ++w) {
+                                const unsigned long long x = u >= 0 ? __ldcg(vcur + (long long)u * W + w) : 0ull;
+                                accL[w] |= warp_or64(x);
+                                all &= (accL[w] | vvL[w] | fin[w]) == ~0ull;
+                            }
+                            if (all) break;
+                        }
+                        if (lane == src_lane) {
+    #pragma unroll
+                            for (int w = 0; w < W; ++w) acc[w] = accL[w];
                         }
                     }
                 }
-                unsigned rest = __ballot_sync(kFull, need && !deferred && j < ie);
-                while (rest) {
-                    const int src_lane = __ffs(rest) - 1;
-                    rest &= rest - 1;
-                    const int jb = __shfl_sync(kFull, j, src_lane);
-                    const int je = __shfl_sync(kFull, ie, src_lane);
-                    unsigned long long accL[W], vvL[W];
+                {
+                    bool cov = true;
 #pragma unroll
-                    for (int w = 0; w < W; ++w) {
-                        accL[w] = __shfl_sync(kFull, acc[w], src_lane);
-                        vvL[w] = __shfl_sync(kFull, vv[w], src_lane);
-                    }
-                    for (int base = jb; base < je; base += 32) {
-                        const int jj = base + lane;
-                        const int u = jj < je ? __ldg(a.in_idx + jj) : -1;
-                        bool all = true;
-#pragma unroll
-                        for (int w = 0; w < W; ++w) {
-                            const unsigned long long x = u >= 0 ? __ldcg(vcur + (long long)u * W + w) : 0ull;
-                            accL[w] |= warp_or64(x);
-                            all &= (accL[w] | vvL[w] | fin[w]) == ~0ull;
-                        }
-                        if (all) break;
-                    }
-                    if (lane == src_lane) {
-#pragma unroll
-                        for (int w = 0; w < W; ++w) acc[w] = accL[w];
+                    for (int w = 0; w < W; ++w) cov &= (acc[w] | vv[w] | fin[w]) == ~0ull;
+                    const unsigned mn = __ballot_sync(kFull, need && !deferred);
+                    const unsigned mc = __ballot_sync(kFull, need && !deferred && cov);
+                    if (lane == 0 && mn) {
+                        atomicAdd(&s_need, __popc(mn));
+                        if (mc) atomicAdd(&s_cover, __popc(mc));
                     }
                 }
                 // new bits, next visited words, distances, counts
@@ -377,9 +466,17 @@ __global__ void __launch_bounds__(kMsThreads, 1) msbfs_kernel(MsArgs a) {
                 atomicOr(&ctl->lanes_new[t % 3][threadIdx.x], s_newmask[threadIdx.x]);
                 s_newmask[threadIdx.x] = 0;
             }
-            if (blockIdx.x == 0 && threadIdx.x >= 32 && threadIdx.x < 32 + W)
+            if (threadIdx.x == 32) {
+                if (s_need) atomicAdd(&ctl->lanes_new[t % 3][4], (unsigned long long)s_need);
+                if (s_cover) atomicAdd(&ctl->lanes_new[t % 3][5], (unsigned long long)s_cover);
+                s_need = 0;
+                s_cover = 0;
+            }
+            if (blockIdx.x == 0 && threadIdx.x >= 32 && threadIdx.x < 38)
                 ctl->lanes_new[(t + 1) % 3][threadIdx.x - 32] = 0ull;
-            if (!ms_barrier(ctl, bar, bar_target, a.spin_limit, ctl->lanes_new[t % 3], W, s_lanes)) return;
+            if (!ms_barrier(ctl, bar, bar_target, a.spin_limit, ctl->lanes_new[t % 3], 6, s_lanes)) return;
+            // next level: arc-parallel while most scanned vertices stay uncovered
+            dense = 2 * s_lanes[5] < s_lanes[4];
             if (a.trace && blockIdx.x == 0 && threadIdx.x == 0 && tslot < a.trace_cap) {
                 unsigned long long tnow;
                 asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(tnow));
