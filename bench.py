@@ -257,7 +257,7 @@ def bench_lattice(dawn, torch, flush, nsrc=16):
             "l2": "flushed between sources"}
 
 
-def bench_batched(dawn, torch, flush, plain_sample=4096):
+def bench_batched(dawn, torch, flush, plain_sample=4096, k=0, lanes_list=(64, 128, 256)):
     """RMAT scale 16 (seed 4), all 65,536 vertices as sources, int16 distance
     block of each pass kept on the device and reduced to eccentricity and
     distance sum: sources/s per lane width, against the plain path (one
@@ -267,18 +267,19 @@ def bench_batched(dawn, torch, flush, plain_sample=4096):
     n = g.n
     stream = torch.cuda.current_stream()
     h = dawn.dawn_graph_upload(g.row_ptr, g.col_idx, flags=dawn.DAWN_SYMMETRIC, stream=stream)
-    srcs = torch.arange(n, dtype=torch.int32, device="cuda")
-    ecc = torch.zeros(n, dtype=torch.int32, device="cuda")
-    dsum = torch.zeros(n, dtype=torch.int64, device="cuda")
-    out = {"workload": "rmat16_all_sources", "n": n, "m": g.m, "k": n, "lanes": {}}
-    for lanes in (64, 128, 256):
-        dawn.dawn_msbfs_ex(h, srcs, n, None, 2, 0, ecc, dsum, None, {"lanes": lanes})  # warm-up
+    k = k or n
+    srcs = torch.arange(k, dtype=torch.int32, device="cuda")
+    ecc = torch.zeros(k, dtype=torch.int32, device="cuda")
+    dsum = torch.zeros(k, dtype=torch.int64, device="cuda")
+    out = {"workload": "rmat16_all_sources" if k == n else f"rmat16_{k}_sources", "n": n, "m": g.m, "k": k, "lanes": {}}
+    for lanes in lanes_list:
+        dawn.dawn_msbfs_ex(h, srcs, k, None, 2, 0, ecc, dsum, None, {"lanes": lanes})  # warm-up
         _flush(flush, lanes)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        dawn.dawn_msbfs_ex(h, srcs, n, None, 2, 0, ecc, dsum, None, {"lanes": lanes})
+        dawn.dawn_msbfs_ex(h, srcs, k, None, 2, 0, ecc, dsum, None, {"lanes": lanes})
         t = time.perf_counter() - t0
-        out["lanes"][str(lanes)] = {"sources_per_s": n / t, "ms": 1e3 * t}
+        out["lanes"][str(lanes)] = {"sources_per_s": k / t, "ms": 1e3 * t}
     best = max(out["lanes"].values(), key=lambda x: x["sources_per_s"])
     # plain path: one single-source launch per source
     dist = torch.empty(n, dtype=torch.int32, device="cuda")
@@ -519,6 +520,22 @@ def run_gpu(args):
     return 0
 
 
+def run_one(args):
+    """One secondary workload alone (for profiling): prints its figures."""
+    import torch
+    from paper_2208_04514_b300 import dawn
+    torch.cuda.set_device(0)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.int32, device="cuda")
+    if args.workload == "lattice":
+        out = bench_lattice(dawn, torch, flush)
+    elif args.workload == "batched":
+        out = bench_batched(dawn, torch, flush, k=args.batched_k, lanes_list=(args.batched_lanes,) if args.batched_lanes else (64, 128, 256))
+    else:
+        out = bench_serving(dawn, torch, nreq=args.serve_requests)
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -533,6 +550,10 @@ def main():
                     help="use only the first N of the 64 sources (small profiling runs; not a bench value)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end host-buffer pass")
     ap.add_argument("--serve-requests", type=int, default=48, help="requests per arrival rate in the serving mix")
+    ap.add_argument("--workload", choices=["all", "lattice", "batched", "serving"], default="all",
+                    help="run one secondary workload alone and print its figures (profiling runs; not a bench line)")
+    ap.add_argument("--batched-k", type=int, default=0, help="with --workload batched: sources (0 = all)")
+    ap.add_argument("--batched-lanes", type=int, default=0, help="with --workload batched: one lane width")
     ap.add_argument("--no-secondary", action="store_true",
                     help="skip the lattice, batched and serving workloads reported beside the headline")
     args = ap.parse_args()
@@ -540,6 +561,8 @@ def main():
         ap.error("at least 3 warm-up steps")
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload != "all":
+        return run_one(args)
     return run_gpu(args)
 
 
