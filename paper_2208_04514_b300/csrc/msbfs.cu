@@ -35,8 +35,8 @@ constexpr int kMsSerial = 8;  // in-neighbours a lane tests before the warp take
 // In-lists longer than this (after the lane's own tests) are deferred to the
 // end of the level and scanned by the whole CTA: a hub's row is split over
 // 1024 threads instead of one warp walking it 32 arcs at a time.
-constexpr int kMsHeavy = 512;
-constexpr int kMsHeavyMax = 32;  // deferred vertices per CTA per level
+constexpr int kMsHeavy = 256;
+constexpr int kMsHeavyMax = 64;  // deferred vertices per CTA per level
 constexpr unsigned kFull = 0xffffffffu;
 
 struct alignas(128) MsCtl {
@@ -190,8 +190,6 @@ __global__ void __launch_bounds__(kMsThreads, 1) msbfs_kernel(MsArgs a) {
     int tslot = 0;
     constexpr int L = 64 * W;
     const int lane = threadIdx.x & 31;
-    const int gw = blockIdx.x * kMsWarps + (threadIdx.x >> 5);
-    const int nw = gridDim.x * kMsWarps;
     const long long gtid = (long long)blockIdx.x * kMsThreads + threadIdx.x;
     const long long gthreads = (long long)gridDim.x * kMsThreads;
     const int n = a.n;
@@ -205,6 +203,27 @@ __global__ void __launch_bounds__(kMsThreads, 1) msbfs_kernel(MsArgs a) {
     }
     if (threadIdx.x < 4) s_newmask[threadIdx.x] = 0;
     if (threadIdx.x == 0) { s_hcount = 0; s_need = 0; s_cover = 0; }
+
+    // This CTA's vertices: a range of whole 32-vertex groups holding about
+    // 1/gridDim of the in-arcs (the CSC row pointer is the arc prefix), found
+    // once per launch; warps take its groups one at a time from a shared
+    // counter, so a warp that drew heavy rows does not hold up the others.
+    __shared__ int s_range[2];
+    __shared__ int s_next;
+    if (threadIdx.x < 2) {
+        const long long m_in = __ldg(a.in_ptr + n);
+        const long long target = m_in * (blockIdx.x + threadIdx.x) / gridDim.x;
+        int lo = 0, hi = n;  // first vertex whose row starts at or after target
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if ((long long)__ldg(a.in_ptr + mid) < target) lo = mid + 1; else hi = mid;
+        }
+        if (blockIdx.x + threadIdx.x == gridDim.x) lo = n;
+        s_range[threadIdx.x] = ((lo + 31) >> 5) << 5;
+    }
+    __syncthreads();
+    const int cv0 = min(s_range[0], n), cv1 = min(s_range[1], ((n + 31) >> 5) << 5);
+    if (threadIdx.x == 0) s_next = cv0;
 
     for (int b = 0; b < nbatches; ++b) {
         const int s0 = b * L;
@@ -239,7 +258,11 @@ __global__ void __launch_bounds__(kMsThreads, 1) msbfs_kernel(MsArgs a) {
                 return;
             }
             // ---- one level: lane = vertex, 32 consecutive vertices per warp
-            for (int vb = gw << 5; vb < n; vb += nw << 5) {
+            while (true) {
+                int vb = 0;
+                if (lane == 0) vb = atomicAdd(&s_next, 32);
+                vb = __shfl_sync(kFull, vb, 0);
+                if (vb >= cv1) break;
                 const int v = vb + lane;
                 const bool valid = v < n;
                 unsigned long long vv[W], acc[W];
@@ -415,6 +438,7 @@ __global__ void __launch_bounds__(kMsThreads, 1) msbfs_kernel(MsArgs a) {
                 }
             }
             __syncthreads();
+            if (threadIdx.x == 0) s_next = cv0;  // every warp has left the group loop
             // deferred long in-lists: the whole CTA scans each one
             const int nh = min(s_hcount, kMsHeavyMax);
             for (int h = 0; h < nh; ++h) {
