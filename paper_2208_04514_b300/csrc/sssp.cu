@@ -38,6 +38,12 @@
 namespace dawn {
 namespace {
 
+#ifndef DAWN_SSSP_MIN_CTAS
+#define DAWN_SSSP_MIN_CTAS 1  // CTAs per SM the register budget is sized for
+#endif
+#ifndef DAWN_SSSP_SMEM_BITMAP_MAX
+#define DAWN_SSSP_SMEM_BITMAP_MAX (200 * 1024)
+#endif
 constexpr int kThreads = 1024;
 constexpr int kWarps = kThreads / 32;
 constexpr unsigned kFull = 0xffffffffu;
@@ -536,7 +542,7 @@ __device__ void bitmap_to_queue(const SsspArgs& a, const uint32_t* vnow, const u
     }
 }
 
-__global__ void __launch_bounds__(kThreads, 1) sssp_kernel(SsspArgs a) {
+__global__ void __launch_bounds__(kThreads, DAWN_SSSP_MIN_CTAS) sssp_kernel(SsspArgs a) {
     Ctl* ctl = a.ctl;
     __shared__ unsigned long long s_snap[3];  // {qpack, nf, mf} of the level just finished
     __shared__ int s_status;
@@ -658,7 +664,7 @@ __global__ void __launch_bounds__(kThreads, 1) sssp_kernel(SsspArgs a) {
 }  // namespace
 
 // Largest bitmap the pull levels copy into shared memory (n up to 1,638,400).
-constexpr int kSmemBitmapMax = 200 * 1024;
+constexpr int kSmemBitmapMax = DAWN_SSSP_SMEM_BITMAP_MAX;
 
 int sssp_occupancy(dawn_graph* g) {
     int nb = 0;
