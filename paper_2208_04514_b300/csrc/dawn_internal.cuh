@@ -92,7 +92,6 @@ struct dawn_graph {
     int* status_host = nullptr;              // pinned
     int sssp_blocks_per_sm = 0;       // occupancy of the persistent kernel
     int sssp_smem_bytes = 0;          // dynamic shared memory: the pull levels' bitmap copy
-    int sssp_stage_cap = 0;           // rows a CTA stages per pull level (after the bitmap)
     unsigned sssp_launches = 0;       // picks the barrier counter of the next launch
     dawn_tuning tuning = {0, 0, 0, 0, 0.0, 0.0};  // 0 fields: built-in defaults
     // multi-source work buffers (allocated on first use)

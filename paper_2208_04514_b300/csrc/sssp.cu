@@ -30,7 +30,6 @@
 // (push -> pull when m_f * alpha > m_u; pull -> push when n_f * beta < n and
 // the frontier shrank).  Levels are separated by a grid barrier whose spin is
 // bounded; on expiry the kernel records DEV_TIMEOUT and every CTA returns.
-#include <algorithm>
 #include <climits>
 #include <mutex>
 
@@ -82,7 +81,6 @@ struct SsspArgs {
     int32_t pull_serial;     // in-neighbours a lane tests alone in a pull level
     int32_t bar_parity;      // which of the two barrier counters this launch uses
     int32_t smem_words;      // > 0: pull levels copy the bitmap (this many words) to shared memory
-    int32_t stage_cap;       // rows a CTA stages in shared memory (after the bitmap) per pull level
 };
 
 // A frontier queue: entries {first arc, arc count} and, in a parallel array,
@@ -406,50 +404,6 @@ __device__ void push_level(const SsspArgs& a, int step, uint32_t* vis, Queue qin
 // whole warp, 32 in-neighbours per round, so that one long row does not
 // hold 31 idle lanes.
 
-// Queue the rows staged by a CTA with one reservation for the whole CTA:
-// thread t takes a contiguous run of staged rows, a CTA-wide scan of their
-// entry and arc counts gives each thread its slots, and thread 0 adds the
-// totals to the level's packed counter.
-__device__ void block_flush(const int2* st, int cnt, Queue q, unsigned long long* qpack) {
-    __shared__ int s_wc[kWarps], s_wd[kWarps];
-    __shared__ unsigned long long s_base;
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int per = (cnt + kThreads - 1) / kThreads;
-    const int i0 = min(cnt, (int)threadIdx.x * per), i1 = min(cnt, i0 + per);
-    int c = 0, d = 0;
-    for (int i = i0; i < i1; ++i) {
-        const int deg = st[i].y - st[i].x;
-        d += deg;
-        c += (deg + kEntryArcs - 1) / kEntryArcs;
-    }
-    const int ci = warp_inclusive_scan(c, lane), di = warp_inclusive_scan(d, lane);
-    if (lane == 31) { s_wc[wid] = ci; s_wd[wid] = di; }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int tc = 0, td = 0;
-        for (int w = 0; w < kWarps; ++w) {
-            const int x = s_wc[w], y = s_wd[w];
-            s_wc[w] = tc;
-            s_wd[w] = td;
-            tc += x;
-            td += y;
-        }
-        s_base = tc ? atomicAdd(qpack, ((unsigned long long)tc << 32) | (unsigned)td) : 0ull;
-    }
-    __syncthreads();
-    int pos = (int)(s_base >> 32) + s_wc[wid] + ci - c;
-    int aoff = (int)(s_base & 0xffffffffu) + s_wd[wid] + di - d;
-    for (int i = i0; i < i1; ++i) {
-        const int rb = st[i].x, re = st[i].y;
-        for (int s0 = rb; s0 < re; s0 += kEntryArcs) {
-            q.ent[pos] = make_int2(s0, min(kEntryArcs, re - s0));
-            q.off[pos] = aoff + (s0 - rb);
-            ++pos;
-        }
-        aoff += re - rb;
-    }
-}
-
 // kSmem: the CTA first copies the whole step-start bitmap into shared memory
 // (it is read-only for the level), so every in-neighbour test is a shared
 // memory load instead of an L2 round trip.
@@ -462,21 +416,18 @@ __device__ __forceinline__ uint32_t bm_word(const uint32_t* vcur, int w) {
 }
 
 template <bool kSmem>
-__device__ void pull_level(const SsspArgs& a, int step, const uint32_t* vcur, uint32_t* vnext, Queue qout,
-                           unsigned long long* qpack, long long& nf, long long& mf) {
+__device__ void pull_level(const SsspArgs& a, int step, const uint32_t* vcur, uint32_t* vnext,
+                           long long& nf, long long& mf) {
     constexpr int U = 2;  // bitmap words per warp per round
-    __shared__ int s_stage_n;
-    int2* s_stage = reinterpret_cast<int2*>(reinterpret_cast<char*>(s_bitmap4) + (size_t)a.smem_words * 4);
     const int lane = threadIdx.x & 31;
     const int gw = blockIdx.x * kWarps + (threadIdx.x >> 5);
     const int nw = gridDim.x * kWarps;
     const bool symmetric = a.in_ptr == a.row_ptr;
-    if (threadIdx.x == 0) s_stage_n = 0;
     if (kSmem) {
         const uint4* src4 = reinterpret_cast<const uint4*>(vcur);
         for (int i = threadIdx.x; i < (a.smem_words >> 2); i += kThreads) s_bitmap4[i] = __ldcg(src4 + i);
+        __syncthreads();
     }
-    __syncthreads();
     for (int w0 = gw; w0 < a.nwords; w0 += U * nw) {
         uint32_t cur[U];
         bool cand[U], found[U];
@@ -554,30 +505,41 @@ __device__ void pull_level(const SsspArgs& a, int step, const uint32_t* vcur, ui
                 if (lane == L) found[u] = hit;
             }
             const uint32_t newbits = __ballot_sync(kFull, found[u]);
-            // the vertices found here are the next frontier: stage their rows
-            // (queued after the level, one reservation per CTA)
-            int rb = 0, re = 0;
-            bool ovf = false;
             if (found[u]) {
                 const int v = (w << 5) + lane;
                 a.dist[v] = step;
-                if (symmetric) { rb = ib[u]; re = ie[u]; }
-                else { rb = __ldg(a.row_ptr + v); re = __ldg(a.row_ptr + v + 1); }
                 nf += 1;
-                mf += re - rb;
-                if (re > rb) {
-                    const int slot = atomicAdd(&s_stage_n, 1);
-                    if (slot < a.stage_cap) s_stage[slot] = make_int2(rb, re);
-                    else ovf = true;
-                }
+                mf += symmetric ? (ie[u] - ib[u]) : (__ldg(a.row_ptr + v + 1) - __ldg(a.row_ptr + v));
             }
-            if (__any_sync(kFull, ovf)) warp_enqueue(ovf, rb, re, lane, qout, qpack);
             if (lane == 0) vnext[w] = cur[u] | newbits;
         }
     }
-    __syncthreads();
-    const int staged = min(s_stage_n, a.stage_cap);
-    if (staged > 0) block_flush(s_stage, staged, qout, qpack);
+}
+
+// After a pull level: queue the vertices it reached (bits of vnow not in vold).
+__device__ void bitmap_to_queue(const SsspArgs& a, const uint32_t* vnow, const uint32_t* vold,
+                                Queue qout, unsigned long long* qpack) {
+    const int lane = threadIdx.x & 31;
+    const int gw = blockIdx.x * kWarps + (threadIdx.x >> 5);
+    const int nw = gridDim.x * kWarps;
+    for (int base = gw << 5; base < a.nwords; base += nw << 5) {
+        const int w = base + lane;
+        uint32_t nb = w < a.nwords ? (__ldcg(vnow + w) & ~__ldcg(vold + w)) : 0u;
+        int rounds = __popc(nb);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) rounds = max(rounds, __shfl_xor_sync(kFull, rounds, o));
+        for (int r = 0; r < rounds; ++r) {
+            const bool has = nb != 0;
+            int rb = 0, re = 0;
+            if (has) {
+                const int v = (w << 5) + (__ffs(nb) - 1);
+                nb &= nb - 1;
+                rb = __ldg(a.row_ptr + v);
+                re = __ldg(a.row_ptr + v + 1);
+            }
+            warp_enqueue(has, rb, re, lane, qout, qpack);
+        }
+    }
 }
 
 __global__ void __launch_bounds__(kThreads, DAWN_SSSP_MIN_CTAS) sssp_kernel(SsspArgs a) {
@@ -643,7 +605,7 @@ __global__ void __launch_bounds__(kThreads, DAWN_SSSP_MIN_CTAS) sssp_kernel(Sssp
         // the frontier found at step s lives in queue (s & 1)
         const Queue qcur = (step & 1) ? Queue{a.q1, a.q1off} : Queue{a.q0, a.q0off};
         const Queue qnext = (step & 1) ? Queue{a.q0, a.q0off} : Queue{a.q1, a.q1off};
-        const unsigned long long qpack = s_snap[0];
+        unsigned long long qpack = s_snap[0];
         const long long nf_cur = (long long)s_snap[1];
         const long long mf_cur = (long long)s_snap[2];
         if (nf_cur == 0 || step >= a.n) break;
@@ -659,11 +621,18 @@ __global__ void __launch_bounds__(kThreads, DAWN_SSSP_MIN_CTAS) sssp_kernel(Sssp
         if (blockIdx.x == 0 && threadIdx.x < (int)(sizeof(CtrSlot) / 8))
             reinterpret_cast<unsigned long long*>(&ctl->ctr[(step + 2) % 3])[threadIdx.x] = 0;
 
+        if (!pull && last_pull) {
+            // the frontier exists only as a bitmap difference: turn it into a queue
+            bitmap_to_queue(a, vcur, vnext, qcur, &cur->qpack);
+            if (!grid_barrier(ctl, bar, bar_target, a.spin_limit, cur, s_snap)) return;
+            qpack = s_snap[0];
+            if (tracer) trace_rec(a, tslot, 4, step, (long long)(qpack >> 32));
+        }
         CtrSlot* out = &ctl->ctr[(step + 1) % 3];
         long long nf = 0, mf = 0;
         if (pull) {
-            if (a.smem_words > 0) pull_level<true>(a, step + 1, vcur, vnext, qnext, &out->qpack, nf, mf);
-            else pull_level<false>(a, step + 1, vcur, vnext, qnext, &out->qpack, nf, mf);
+            if (a.smem_words > 0) pull_level<true>(a, step + 1, vcur, vnext, nf, mf);
+            else pull_level<false>(a, step + 1, vcur, vnext, nf, mf);
             ++pulls;
         } else {
             push_level(a, step + 1, vcur, qcur, qpack, qnext, out, nf, mf);
@@ -697,20 +666,12 @@ __global__ void __launch_bounds__(kThreads, DAWN_SSSP_MIN_CTAS) sssp_kernel(Sssp
 // Largest bitmap the pull levels copy into shared memory (n up to 1,638,400).
 constexpr int kSmemBitmapMax = DAWN_SSSP_SMEM_BITMAP_MAX;
 
-// Dynamic shared memory of the persistent kernel: the pull levels' bitmap
-// copy (when it fits) followed by the staging area of rows found by a pull
-// level (kStageRows, fewer if the bitmap leaves less room).
-constexpr int kSmemTotalMax = 216 * 1024;
-constexpr int kStageRows = 4096;
-
 int sssp_occupancy(dawn_graph* g) {
     int nb = 0;
-    DAWN_CUDA_TRY(cudaFuncSetAttribute(sssp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemTotalMax));
+    DAWN_CUDA_TRY(cudaFuncSetAttribute(sssp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBitmapMax));
     const size_t words4 = (size_t)(g->nwords + 3) / 4 * 4;
     g->sssp_smem_bytes = words4 * 4 <= (size_t)kSmemBitmapMax ? (int)(words4 * 4) : 0;
-    g->sssp_stage_cap = std::min<int>(kStageRows, (kSmemTotalMax - g->sssp_smem_bytes) / (int)sizeof(int2));
-    DAWN_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        &nb, sssp_kernel, kThreads, g->sssp_smem_bytes + g->sssp_stage_cap * sizeof(int2)));
+    DAWN_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sssp_kernel, kThreads, g->sssp_smem_bytes));
     if (nb < 1) return fail(DAWN_E_CUDA, "persistent SSSP kernel cannot be resident on an SM");
     g->sssp_blocks_per_sm = nb;
     return DAWN_OK;
@@ -752,12 +713,11 @@ int sssp_launch(dawn_graph* g, int32_t src, int32_t* dist_dev, const dawn_sssp_o
     int bps = g->sssp_blocks_per_sm;
     if (opts && opts->blocks_per_sm > 0 && opts->blocks_per_sm < bps) bps = opts->blocks_per_sm;
     a.smem_words = g->sssp_smem_bytes / 4;
-    a.stage_cap = g->sssp_stage_cap;
     a.bar_parity = (int32_t)(g->sssp_launches & 1u);
     dim3 grid(g->sms * bps), block(kThreads);
     void* args[] = {&a};
     DAWN_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)sssp_kernel, grid, block, args,
-                                              (size_t)g->sssp_smem_bytes + g->sssp_stage_cap * sizeof(int2), st));
+                                              (size_t)g->sssp_smem_bytes, st));
     g->sssp_launches += 1;  // only a launch that was accepted zeroes the other counter
     return DAWN_OK;
 }
@@ -891,7 +851,6 @@ int sssp_noalloc(const int32_t* row_ptr, const int32_t* col_idx, int32_t n, int6
     a.mode = DAWN_MODE_PUSH;
     a.bar_parity = 0;  // the whole control block was just zeroed
     a.smem_words = 0;
-    a.stage_cap = 0;   // push only: pull levels (the only stagers) never run
     a.alpha = 15;
     a.beta = 18;
     a.pull_serial = 8;
