@@ -487,22 +487,36 @@ __device__ void pull_level(const SsspArgs& a, int step, const uint32_t* vcur, ui
         for (int u = 0; u < U; ++u) {
             const int w = w0 + u * nw;
             if (w >= a.nwords) continue;  // warp-uniform
-            unsigned rest = __ballot_sync(kFull, cand[u] && !found[u] && j[u] < ie[u]);
-            while (rest) {
-                const int L = __ffs(rest) - 1;
-                rest &= rest - 1;
-                const int jb = __shfl_sync(kFull, j[u], L);
-                const int je = __shfl_sync(kFull, ie[u], L);
-                bool hit = false;
-                for (int base = jb; base < je; base += 32) {
-                    bool hh = false;
-                    if (base + lane < je) {
-                        const int x = __ldg(a.in_idx + base + lane);
-                        hh = (bm_word<kSmem>(vcur, x >> 5) >> (x & 31)) & 1u;
-                    }
-                    if (__any_sync(kFull, hh)) { hit = true; break; }
+            // rows with in-arcs left: each round packs the unresolved rows of
+            // the warp end to end, tests their next 32 in-arcs (one per lane)
+            // and resolves every owner from one ballot; found rows drop out
+            while (true) {
+                const int rem = (cand[u] && !found[u]) ? ie[u] - j[u] : 0;
+                const int incl = warp_inclusive_scan(rem, lane);
+                const int total = __shfl_sync(kFull, incl, 31);
+                if (total == 0) break;
+                const int ex = incl - rem;
+                int o = 0;
+#pragma unroll
+                for (int bb = 16; bb > 0; bb >>= 1) {
+                    const int cidx = o + bb;
+                    const int pv = __shfl_sync(kFull, ex, cidx);
+                    if (pv <= lane) o = cidx;
                 }
-                if (lane == L) found[u] = hit;
+                const int oj = __shfl_sync(kFull, j[u], o);
+                const int oex = __shfl_sync(kFull, ex, o);
+                bool hh = false;
+                if (lane < total) {
+                    const int x = __ldg(a.in_idx + oj + (lane - oex));
+                    hh = (bm_word<kSmem>(vcur, x >> 5) >> (x & 31)) & 1u;
+                }
+                const unsigned hits = __ballot_sync(kFull, hh);
+                if (rem > 0 && ex < 32) {
+                    const int hi = min(32, ex + rem);
+                    const unsigned seg = (hi >= 32 ? kFull : ((1u << hi) - 1u)) & ~((1u << ex) - 1u);
+                    if (hits & seg) found[u] = true;
+                    j[u] += hi - ex;
+                }
             }
             const uint32_t newbits = __ballot_sync(kFull, found[u]);
             if (found[u]) {
