@@ -96,6 +96,7 @@ struct dawn_graph {
     dawn_tuning tuning = {0, 0, 0, 0, 0.0, 0.0};  // 0 fields: built-in defaults
     // multi-source work buffers (allocated on first use)
     uint64_t* ms_vis[2] = {nullptr, nullptr};
+    uint64_t* ms_acc = nullptr;       // per-vertex OR accumulators of dense batched levels
     int ms_words_cap = 0;             // W capacity of ms_vis
     void* ms_scratch = nullptr;       // per-pass distance block when the caller passes none
     size_t ms_scratch_bytes = 0;

@@ -176,6 +176,7 @@ void release(dawn_graph* g) {
     f(g->stats_dev);
     f(g->ms_vis[0]);
     f(g->ms_vis[1]);
+    f(g->ms_acc);
     f(g->ms_scratch);
     f(g->ms_counts);
     if (g->stats_host) cudaFreeHost(g->stats_host);

@@ -55,6 +55,7 @@ struct MsArgs {
     const int32_t* __restrict__ sources;  // device, k
     uint64_t* V0;                         // [n][W]
     uint64_t* V1;
+    unsigned long long* acc;              // [n][W] per-vertex OR of in-neighbours (dense levels); kept zero
     void* out;                            // distance rows, see layout
     int32_t* ecc;                         // device, k
     long long* dsum;
@@ -166,6 +167,81 @@ __device__ void fill_batch(const MsArgs& a, int s0, int kb) {
     }
 }
 
+// Dense level, first phase: the in-arcs of the whole CSC are cut into equal
+// ranges (a multiple of 32 long), one per warp of the grid.  A warp finds the
+// vertex holding its first arc with a 32-ary search over the row pointer,
+// keeps a batch of 32 consecutive vertices' row starts in its lanes, and walks
+// its range 32 arcs at a time: lane i loads the visited words of the arc's
+// source vertex, a segmented OR scan across lanes combines arcs of the same
+// target vertex, and the last lane of each segment ORs the result into
+// acc[target] (global atomics: a row may span two warps).  Rows of any
+// length are split evenly this way; no early exit.
+template <int W>
+__device__ void dense_accumulate(const MsArgs& a, const uint64_t* vcur) {
+    const int lane = threadIdx.x & 31;
+    const long long nw = (long long)gridDim.x * kMsWarps;
+    const long long gw = (long long)blockIdx.x * kMsWarps + (threadIdx.x >> 5);
+    const int n = a.n;
+    const long long M = __ldg(a.in_ptr + n);
+    long long chunk = (M + nw - 1) / nw;
+    chunk = (chunk + 31) & ~31LL;
+    const long long a0 = gw * chunk;
+    if (a0 >= M) return;
+    const long long a1 = min(M, a0 + chunk);
+    int lo = 0, hi = n;  // largest v with in_ptr[v] <= a0 lies in [lo, hi)
+    while (hi - lo > 32) {
+        const int stp = (hi - lo + 31) >> 5;
+        const int p = lo + lane * stp;
+        const int val = p < hi ? __ldg(a.in_ptr + p) : INT_MAX;
+        const unsigned b = __ballot_sync(kFull, (long long)val <= a0);
+        lo += (31 - __clz(b)) * stp;
+        hi = min(hi, lo + stp);
+    }
+    int vb = lo;
+    int beg = vb + lane < n ? __ldg(a.in_ptr + vb + lane) : INT_MAX;
+    long long endb = __ldg(a.in_ptr + min(n, vb + 32));
+    long long r = a0;
+    while (r < a1) {
+        if (r >= endb) {  // past this batch's rows (empty rows can leave it short of 32 arcs)
+            vb += 32;
+            beg = vb + lane < n ? __ldg(a.in_ptr + vb + lane) : INT_MAX;
+            endb = __ldg(a.in_ptr + min(n, vb + 32));
+            continue;
+        }
+        const int span = (int)min(min(32LL, a1 - r), endb - r);
+        const long long tt = r + lane;
+        const bool act = lane < span;
+        int o = 0;
+#pragma unroll
+        for (int bb = 16; bb > 0; bb >>= 1) {
+            const int cand = o + bb;
+            const int pv = __shfl_sync(kFull, beg, cand);
+            if ((long long)pv <= tt) o = cand;
+        }
+        const int key = act ? vb + o : -1 - lane;
+        unsigned long long x[W];
+        const int u = act ? __ldg(a.in_idx + tt) : 0;
+#pragma unroll
+        for (int w = 0; w < W; ++w) x[w] = act ? __ldcg(vcur + (long long)u * W + w) : 0ull;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int k2 = __shfl_up_sync(kFull, key, d);
+#pragma unroll
+            for (int w = 0; w < W; ++w) {
+                const unsigned long long y = __shfl_up_sync(kFull, x[w], d);
+                if (lane >= d && k2 == key) x[w] |= y;
+            }
+        }
+        const int knext = __shfl_down_sync(kFull, key, 1);
+        if (act && (lane == span - 1 || knext != key)) {
+#pragma unroll
+            for (int w = 0; w < W; ++w)
+                if (x[w]) atomicOr(a.acc + (long long)key * W + w, x[w]);
+        }
+        r += span;
+    }
+}
+
 template <int W>
 __global__ void __launch_bounds__(kMsThreads, 1) msbfs_kernel(MsArgs a) {
     __shared__ int s_cnt[kMsMaxLanes];
@@ -179,7 +255,6 @@ __global__ void __launch_bounds__(kMsThreads, 1) msbfs_kernel(MsArgs a) {
 
     MsCtl* ctl = a.ctl;
     __shared__ unsigned long long s_lanes[6];
-    __shared__ unsigned long long s_acc[kMsWarps][32][W];  // dense levels: per-vertex OR accumulators
     __shared__ int s_need, s_cover;
     __shared__ int s_status;
     if (threadIdx.x == 0) s_status = ms_ld_relaxed_s32(&ctl->status);
@@ -257,6 +332,12 @@ __global__ void __launch_bounds__(kMsThreads, 1) msbfs_kernel(MsArgs a) {
                 if (gtid == 0) atomicCAS(&ctl->status, DEV_OK, DEV_OVERFLOW);
                 return;
             }
+            if (dense) {
+                // arc-parallel phase: every in-arc of the graph once, in equal
+                // ranges per warp; then the per-vertex pass below finishes
+                dense_accumulate<W>(a, vcur);
+                if (!ms_barrier(ctl, bar, bar_target, a.spin_limit)) return;
+            }
             // ---- one level: lane = vertex, 32 consecutive vertices per warp
             while (true) {
                 int vb = 0;
@@ -276,76 +357,19 @@ __global__ void __launch_bounds__(kMsThreads, 1) msbfs_kernel(MsArgs a) {
                 if (valid && need && ((__ldg(a.excl + (v >> 5)) >> (v & 31)) & 1u)) need = false;
                 bool deferred = false;
                 if (dense) {
-                    // arc-parallel: the warp walks the concatenated in-lists of its
-                    // 32 vertices, 32 arcs per round, with a segmented OR scan
-                    // across the lanes of each round (no early exit)
-                    const int wib = threadIdx.x >> 5;
-                    int ib = 0, ie = 0;
-                    if (need) {
-                        ib = __ldg(a.in_ptr + v);
-                        ie = __ldg(a.in_ptr + v + 1);
+                    // the arc-parallel phase left the OR over v's in-neighbours in
+                    // acc_g[v]: take it and leave the slot zero for the next level
+                    bool nz = false;
+#pragma unroll
+                    for (int w = 0; w < W; ++w) {
+                        const unsigned long long x = valid ? __ldcg(a.acc + (long long)v * W + w) : 0ull;
+                        acc[w] = need ? x : 0ull;
+                        nz |= x != 0ull;
                     }
-                    if (need && ie - ib > kMsHeavy) {
-                        const int slot = atomicAdd(&s_hcount, 1);
-                        if (slot < kMsHeavyMax) {
-                            deferred = true;
-                            s_hv[slot] = v;
-                            s_hj[slot] = ib;
-                            s_hie[slot] = ie;
+                    if (nz) {
 #pragma unroll
-                            for (int w = 0; w < W; ++w) {
-                                s_hvv[slot][w] = vv[w];
-                                s_hacc[slot][w] = 0ull;
-                            }
-                        }
+                        for (int w = 0; w < W; ++w) a.acc[(long long)v * W + w] = 0ull;
                     }
-                    const int deg = (need && !deferred) ? ie - ib : 0;
-                    int incl = deg;
-#pragma unroll
-                    for (int o = 1; o < 32; o <<= 1) {
-                        const int y = __shfl_up_sync(kFull, incl, o);
-                        if (lane >= o) incl += y;
-                    }
-                    const int total = __shfl_sync(kFull, incl, 31);
-                    const int ex = incl - deg;
-#pragma unroll
-                    for (int w = 0; w < W; ++w) s_acc[wib][lane][w] = 0ull;
-                    __syncwarp();
-                    for (int base = 0; base < total; base += 32) {
-                        const int tt = base + lane;
-                        int o = 0;
-#pragma unroll
-                        for (int bb = 16; bb > 0; bb >>= 1) {
-                            const int cand = o + bb;
-                            const int pv = __shfl_sync(kFull, ex, cand);
-                            if (pv <= tt) o = cand;
-                        }
-                        const int oib = __shfl_sync(kFull, ib, o);
-                        const int oex = __shfl_sync(kFull, ex, o);
-                        const bool act = tt < total;
-                        if (!act) o = 32 + lane;  // lanes past the end form their own segments
-                        unsigned long long x[W];
-                        const int u = act ? __ldg(a.in_idx + oib + (tt - oex)) : 0;
-#pragma unroll
-                        for (int w = 0; w < W; ++w) x[w] = act ? __ldcg(vcur + (long long)u * W + w) : 0ull;
-#pragma unroll
-                        for (int d = 1; d < 32; d <<= 1) {
-                            const int o2 = __shfl_up_sync(kFull, o, d);
-#pragma unroll
-                            for (int w = 0; w < W; ++w) {
-                                const unsigned long long y = __shfl_up_sync(kFull, x[w], d);
-                                if (lane >= d && o2 == o) x[w] |= y;
-                            }
-                        }
-                        const int onext = __shfl_down_sync(kFull, o, 1);
-                        if (act && (lane == 31 || onext != o)) {
-#pragma unroll
-                            for (int w = 0; w < W; ++w) s_acc[wib][o][w] |= x[w];
-                        }
-                    }
-                    __syncwarp();
-#pragma unroll
-                    for (int w = 0; w < W; ++w) acc[w] = s_acc[wib][lane][w];
                 } else {
                     int j = 0, ie = 0;
                     if (need) {
@@ -568,6 +592,10 @@ int ms_workspace(dawn_graph* g, int W) {
         const size_t bytes = sizeof(uint64_t) * (size_t)g->n * 4;  // room for W = 4
         DAWN_CUDA_TRY(cudaMalloc((void**)&g->ms_vis[0], bytes));
         DAWN_CUDA_TRY(cudaMalloc((void**)&g->ms_vis[1], bytes));
+        if (g->ms_acc) cudaFree(g->ms_acc);
+        g->ms_acc = nullptr;
+        DAWN_CUDA_TRY(cudaMalloc((void**)&g->ms_acc, bytes));
+        DAWN_CUDA_TRY(cudaMemset(g->ms_acc, 0, bytes));
         g->ms_words_cap = 4;
     }
     if (!g->ms_counts) {
@@ -635,6 +663,7 @@ int msbfs_run(dawn_graph* g, const int32_t* sources, int32_t k, void* dist_block
     a.sources = d_src;
     a.V0 = g->ms_vis[0];
     a.V1 = g->ms_vis[1];
+    a.acc = reinterpret_cast<unsigned long long*>(g->ms_acc);
     a.ecc = d_ecc;
     a.dsum = d_dsum;
     a.reached = d_reached;
@@ -691,6 +720,8 @@ int msbfs_run(dawn_graph* g, const int32_t* sources, int32_t k, void* dist_block
     if (e != cudaSuccess) return cuda_fail(e, "dawn_msbfs", __FILE__, __LINE__);
     if (status != DEV_OK) {
         DAWN_CUDA_TRY(cudaMemsetAsync(ctl, 0, sizeof(MsCtl), st));
+        // a pass cut short can leave accumulator slots set
+        DAWN_CUDA_TRY(cudaMemsetAsync(g->ms_acc, 0, sizeof(uint64_t) * (size_t)g->n * 4, st));
         DAWN_CUDA_TRY(cudaStreamSynchronize(st));
         if (status == DEV_OVERFLOW) return fail(DAWN_E_OVERFLOW, "a distance exceeded the int16 range (32767)");
         if (status == DEV_TIMEOUT) return fail(DAWN_E_TIMEOUT, "a grid-barrier wait on the device ran out of its spin budget");
