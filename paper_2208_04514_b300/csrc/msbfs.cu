@@ -524,7 +524,13 @@ __global__ void __launch_bounds__(kMsThreads, 1) msbfs_kernel(MsArgs a) {
                 ctl->lanes_new[(t + 1) % 3][threadIdx.x - 32] = 0ull;
             if (!ms_barrier(ctl, bar, bar_target, a.spin_limit, ctl->lanes_new[t % 3], 6, s_lanes)) return;
             // next level: arc-parallel while most scanned vertices stay uncovered
-            dense = 2 * s_lanes[5] < s_lanes[4];
+            // and a good share of the lanes is still growing
+            {
+                int growing = 0;
+#pragma unroll
+                for (int w = 0; w < W; ++w) growing += __popcll(s_lanes[w]);
+                dense = 2 * s_lanes[5] < s_lanes[4] && 4 * growing > L;
+            }
             if (a.trace && blockIdx.x == 0 && threadIdx.x == 0 && tslot < a.trace_cap) {
                 unsigned long long tnow;
                 asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(tnow));
