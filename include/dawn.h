@@ -81,6 +81,11 @@ extern "C" {
 #define DAWN_REQ_DONE    2 /* every distance row is in the caller's buffer */
 #define DAWN_REQ_FAILED  3 /* the request ended with an error (see dawn_serve_poll's return) */
 
+/* Per-graph server step (dawn_serve_create_ex). */
+#define DAWN_SERVE_AUTO     0 /* FRONTIER when the average out-degree m / n is below 8, else DENSE */
+#define DAWN_SERVE_DENSE    1 /* every iteration pulls every vertex (bit-lane Alg. 1 over the CSC) */
+#define DAWN_SERVE_FRONTIER 2 /* every iteration pushes only the last iteration's arrivals (bit-lane Alg. 3 over the CSR) */
+
 typedef struct dawn_graph* dawn_graph_t;
 typedef struct dawn_server* dawn_server_t;
 
@@ -272,6 +277,22 @@ DAWN_API int dawn_msbfs_ex(dawn_graph_t g, const int32_t* sources, int32_t k, vo
  */
 DAWN_API int dawn_serve_create(const dawn_graph_t* graphs, int ngraphs, size_t mem_budget_bytes,
                                int max_lanes, dawn_server_t* out);
+
+/*
+ * dawn_serve_create with the step chosen per graph.  modes: ngraphs values
+ * DAWN_SERVE_AUTO / _DENSE / _FRONTIER (host memory, read during the call), or
+ * NULL for all AUTO.  Both steps give identical distances.  DENSE keeps two
+ * n * max_lanes / 8-byte visited arrays per graph and reads all of them every
+ * iteration.  FRONTIER keeps per vertex its visited words and two frontier
+ * words per lane word (3 * n * max_lanes / 8 bytes) and two lists of
+ * n * max_lanes / 64 uint32 keys; an iteration touches only the out-arcs of
+ * the vertices reached in the previous one, plus one clearing pass over the
+ * visited words in iterations that admit lanes to that graph.  FRONTIER
+ * needs n * max_lanes / 64 < 2^32 (AUTO falls back to DENSE above it).
+ * DAWN_E_INVALID on a bad mode.
+ */
+DAWN_API int dawn_serve_create_ex(const dawn_graph_t* graphs, int ngraphs, size_t mem_budget_bytes,
+                                  int max_lanes, const int32_t* modes, dawn_server_t* out);
 
 /*
  * Enqueue a request (non-blocking).  dist_out: host or device, k x n

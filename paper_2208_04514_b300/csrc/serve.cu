@@ -10,6 +10,13 @@
 // iteration t, so its row is exactly the single-source result whatever else
 // shares the device (Thm 1: the first level at which a vertex is reached).
 //
+// Graphs of low average degree (many levels, small frontiers) take the
+// frontier step instead: the bit-lane push of Alg. 3 (Eq. 5-7) from only the
+// (vertex, lane word) pairs that gained lanes in the previous iteration,
+// along their CSR rows.  New lanes are set in one visited array in place by
+// atomic OR, so each new (vertex, lane) is claimed by exactly one arc and
+// gets the same level as in the pull; the arrivals form the next frontier.
+//
 // Host <-> device protocol (device-mapped pinned memory):
 //   * admission slot: the host thread writes one sorted batch of
 //     {graph, lane, source, row address, element size, token} entries and
@@ -49,6 +56,8 @@ constexpr int kSvSerial = 8;
 constexpr int kSvHeavy = 512;
 constexpr int kSvHeavyMax = 32;
 constexpr long long kSvSegBytes = 1 << 16; // row-fill work item
+constexpr int kSvPushCap = 4096;           // next-frontier keys staged per CTA round
+constexpr int kSvPushWarpDeg = 32;         // longer rows are pushed by the whole warp
 constexpr unsigned kFull = 0xffffffffu;
 
 struct AdmitEntry {
@@ -80,14 +89,25 @@ struct HostShared {
     DoneRec done[kSvDoneRing];
 };
 
-// Per graph, device memory.
+// Per graph, device memory.  Dense graphs keep two vertex-major visited arrays
+// (V[0], V[1], ping-pong; W words per vertex).  Frontier graphs are stored
+// word-major, one n-word array per lane word, indexed by the key w * n + v:
+// the visited words VS (updated in place), per iteration parity the frontier
+// words F[p] (lanes that reached (v, w) in the last iteration) and the list
+// Q[p] of the keys whose frontier word is nonzero (each key once: its first
+// writer appends it).
 struct SvGraph {
     const int32_t* in_ptr;
     const int32_t* in_idx;
     const uint32_t* excl;
+    const int32_t* row_ptr;
+    const int32_t* col_idx;
     uint64_t* V[2];
+    uint64_t* VS;
+    uint64_t* F[2];
+    uint32_t* Q[2];
     int32_t n;
-    int32_t pad;
+    int32_t frontier;
     int32_t lane_start[kSvMaxLanes];
     int32_t lane_bytes[kSvMaxLanes];
     unsigned long long lane_row[kSvMaxLanes];
@@ -99,9 +119,13 @@ struct alignas(128) SvCtl {
     int status;
     int pad[31];
     unsigned long long lanes_new[3][kSvMaxGraphs][4];
+    unsigned long long lanes_over[3][kSvMaxGraphs][4];  // lanes whose next distance overflowed an int16 row
     // published by CTA 0 for iteration t into pub[t & 1]: {admitted entries,
     // exit flag, first entry of each graph (kSvMaxGraphs + 1 values)}
     int pub[2][32];
+    // frontier graphs: keys appended to Q during iteration t are counted in
+    // qn[(t + 1) % 3][g]; slot (t + 2) % 3 is cleared during iteration t
+    int qn[3][kSvMaxGraphs];
     AdmitEntry admit[2][kSvMaxAdmit];     // sorted by (graph, src)
     long long seg_prefix[2][kSvMaxAdmit + 1];  // row-fill work items before each entry
 };
@@ -119,6 +143,11 @@ struct SvArgs {
 __device__ __forceinline__ unsigned sv_ld_acquire(const unsigned* p) {
     unsigned v;
     asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ unsigned sv_ld_relaxed_sys(const volatile unsigned* p) {
+    unsigned v;
+    asm volatile("ld.relaxed.sys.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
 }
 __device__ __forceinline__ unsigned sv_ld_acquire_sys(const volatile unsigned* p) {
@@ -157,10 +186,12 @@ __device__ __forceinline__ AdmitEntry ld_entry(const AdmitEntry* p) {
     return e;
 }
 
-// With `snap`, thread 0 copies nsnap ints after the acquire into s_snap
-// for the whole CTA (one L2 request per CTA, not one per warp).
+// With `snap`, thread 0 copies nsnap ints (and nsnap2 from snap2) after the
+// acquire into shared memory for the whole CTA (one L2 request per CTA, not
+// one per warp).
 __device__ bool sv_barrier(SvCtl* ctl, unsigned* count, unsigned& target, long long spin_limit,
-                           const int* snap = nullptr, int nsnap = 0, int* s_snap = nullptr) {
+                           const int* snap = nullptr, int nsnap = 0, int* s_snap = nullptr,
+                           const int* snap2 = nullptr, int nsnap2 = 0, int* s_snap2 = nullptr) {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -177,8 +208,10 @@ __device__ bool sv_barrier(SvCtl* ctl, unsigned* count, unsigned& target, long l
             }
             if ((++polls & 15u) == 0 && sv_ld_relaxed_s32(&ctl->status) != DEV_OK) { ok = 0; break; }
         }
-        if (ok)
+        if (ok) {
             for (int i = 0; i < nsnap; ++i) s_snap[i] = sv_ld_relaxed_s32(snap + i);
+            for (int i = 0; i < nsnap2; ++i) s_snap2[i] = sv_ld_relaxed_s32(snap2 + i);
+        }
         s_ok = ok;
     }
     __syncthreads();
@@ -196,6 +229,90 @@ __device__ __forceinline__ void sv_store(unsigned long long row, int bytes, long
     else reinterpret_cast<int32_t*>(row)[v] = value;
 }
 
+// One distance of a lane; false (nothing stored) when it does not fit the
+// lane's int16 row, which retires the lane with an overflow report.
+__device__ __forceinline__ bool sv_put(unsigned long long row, int bytes, long long v, int value) {
+    if (bytes == 2) {
+        if (value > 32767) return false;
+        reinterpret_cast<int16_t*>(row)[v] = (int16_t)value;
+    } else {
+        reinterpret_cast<int32_t*>(row)[v] = value;
+    }
+    return true;
+}
+
+// Frontier push of lane word w along up to four arcs (u -> x[q]) of one row:
+// f holds the lanes that reached u in the last iteration; Vw / Fw are the
+// word-w visited words and next-parity frontier words.  The arcs' loads and
+// atomics are issued together.  Lanes new at x are set in Vw[x] in place by
+// atomic OR (so every new (x, lane) is claimed by exactly one arc), their
+// distances stored, and OR-ed into Fw[x].  Bit q of the result: arc q made
+// Fw[x[q]] nonzero, so its key joins the next list.  nm / om collect the
+// lanes that grew / overflowed their rows.
+template <int W>
+__device__ __forceinline__ unsigned sv_push_arcs(uint64_t* Vw, uint64_t* Fw, const int32_t* __restrict__ ci, int j,
+                                                 int cnt, int w, unsigned long long f, int t,
+                                                 const unsigned long long* s_row, const int* s_bytes, const int* s_start,
+                                                 unsigned long long (&nm)[W], unsigned long long (&om)[W], int (&x)[4]) {
+    unsigned long long have[4], nb[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) x[q] = q < cnt ? __ldg(ci + j + q) : 0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) have[q] = q < cnt ? __ldcg(Vw + x[q]) : ~0ull;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        nb[q] = f & ~have[q];
+        if (nb[q]) nb[q] &= ~atomicOr(reinterpret_cast<unsigned long long*>(Vw + x[q]), nb[q]);
+    }
+    unsigned app = 0u;
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+        if (nb[q] && atomicOr(reinterpret_cast<unsigned long long*>(Fw + x[q]), nb[q]) == 0ull) app |= 1u << q;
+    unsigned long long grew = 0ull, over = 0ull;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        unsigned long long m = nb[q];
+        grew |= m;
+        while (m) {
+            const int b = __ffsll((long long)m) - 1;
+            m &= m - 1;
+            const int s = w * 64 + b;
+            if (!sv_put(s_row[s], s_bytes[s], x[q], t - s_start[s])) over |= 1ull << b;
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < W; ++q)
+        if (q == w) {
+            nm[q] |= grew;
+            om[q] |= over;
+        }
+    return app;
+}
+
+// Warp-wide append of the lanes' keys with app set: one shared-memory
+// reservation per warp into the CTA's staging buffer; what does not fit goes
+// straight to the list with one global reservation.
+__device__ __forceinline__ void sv_append(bool app, uint32_t key, uint32_t* s_pbuf, int* s_pcount, uint32_t* Qn,
+                                          int* qnext, int lane) {
+    const unsigned b = __ballot_sync(kFull, app);
+    if (!b) return;
+    const int leader = __ffs(b) - 1;
+    const int cnt = __popc(b);
+    int slot0 = 0, gbase = 0;
+    if (lane == leader) {
+        slot0 = atomicAdd(s_pcount, cnt);
+        const int spill = slot0 + cnt - max(kSvPushCap, slot0);
+        if (spill > 0) gbase = atomicAdd(qnext, spill);
+    }
+    slot0 = __shfl_sync(kFull, slot0, leader);
+    gbase = __shfl_sync(kFull, gbase, leader);
+    if (app) {
+        const int slot = slot0 + __popc(b & ((1u << lane) - 1u));
+        if (slot < kSvPushCap) s_pbuf[slot] = key;
+        else Qn[gbase + slot - max(kSvPushCap, slot0)] = key;
+    }
+}
+
 template <int W>
 __global__ void __launch_bounds__(kSvThreads, 1) serve_kernel(SvArgs a) {
     constexpr int L = 64 * W;
@@ -208,7 +325,15 @@ __global__ void __launch_bounds__(kSvThreads, 1) serve_kernel(SvArgs a) {
     __shared__ int s_hcount;
     __shared__ int s_hv[kSvHeavyMax], s_hj[kSvHeavyMax], s_hie[kSvHeavyMax];
     __shared__ unsigned long long s_hvv[kSvHeavyMax][W], s_hacc[kSvHeavyMax][W], s_hseed[kSvHeavyMax][W];
-    __shared__ int s_exit;
+    __shared__ int s_front[kSvMaxGraphs];    // 1: frontier graph
+    __shared__ int s_qn[kSvMaxGraphs];       // frontier entries to expand this iteration
+    __shared__ unsigned long long s_adm[kSvMaxGraphs][W];
+    __shared__ uint32_t s_pbuf[kSvPushCap];  // next-frontier keys staged by this CTA
+    __shared__ int s_pcount, s_pc, s_pbase;
+    __shared__ unsigned long long s_overmask[4];
+    __shared__ unsigned long long s_fin[kSvMaxGraphs * 4], s_ovr[kSvMaxGraphs * 4];
+    __shared__ int s_recoff[kSvMaxGraphs * 4 + 1];
+    __shared__ unsigned long long s_done_tail;  // CTA 0: completion records written so far
 
     SvCtl* ctl = a.ctl;
     HostShared* hs = a.hs;
@@ -232,7 +357,11 @@ __global__ void __launch_bounds__(kSvThreads, 1) serve_kernel(SvArgs a) {
     unsigned int seen_seq = 0;  // CTA 0, thread 0: last admission batch taken
 
     if (threadIdx.x == 0) s_hcount = 0;
+    if (threadIdx.x == 0) s_pcount = 0;
     if (threadIdx.x < 4) s_newmask[threadIdx.x] = 0;
+    if (threadIdx.x < 4) s_overmask[threadIdx.x] = 0;
+    if (blockIdx.x == 0 && threadIdx.x == 0) s_done_tail = hs->done_tail;
+    for (int g = threadIdx.x; g < kSvMaxGraphs; g += kSvThreads) s_front[g] = g < a.ngraphs ? a.graphs[g].frontier : 0;
 
     // iteration -1: CTA 0 picks up a batch that is already waiting
     if (blockIdx.x == 0) {
@@ -274,13 +403,33 @@ __global__ void __launch_bounds__(kSvThreads, 1) serve_kernel(SvArgs a) {
             }
         }
         if (threadIdx.x < 3 * kSvMaxGraphs * 4) (&ctl->lanes_new[0][0][0])[threadIdx.x] = 0ull;
+        if (threadIdx.x < 3 * kSvMaxGraphs * 4) (&ctl->lanes_over[0][0][0])[threadIdx.x] = 0ull;
     }
-    if (!sv_barrier(ctl, bar, bar_target, a.spin_limit, ctl->pub[0], 2 + kSvMaxGraphs + 1, s_pub)) return;
+    if (!sv_barrier(ctl, bar, bar_target, a.spin_limit, ctl->pub[0], 2 + kSvMaxGraphs + 1, s_pub, ctl->qn[0],
+                    kSvMaxGraphs, s_qn))
+        return;
 
     for (int t = 0;; ++t) {
         const int par = t & 1;
         const int na = s_pub[0];
         const long long* seg = ctl->seg_prefix[par];
+        // CTA 0 issues its reads of the host mailbox now and uses them at the
+        // end of the iteration, so the PCIe round trip overlaps the level
+        unsigned seq_early = 0u, stop_early = 0u;
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            seq_early = sv_ld_relaxed_sys(&hs->batch_seq);
+            stop_early = *(volatile unsigned*)&hs->stop;
+        }
+        // lanes admitted now, per graph
+        if (na > 0) {
+            for (int i = threadIdx.x; i < kSvMaxGraphs * W; i += kSvThreads) (&s_adm[0][0])[i] = 0ull;
+            __syncthreads();
+            for (int i = threadIdx.x; i < na; i += kSvThreads) {
+                const AdmitEntry e = ld_entry(&ctl->admit[par][i]);
+                atomicOr(&s_adm[e.graph][e.lane >> 6], 1ull << (e.lane & 63));
+            }
+            __syncthreads();
+        }
         // ---- (1) fill the rows of lanes admitted now: -1, and 0 at the source
         if (na > 0) {
             const long long items = __ldcg(seg + na);
@@ -307,6 +456,29 @@ __global__ void __launch_bounds__(kSvThreads, 1) serve_kernel(SvArgs a) {
                 if (threadIdx.x == 0 && srcoff >= off && srcoff < off + len) sv_store(e.row, e.bytes, e.src, 0);
             }
         }
+        // ---- (1b) frontier graphs that receive lanes now: clear those lanes'
+        //      visited bits left by earlier requests (dense graphs mask them
+        //      on read instead), then one barrier before any push reads V
+        {
+            bool clear = false;
+            for (int g = 0; g < a.ngraphs; ++g) clear |= s_front[g] && s_pub[2 + g + 1] > s_pub[2 + g];
+            if (clear) {
+                for (int g = 0; g < a.ngraphs; ++g) {
+                    if (!s_front[g] || s_pub[2 + g + 1] == s_pub[2 + g]) continue;
+                    const long long ng = a.graphs[g].n;
+                    for (int w = 0; w < W; ++w) {
+                        const unsigned long long m = s_adm[g][w];
+                        if (!m) continue;
+                        uint64_t* Vw = a.graphs[g].VS + w * ng;
+                        for (long long v = gtid; v < ng; v += gthreads) {
+                            const unsigned long long x = __ldcg(Vw + v);
+                            if (x & m) Vw[v] = x & ~m;
+                        }
+                    }
+                }
+                if (!sv_barrier(ctl, bar, bar_target, a.spin_limit)) return;
+            }
+        }
         // ---- (2) one level for every graph with occupied or admitted lanes
         for (int g = 0; g < a.ngraphs; ++g) {
             const int a0 = s_pub[2 + g];  // admitted entries are sorted by graph
@@ -315,12 +487,12 @@ __global__ void __launch_bounds__(kSvThreads, 1) serve_kernel(SvArgs a) {
             unsigned long long adm[W];
             bool any = false;
 #pragma unroll
-            for (int w = 0; w < W; ++w) { adm[w] = 0ull; any |= occ[g][w] != 0ull; }
-            for (int i = a0; i < ai; ++i) {
-                const int ln = ld_entry(&ctl->admit[par][i]).lane;
-                adm[ln >> 6] |= 1ull << (ln & 63);
+            for (int w = 0; w < W; ++w) {
+                adm[w] = nag > 0 ? s_adm[g][w] : 0ull;
+                any |= occ[g][w] != 0ull;
             }
-            if (!any && nag == 0) continue;
+            const bool front = s_front[g] != 0;
+            if (front ? (s_qn[g] == 0 && nag == 0) : (!any && nag == 0)) continue;
             SvGraph* G = &a.graphs[g];
             const int n = G->n;
             uint64_t* vcur = G->V[t & 1];
@@ -335,13 +507,111 @@ __global__ void __launch_bounds__(kSvThreads, 1) serve_kernel(SvArgs a) {
                 s_bytes[i] = __ldcg(G->lane_bytes + i);
                 s_row[i] = __ldcg(G->lane_row + i);
             }
-            for (int i = threadIdx.x; i < nag; i += kSvThreads) {
+            for (int i = threadIdx.x; i < nag && !front; i += kSvThreads) {
                 const AdmitEntry e = ld_entry(&ctl->admit[par][a0 + i]);
                 s_asrc[i] = e.src;
                 s_alane[i] = e.lane;
             }
             __syncthreads();
-            for (int vb = gw << 5; vb < n; vb += nw << 5) {
+            if (front) {
+                // ---- frontier graph: push the lanes that reached each listed
+                //      (vertex, word) in the last iteration along its CSR row
+                const int pq = t & 1;
+                uint64_t* VS = G->VS;
+                uint64_t* Fc = G->F[pq];
+                uint64_t* Fn = G->F[pq ^ 1];
+                const uint32_t* Qc = G->Q[pq];
+                uint32_t* Qn = G->Q[pq ^ 1];
+                const int32_t* rp = G->row_ptr;
+                const int32_t* ci = G->col_idx;
+                int* qnext = &ctl->qn[(t + 1) % 3][g];
+                // sources of the lanes admitted now: visited, and in the next frontier
+                for (long long i = gtid; i < nag; i += gthreads) {
+                    const AdmitEntry e = ld_entry(&ctl->admit[par][a0 + i]);
+                    const unsigned long long bit = 1ull << (e.lane & 63);
+                    const long long key = (long long)(e.lane >> 6) * n + e.src;
+                    atomicOr(reinterpret_cast<unsigned long long*>(VS + key), bit);
+                    if (atomicOr(reinterpret_cast<unsigned long long*>(Fn + key), bit) == 0ull)
+                        Qn[atomicAdd(qnext, 1)] = (uint32_t)key;
+                }
+                unsigned long long nm[W], om[W];
+#pragma unroll
+                for (int w = 0; w < W; ++w) nm[w] = om[w] = 0ull;
+                const int nq = s_qn[g];
+                // one listed key per thread and round (the loop bound is the
+                // same for the whole CTA); appends are staged in shared memory
+                for (long long base = (long long)blockIdx.x * kSvThreads; base < nq; base += gthreads) {
+                    const long long i = base + threadIdx.x;
+                    int w = 0;
+                    unsigned long long f = 0ull;
+                    int rb = 0, re = 0;
+                    if (i < nq) {
+                        const uint32_t key = __ldcg(Qc + i);
+                        w = (int)(key / (uint32_t)n);
+                        const int u = (int)(key - (uint32_t)w * (uint32_t)n);
+                        f = __ldcg(Fc + key);
+                        rb = __ldg(rp + u);
+                        re = __ldg(rp + u + 1);
+                        Fc[key] = 0ull;
+                        f &= occ[g][w];  // lanes retired since: dropped
+                        if (!f) re = rb;
+                    }
+                    uint64_t* Vw = VS + (long long)w * n;
+                    uint64_t* Fw = Fn + (long long)w * n;
+                    const bool wide = re - rb > kSvPushWarpDeg;
+                    const int deg = wide ? 0 : re - rb;
+                    const int dmax = (int)__reduce_max_sync(kFull, (unsigned)deg);
+                    for (int d0 = 0; d0 < dmax; d0 += 4) {
+                        int x[4] = {0, 0, 0, 0};
+                        const int cnt = min(4, deg - d0);
+                        const unsigned app = cnt > 0 ? sv_push_arcs<W>(Vw, Fw, ci, rb + d0, cnt, w, f, t, s_row,
+                                                                       s_bytes, s_start, nm, om, x)
+                                                     : 0u;
+#pragma unroll
+                        for (int q = 0; q < 4; ++q)
+                            sv_append((app >> q) & 1u, (uint32_t)w * (uint32_t)n + (uint32_t)x[q], s_pbuf, &s_pcount,
+                                      Qn, qnext, lane);
+                    }
+                    unsigned wl = __ballot_sync(kFull, wide);
+                    while (wl) {  // long rows: the whole warp, one arc per thread
+                        const int sl = __ffs(wl) - 1;
+                        wl &= wl - 1;
+                        const int jb = __shfl_sync(kFull, rb, sl);
+                        const int je = __shfl_sync(kFull, re, sl);
+                        const unsigned long long fs = __shfl_sync(kFull, f, sl);
+                        const int ws = __shfl_sync(kFull, w, sl);
+                        uint64_t* Vws = VS + (long long)ws * n;
+                        uint64_t* Fws = Fn + (long long)ws * n;
+                        for (int j0 = jb; j0 < je; j0 += 32) {
+                            int x[4] = {0, 0, 0, 0};
+                            const int j = j0 + lane;
+                            const unsigned app = j < je ? sv_push_arcs<W>(Vws, Fws, ci, j, 1, ws, fs, t, s_row, s_bytes,
+                                                                          s_start, nm, om, x)
+                                                        : 0u;
+                            sv_append(app & 1u, (uint32_t)ws * (uint32_t)n + (uint32_t)x[0], s_pbuf, &s_pcount, Qn,
+                                      qnext, lane);
+                        }
+                    }
+                    __syncthreads();
+                    if (threadIdx.x == 0) {
+                        const int c = min(s_pcount, kSvPushCap);
+                        s_pcount = 0;
+                        s_pc = c;
+                        s_pbase = c > 0 ? atomicAdd(qnext, c) : 0;
+                    }
+                    __syncthreads();
+                    for (int k = threadIdx.x; k < s_pc; k += kSvThreads) Qn[s_pbase + k] = s_pbuf[k];
+                    __syncthreads();
+                }
+#pragma unroll
+                for (int w = 0; w < W; ++w) {
+                    const unsigned long long m = sv_warp_or64(nm[w]);
+                    if (lane == 0 && m) atomicOr(&s_newmask[w], m);
+                    const unsigned long long o = sv_warp_or64(om[w]);
+                    if (lane == 0 && o) atomicOr(&s_overmask[w], o);
+                }
+            }
+            for (int vb = front ? n : gw << 5; vb < n; vb += nw << 5) {
                 const int v = vb + lane;
                 const bool valid = v < n;
                 unsigned long long vv[W], acc[W], seed[W];
@@ -435,7 +705,8 @@ __global__ void __launch_bounds__(kSvThreads, 1) serve_kernel(SvArgs a) {
                         const int bit = __ffsll((long long)uni) - 1;
                         uni &= uni - 1;
                         const int s = w * 64 + bit;
-                        if ((nb >> bit) & 1ull) sv_store(s_row[s], s_bytes[s], v, t - s_start[s]);
+                        if (((nb >> bit) & 1ull) && !sv_put(s_row[s], s_bytes[s], v, t - s_start[s]))
+                            atomicOr(&s_overmask[w], 1ull << bit);
                     }
                 }
             }
@@ -468,13 +739,16 @@ __global__ void __launch_bounds__(kSvThreads, 1) serve_kernel(SvArgs a) {
                     if (lane == 0 && nbw[w]) atomicOr(&s_newmask[w], nbw[w]);
                 }
                 for (int i = lane; i < L; i += 32)
-                    if ((nbw[i >> 6] >> (i & 63)) & 1ull) sv_store(s_row[i], s_bytes[i], v, t - s_start[i]);
+                    if (((nbw[i >> 6] >> (i & 63)) & 1ull) && !sv_put(s_row[i], s_bytes[i], v, t - s_start[i]))
+                        atomicOr(&s_overmask[i >> 6], 1ull << (i & 63));
             }
             __syncthreads();
             if (threadIdx.x == 0) s_hcount = 0;
             if (threadIdx.x < W) {
                 if (s_newmask[threadIdx.x]) atomicOr(&ctl->lanes_new[t % 3][g][threadIdx.x], s_newmask[threadIdx.x]);
+                if (s_overmask[threadIdx.x]) atomicOr(&ctl->lanes_over[t % 3][g][threadIdx.x], s_overmask[threadIdx.x]);
                 s_newmask[threadIdx.x] = 0;
+                s_overmask[threadIdx.x] = 0;
             }
             // lanes admitted now start counting at this iteration (all threads
             // have read occ[g] above; the next graph's first barrier orders this)
@@ -488,11 +762,17 @@ __global__ void __launch_bounds__(kSvThreads, 1) serve_kernel(SvArgs a) {
             __shared__ int s_take;
             const int npar = par ^ 1;
             if (threadIdx.x == 0) {
-                const unsigned seq = sv_ld_acquire_sys(&hs->batch_seq);
-                s_take = (seq != seen_seq) ? (int)min(hs->count, (unsigned)kSvMaxAdmit) : 0;
-                if (seq != seen_seq) seen_seq = seq;
+                const unsigned seq = seq_early;
+                s_take = 0;
+                if (seq != seen_seq) {
+                    __threadfence_system();  // the batch was written before its sequence number
+                    s_take = (int)min(hs->count, (unsigned)kSvMaxAdmit);
+                    seen_seq = seq;
+                }
             }
             if (threadIdx.x < kSvMaxGraphs * 4) (&ctl->lanes_new[(t + 1) % 3][0][0])[threadIdx.x] = 0ull;
+            if (threadIdx.x < kSvMaxGraphs * 4) (&ctl->lanes_over[(t + 1) % 3][0][0])[threadIdx.x] = 0ull;
+            if (threadIdx.x < kSvMaxGraphs) ctl->qn[(t + 2) % 3][threadIdx.x] = 0;
             __syncthreads();
             const int take = min(s_take, kSvMaxAdmit);
             for (int i = threadIdx.x; i < take; i += kSvThreads) ctl->admit[npar][i] = hs->entries[i];
@@ -526,47 +806,62 @@ __global__ void __launch_bounds__(kSvThreads, 1) serve_kernel(SvArgs a) {
                     for (int w = 0; w < W; ++w) busy |= occ[g][w] != 0ull;
                 const unsigned long long now = sv_globaltimer();
                 if (busy) last_busy = now;
-                ctl->pub[npar][1] = (*(volatile unsigned*)&hs->stop != 0u) ||
+                ctl->pub[npar][1] = (stop_early != 0u) ||
                                     (!busy && (long long)(now - last_busy) > a.idle_ns);
             }
         }
-        if (!sv_barrier(ctl, bar, bar_target, a.spin_limit, ctl->pub[par ^ 1], 2 + kSvMaxGraphs + 1, s_pub)) return;
-        // ---- (4) lanes whose level reached nothing are done (thread 0 of every
-        //      CTA computes the same masks; CTA 0 reports them to the host)
-        if (threadIdx.x == 0) {
-            for (int g = 0; g < a.ngraphs; ++g) {
-                SvGraph* G = &a.graphs[g];
-                for (int w = 0; w < W; ++w) {
-                    if (!occ[g][w]) continue;
-                    const unsigned long long got = sv_ld_relaxed_u64(&ctl->lanes_new[t % 3][g][w]);
-                    unsigned long long started_now = 0ull, over = 0ull;
-                    unsigned long long m = occ[g][w];
-                    while (m) {
-                        const int b = __ffsll((long long)m) - 1;
-                        m &= m - 1;
-                        const int s = w * 64 + b;
-                        const int st = __ldcg(G->lane_start + s);
-                        if (st == t) started_now |= 1ull << b;  // admitted now: has not expanded yet
-                        else if (__ldcg(G->lane_bytes + s) == 2 && t + 1 - st > 32767) over |= 1ull << b;
-                    }
-                    const unsigned long long fin = ((occ[g][w] & ~got) & ~started_now) | over;
-                    if (fin && blockIdx.x == 0) {
-                        unsigned long long f = fin;
-                        while (f) {
-                            const int b = __ffsll((long long)f) - 1;
-                            f &= f - 1;
-                            const int s = w * 64 + b;
-                            const unsigned long long tail = hs->done_tail;
-                            const bool ov = (over >> b) & 1ull;
-                            volatile DoneRec* dst = &hs->done[tail % kSvDoneRing];
-                            dst->token = __ldcg(G->lane_token + s);
-                            dst->levels = ov ? -1 : t - 1 - __ldcg(G->lane_start + s);
-                            dst->status = ov ? DEV_OVERFLOW : DEV_OK;
-                            __threadfence_system();
-                            hs->done_tail = tail + 1;
-                        }
-                    }
-                    occ[g][w] &= ~fin;
+        if (!sv_barrier(ctl, bar, bar_target, a.spin_limit, ctl->pub[par ^ 1], 2 + kSvMaxGraphs + 1, s_pub,
+                        ctl->qn[(t + 1) % 3], kSvMaxGraphs, s_qn))
+            return;
+        // ---- (4) lanes whose level reached nothing, or whose distances no
+        //      longer fit their int16 rows, are done: every CTA updates its
+        //      occupancy the same way; CTA 0 reports them to the host
+        if (threadIdx.x < a.ngraphs * W) {
+            const int g = threadIdx.x / W, w = threadIdx.x % W;
+            const unsigned long long o = occ[g][w];
+            unsigned long long fin = 0ull, ovr = 0ull;
+            if (o) {
+                const unsigned long long got = sv_ld_relaxed_u64(&ctl->lanes_new[t % 3][g][w]);
+                ovr = sv_ld_relaxed_u64(&ctl->lanes_over[t % 3][g][w]) & o;
+                const unsigned long long started_now = na > 0 ? s_adm[g][w] : 0ull;  // not expanded yet
+                fin = (o & ~got & ~started_now) | ovr;
+            }
+            s_fin[threadIdx.x] = fin;
+            s_ovr[threadIdx.x] = ovr;
+            occ[g][w] = o & ~fin;
+        }
+        __syncthreads();
+        if (blockIdx.x == 0) {
+            const int nwords = a.ngraphs * W;
+            if (threadIdx.x == 0) {
+                int acc = 0;
+                for (int i = 0; i < nwords; ++i) {
+                    s_recoff[i] = acc;
+                    acc += __popcll(s_fin[i]);
+                }
+                s_recoff[nwords] = acc;
+            }
+            __syncthreads();
+            if (s_recoff[nwords] > 0) {
+                const unsigned long long tail = s_done_tail;
+                for (int i = threadIdx.x; i < nwords * 64; i += kSvThreads) {
+                    const int wi = i >> 6, b = i & 63;
+                    const unsigned long long fw = s_fin[wi];
+                    if (!((fw >> b) & 1ull)) continue;
+                    const int g = wi / W, s = (wi % W) * 64 + b;
+                    const SvGraph* G = &a.graphs[g];
+                    const bool ov = (s_ovr[wi] >> b) & 1ull;
+                    const unsigned long long r = tail + s_recoff[wi] + __popcll(fw & ((1ull << b) - 1ull));
+                    volatile DoneRec* dst = &hs->done[r % kSvDoneRing];
+                    dst->token = __ldcg(G->lane_token + s);
+                    dst->levels = ov ? -1 : t - 1 - __ldcg(G->lane_start + s);
+                    dst->status = ov ? DEV_OVERFLOW : DEV_OK;
+                }
+                __syncthreads();
+                if (threadIdx.x == 0) {
+                    __threadfence_system();  // records before the tail that publishes them
+                    s_done_tail = tail + s_recoff[nwords];
+                    hs->done_tail = s_done_tail;
                 }
             }
         }
@@ -634,6 +929,7 @@ struct dawn_server {
     std::map<uint64_t, dawn::Request*> reqs;
     std::atomic<bool> stop{false};
     std::thread worker;
+    std::vector<dawn::SvGraph> host_graphs;  // device pointers of each graph's server state
     int fatal = DAWN_OK;
     int device = 0;
 };
@@ -834,6 +1130,19 @@ void worker_main(dawn_server* s) {
     }
 }
 
+void free_graph_state(SvGraph& hg) {
+    for (int p = 0; p < 2; ++p) {
+        cudaFree(hg.V[p]);
+        cudaFree(hg.F[p]);
+        cudaFree(hg.Q[p]);
+        hg.V[p] = nullptr;
+        hg.F[p] = nullptr;
+        hg.Q[p] = nullptr;
+    }
+    cudaFree(hg.VS);
+    hg.VS = nullptr;
+}
+
 void server_release(dawn_server* s) {
     if (!s) return;
     for (auto& kv : s->reqs) {
@@ -842,13 +1151,7 @@ void server_release(dawn_server* s) {
     }
     if (s->kstream) cudaStreamSynchronize(s->kstream);
     if (s->cstream) cudaStreamSynchronize(s->cstream);
-    for (int g = 0; g < (int)s->graphs.size() && s->d_graphs; ++g) {
-        SvGraph hg;
-        if (cudaMemcpy(&hg, s->d_graphs + g, sizeof(SvGraph), cudaMemcpyDeviceToHost) == cudaSuccess) {
-            cudaFree(hg.V[0]);
-            cudaFree(hg.V[1]);
-        }
-    }
+    for (auto& hg : s->host_graphs) free_graph_state(hg);
     if (s->d_graphs) cudaFree(s->d_graphs);
     if (s->d_ctl) cudaFree(s->d_ctl);
     if (s->arena) cudaFree(s->arena);
@@ -864,8 +1167,8 @@ void server_release(dawn_server* s) {
 
 extern "C" {
 
-DAWN_API int dawn_serve_create(const dawn_graph_t* graphs, int ngraphs, size_t mem_budget_bytes, int max_lanes,
-                               dawn_server_t* out) {
+DAWN_API int dawn_serve_create_ex(const dawn_graph_t* graphs, int ngraphs, size_t mem_budget_bytes, int max_lanes,
+                                  const int32_t* modes, dawn_server_t* out) {
     using namespace dawn;
     if (!out) return fail(DAWN_E_INVALID, "out is NULL");
     *out = nullptr;
@@ -873,8 +1176,12 @@ DAWN_API int dawn_serve_create(const dawn_graph_t* graphs, int ngraphs, size_t m
         return fail(DAWN_E_INVALID, "ngraphs = %d: need 1..%d", ngraphs, kSvMaxGraphs);
     if (max_lanes != 64 && max_lanes != 128 && max_lanes != 256)
         return fail(DAWN_E_INVALID, "max_lanes = %d: need 64, 128 or 256", max_lanes);
-    for (int i = 0; i < ngraphs; ++i)
+    for (int i = 0; i < ngraphs; ++i) {
         if (!graphs[i]) return fail(DAWN_E_INVALID, "graphs[%d] is NULL", i);
+        const int md = modes ? modes[i] : DAWN_SERVE_AUTO;
+        if (md != DAWN_SERVE_AUTO && md != DAWN_SERVE_DENSE && md != DAWN_SERVE_FRONTIER)
+            return fail(DAWN_E_INVALID, "modes[%d] = %d: need DAWN_SERVE_AUTO, _DENSE or _FRONTIER", i, md);
+    }
     dawn_server* s = new dawn_server();
     s->lanes = max_lanes;
     s->W = max_lanes / 64;
@@ -897,22 +1204,47 @@ DAWN_API int dawn_serve_create(const dawn_graph_t* graphs, int ngraphs, size_t m
     }
     std::memset(s->hs, 0, sizeof(HostShared));
     s->free_blocks[0] = s->budget;
-    std::vector<SvGraph> hg((size_t)ngraphs);
+    std::vector<SvGraph>& hg = s->host_graphs;
+    hg.resize((size_t)ngraphs);
     for (int i = 0; i < ngraphs; ++i) {
         std::memset(&hg[i], 0, sizeof(SvGraph));
-        hg[i].in_ptr = graphs[i]->in_ptr;
-        hg[i].in_idx = graphs[i]->in_idx;
-        hg[i].excl = graphs[i]->excl;
-        hg[i].n = graphs[i]->n;
-        const size_t vb = sizeof(uint64_t) * (size_t)graphs[i]->n * s->W;
-        if ((e = cudaMalloc((void**)&hg[i].V[0], vb)) != cudaSuccess ||
-            (e = cudaMalloc((void**)&hg[i].V[1], vb)) != cudaSuccess ||
-            (e = cudaMemset(hg[i].V[0], 0, vb)) != cudaSuccess || (e = cudaMemset(hg[i].V[1], 0, vb)) != cudaSuccess) {
-            for (int j = 0; j <= i; ++j) { cudaFree(hg[j].V[0]); cudaFree(hg[j].V[1]); }
-            cudaFree(s->d_graphs);
-            s->d_graphs = nullptr;
+        const dawn_graph* gi = graphs[i];
+        hg[i].in_ptr = gi->in_ptr;
+        hg[i].in_idx = gi->in_idx;
+        hg[i].excl = gi->excl;
+        hg[i].row_ptr = gi->row_ptr;
+        hg[i].col_idx = gi->col_idx;
+        hg[i].n = gi->n;
+        const int md = modes ? modes[i] : DAWN_SERVE_AUTO;
+        // auto: low average degree (lattices, road-like graphs) means many
+        // levels with small frontiers, where a full pass per level is waste
+        hg[i].frontier = md == DAWN_SERVE_FRONTIER || (md == DAWN_SERVE_AUTO && gi->m < 8 * (int64_t)gi->n);
+        if (hg[i].frontier && (int64_t)gi->n * s->W >= ((int64_t)1 << 32)) {
+            if (md == DAWN_SERVE_FRONTIER) {
+                server_release(s);
+                return fail(DAWN_E_INVALID, "graphs[%d]: the frontier step needs n * max_lanes / 64 < 2^32", i);
+            }
+            hg[i].frontier = 0;
+        }
+        const size_t nk = (size_t)gi->n * s->W;
+        const size_t vb = sizeof(uint64_t) * nk;
+        if (hg[i].frontier) {
+            e = cudaMalloc((void**)&hg[i].VS, vb);
+            if (e == cudaSuccess) e = cudaMemset(hg[i].VS, 0, vb);
+            for (int p = 0; p < 2 && e == cudaSuccess; ++p) {
+                e = cudaMalloc((void**)&hg[i].F[p], vb);
+                if (e == cudaSuccess) e = cudaMemset(hg[i].F[p], 0, vb);
+                if (e == cudaSuccess) e = cudaMalloc((void**)&hg[i].Q[p], sizeof(uint32_t) * nk);
+            }
+        } else {
+            for (int p = 0; p < 2 && e == cudaSuccess; ++p) {
+                e = cudaMalloc((void**)&hg[i].V[p], vb);
+                if (e == cudaSuccess) e = cudaMemset(hg[i].V[p], 0, vb);
+            }
+        }
+        if (e != cudaSuccess) {
             server_release(s);
-            return cuda_fail(e, "dawn_serve_create (visited words)", __FILE__, __LINE__);
+            return cuda_fail(e, "dawn_serve_create (per-graph state)", __FILE__, __LINE__);
         }
         std::vector<int> fl;
         for (int l = max_lanes - 1; l >= 0; --l) fl.push_back(l);
@@ -926,6 +1258,11 @@ DAWN_API int dawn_serve_create(const dawn_graph_t* graphs, int ngraphs, size_t m
     s->worker = std::thread(worker_main, s);
     *out = s;
     return DAWN_OK;
+}
+
+DAWN_API int dawn_serve_create(const dawn_graph_t* graphs, int ngraphs, size_t mem_budget_bytes, int max_lanes,
+                               dawn_server_t* out) {
+    return dawn_serve_create_ex(graphs, ngraphs, mem_budget_bytes, max_lanes, nullptr, out);
 }
 
 DAWN_API int dawn_serve_submit(dawn_server_t s, int graph_idx, const int32_t* sources, int32_t k, int dist_bytes,

@@ -40,6 +40,10 @@ DAWN_REQ_RUNNING = 1
 DAWN_REQ_DONE = 2
 DAWN_REQ_FAILED = 3
 
+DAWN_SERVE_AUTO = 0
+DAWN_SERVE_DENSE = 1
+DAWN_SERVE_FRONTIER = 2
+
 _NAMES = {1: "DAWN_E_INVALID", 2: "DAWN_E_NOMEM", 3: "DAWN_E_OVERFLOW", 4: "DAWN_E_TIMEOUT",
           5: "DAWN_E_CUDA", 6: "DAWN_E_STATE"}
 
@@ -95,6 +99,7 @@ _SIGNATURES = {
     "dawn_autotune": [_vp, _vp, _i32, _vp, _vp],
     "dawn_set_tuning": [_vp, _vp],
     "dawn_serve_create": [_vp, ctypes.c_int, _sz, ctypes.c_int, ctypes.POINTER(_vp)],
+    "dawn_serve_create_ex": [_vp, ctypes.c_int, _sz, ctypes.c_int, _vp, ctypes.POINTER(_vp)],
     "dawn_serve_submit": [_vp, ctypes.c_int, _vp, _i32, ctypes.c_int, _vp, ctypes.POINTER(_u64)],
     "dawn_serve_poll": [_vp, _u64, ctypes.POINTER(ctypes.c_int)],
     "dawn_serve_times": [_vp, _u64, _vp, _vp],
@@ -278,6 +283,17 @@ def dawn_serve_create(graphs: list[int], mem_budget_bytes: int = 0, max_lanes: i
     arr = (_vp * len(graphs))(*graphs)
     h = _vp()
     _check(load().dawn_serve_create(arr, len(graphs), mem_budget_bytes, max_lanes, ctypes.byref(h)))
+    return h.value
+
+
+def dawn_serve_create_ex(graphs: list[int], mem_budget_bytes: int = 0, max_lanes: int = 256,
+                         modes: list[int] | None = None) -> int:
+    """modes: one DAWN_SERVE_* per graph, or None for all DAWN_SERVE_AUTO."""
+    arr = (_vp * len(graphs))(*graphs)
+    marr = (_i32 * len(graphs))(*modes) if modes is not None else None
+    h = _vp()
+    _check(load().dawn_serve_create_ex(arr, len(graphs), mem_budget_bytes, max_lanes,
+                                       ctypes.cast(marr, _vp) if marr is not None else None, ctypes.byref(h)))
     return h.value
 
 

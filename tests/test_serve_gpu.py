@@ -43,8 +43,16 @@ def wait_done(dawn, s, rid, timeout=60.0):
     raise AssertionError(f"request {rid} not done after {timeout} s")
 
 
-def test_alone_and_in_the_mix(dawn, graphs, handles):
-    s = dawn.dawn_serve_create(handles, 0, 256)
+@pytest.mark.parametrize("modes", ["auto", "dense", "frontier", "mixed"])
+def test_alone_and_in_the_mix(dawn, graphs, handles, modes):
+    """The same stream under each per-graph step: the dense pull, the frontier
+    push, the automatic choice, and the two alternating across graphs."""
+    if modes == "auto":
+        s = dawn.dawn_serve_create(handles, 0, 256)
+    else:
+        pick = {"dense": [dawn.DAWN_SERVE_DENSE] * 4, "frontier": [dawn.DAWN_SERVE_FRONTIER] * 4,
+                "mixed": [dawn.DAWN_SERVE_FRONTIER, dawn.DAWN_SERVE_DENSE] * 2}[modes]
+        s = dawn.dawn_serve_create_ex(handles, 0, 256, pick)
     try:
         probe_srcs = np.array([3, 17, 200, 511, 1000], dtype=np.int32)
         alone = np.full((5, graphs[0].n), 99, dtype=np.int16)
@@ -104,12 +112,16 @@ def test_memory_budget_admission_and_device_outputs(dawn, graphs, handles):
         dawn.dawn_serve_destroy(s)
 
 
-def test_overflow_and_bad_arguments(dawn):
+@pytest.mark.parametrize("mode", ["dense", "frontier"])
+def test_overflow_and_bad_arguments(dawn, mode):
+    """A 40,000-vertex path: levels past 32767 overflow an int16 row (the
+    request fails with DAWN_E_OVERFLOW), the int32 request on the same path
+    completes exactly."""
     n = 40000
     s_ = np.arange(n - 1)
     path = gg.from_arcs(n, np.r_[s_, s_ + 1], np.r_[s_ + 1, s_], symmetric=True)
     h = dawn.dawn_graph_upload(path.row_ptr, path.col_idx, flags=dawn.DAWN_SYMMETRIC)
-    s = dawn.dawn_serve_create([h], 0, 64)
+    s = dawn.dawn_serve_create_ex([h], 0, 64, [dawn.DAWN_SERVE_DENSE if mode == "dense" else dawn.DAWN_SERVE_FRONTIER])
     try:
         out16 = np.zeros((1, n), dtype=np.int16)
         r16 = dawn.dawn_serve_submit(s, 0, np.array([0], dtype=np.int32), dist_bytes=2, dist_out=out16)
@@ -136,3 +148,42 @@ def test_overflow_and_bad_arguments(dawn):
         dawn.dawn_graph_free(h)
     with pytest.raises(dawn.DawnError):
         dawn.dawn_serve_create([h], 0, 100)
+
+
+@pytest.mark.parametrize("mode", ["dense", "frontier"])
+def test_lane_reuse_on_long_lattice(dawn, mode):
+    """64 lanes, many more sources than lanes on a high-diameter lattice and a
+    directed graph: every lane is re-admitted many times, so stale visited
+    bits of finished lanes must never leak into a new lane's search."""
+    lat = gg.lattice(96, 96, 0.25, seed=8)
+    dg = gg.rmat(11, seed=31, symmetrise=False)
+    hs = [dawn.dawn_graph_upload(lat.row_ptr, lat.col_idx, flags=dawn.DAWN_SYMMETRIC),
+          dawn.dawn_graph_upload(dg.row_ptr, dg.col_idx, flags=dawn.DAWN_DIRECTED)]
+    md = dawn.DAWN_SERVE_DENSE if mode == "dense" else dawn.DAWN_SERVE_FRONTIER
+    s = dawn.dawn_serve_create_ex(hs, 0, 64, [md, md])
+    try:
+        rng = np.random.default_rng(11)
+        reqs = []
+        for i in range(40):
+            gi = i % 2
+            g = (lat, dg)[gi]
+            k = int(rng.integers(1, 40))
+            srcs = rng.integers(0, g.n, k).astype(np.int32)
+            out = np.full((k, g.n), 99, dtype=np.int32)
+            reqs.append((dawn.dawn_serve_submit(s, gi, srcs, dist_bytes=4, dist_out=out), g, srcs, out))
+            if i % 8 == 7:
+                time.sleep(0.003)
+        dawn.dawn_serve_drain(s, 120000)
+        for rid, g, srcs, out in reqs:
+            assert dawn.dawn_serve_poll(s, rid) == dawn.DAWN_REQ_DONE
+            np.testing.assert_array_equal(out, want_rows(g, srcs), err_msg=f"request {rid}")
+    finally:
+        dawn.dawn_serve_destroy(s)
+        for h in hs:
+            dawn.dawn_graph_free(h)
+
+
+def test_bad_serve_modes(dawn, handles):
+    with pytest.raises(dawn.DawnError) as ei:
+        dawn.dawn_serve_create_ex(handles, 0, 64, [0, 1, 2, 3])
+    assert ei.value.code == dawn.DAWN_E_INVALID
