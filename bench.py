@@ -257,6 +257,49 @@ def bench_lattice(dawn, torch, flush, nsrc=16):
             "l2": "flushed between sources"}
 
 
+def bench_tree(dawn, torch, flush, g, srcs, peak):
+    """Shortest-path tree on the headline graph and sources: microseconds per
+    source of dawn_sssp_tree_async (level loop + parent pass) against the
+    plain level loop, L2 flushed between sources.  A full parent pass reads
+    every in-arc of every reached vertex: 8 E_r (in_idx + the gathered dist)
+    + 8 V_r (in_ptr pairs) + 8 n (dist read, parent write) bytes; with rows in
+    ascending order it stops at the first qualifying arc, so that figure is
+    an upper bound of the bytes it moves and the rate below is an effective
+    rate against it, not a roofline fraction."""
+    stream = torch.cuda.current_stream()
+    h = dawn.dawn_graph_upload(g.row_ptr, g.col_idx, flags=dawn.DAWN_SYMMETRIC, stream=stream)
+    dist = torch.empty(g.n, dtype=torch.int32, device="cuda")
+    par = torch.empty(g.n, dtype=torch.int32, device="cuda")
+    stats = torch.zeros((len(srcs), dawn.STATS_WORDS), dtype=torch.int64, device="cuda")
+    deg = g.out_degree()
+    times = {}
+    for kind in ("sssp", "tree", "sssp", "tree"):  # second round is the measured one
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in srcs]
+        for i, sv in enumerate(srcs):
+            _flush(flush, i)
+            ev[i][0].record(stream)
+            if kind == "tree":
+                dawn.dawn_sssp_tree_async(h, int(sv), dist, par, stream)
+            else:
+                dawn.dawn_sssp_async(h, int(sv), dist, None, stats[i], stream)
+            ev[i][1].record(stream)
+        dawn.dawn_graph_sync(h, stream)
+        times[kind] = [a.elapsed_time(b) * 1e3 for a, b in ev]
+    st = [dawn.stats_from_words(r) for r in stats.cpu().numpy()]
+    dawn.dawn_graph_free(h)
+    t_sssp = statistics.median(times["sssp"])
+    t_tree = statistics.median(times["tree"])
+    e_r = statistics.median(x["edges"] for x in st)
+    v_r = statistics.median(x["reached"] for x in st)
+    pass_us = max(t_tree - t_sssp, 1e-9)
+    balg = 8 * e_r + 8 * v_r + 8 * g.n
+    return {"workload": "rmat20_sssp_tree_64src", "us_per_source_tree": t_tree, "us_per_source_sssp": t_sssp,
+            "parent_pass_us": pass_us, "parent_pass_full_scan_bytes": balg,
+            "parent_pass_effective_gbs_vs_full_scan": balg / (pass_us * 1e-6) / 1e9,
+            "measured_hbm_gbs": peak, "l2": "flushed between sources",
+            "tie_break": "smallest-id predecessor", "early_stop": "rows in ascending order"}
+
+
 def bench_batched(dawn, torch, flush, plain_sample=4096, k=0, lanes_list=(64, 128, 256)):
     """RMAT scale 16 (seed 4), all 65,536 vertices as sources, int16 distance
     block of each pass kept on the device and reduced to eccentricity and
@@ -508,7 +551,8 @@ def run_gpu(args):
     }
     if world == 1 and not args.no_secondary:
         line["secondary"] = {"lattice": bench_lattice(dawn, torch, flush),
-                             "batched": bench_batched(dawn, torch, flush)}
+                             "batched": bench_batched(dawn, torch, flush),
+                             "tree": bench_tree(dawn, torch, flush, g, srcs, peak)}
         del flush
         torch.cuda.empty_cache()
         line["secondary"]["serving"] = bench_serving(dawn, torch, nreq=args.serve_requests)
@@ -528,6 +572,9 @@ def run_one(args):
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.int32, device="cuda")
     if args.workload == "lattice":
         out = bench_lattice(dawn, torch, flush)
+    elif args.workload == "tree":
+        g, srcs = build_workload()
+        out = bench_tree(dawn, torch, flush, g, srcs, measured_peaks()[0])
     elif args.workload == "batched":
         out = bench_batched(dawn, torch, flush, k=args.batched_k, lanes_list=(args.batched_lanes,) if args.batched_lanes else (64, 128, 256))
     else:
@@ -550,7 +597,7 @@ def main():
                     help="use only the first N of the 64 sources (small profiling runs; not a bench value)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end host-buffer pass")
     ap.add_argument("--serve-requests", type=int, default=48, help="requests per arrival rate in the serving mix")
-    ap.add_argument("--workload", choices=["all", "lattice", "batched", "serving"], default="all",
+    ap.add_argument("--workload", choices=["all", "lattice", "batched", "serving", "tree"], default="all",
                     help="run one secondary workload alone and print its figures (profiling runs; not a bench line)")
     ap.add_argument("--batched-k", type=int, default=0, help="with --workload batched: sources (0 = all)")
     ap.add_argument("--batched-lanes", type=int, default=0, help="with --workload batched: one lane width")

@@ -163,6 +163,26 @@ DAWN_API int dawn_sssp_ex(dawn_graph_t g, int32_t src, int32_t* dist, const dawn
 DAWN_API int dawn_sssp_async(dawn_graph_t g, int32_t src, int32_t* dist_dev, const dawn_sssp_opts* opts,
                              dawn_sssp_stats* stats_dev, void* stream);
 
+/*
+ * Shortest-path tree (Fact 1 / Thm 1: a vertex first reached at level d has
+ * an in-neighbour at level d - 1 on a shortest path).  Runs the level loop of
+ * dawn_sssp (DAWN_MODE_AUTO), then one pass over the in-adjacency:
+ *   parent[v] = min { u : (u, v) is an arc and dist[u] = dist[v] - 1 }
+ * for dist[v] > 0, and -1 for the source and for unreached vertices.  Several
+ * predecessors can qualify; the smallest id is the tie-break that makes the
+ * tree unique.  Following parent from any reached v visits dist[v] arcs and
+ * ends at src.
+ *   dist, parent  host or device int32[n], caller-owned (written; synchronous).
+ * Cost: the level loop plus a read of every in-arc of every reached vertex.
+ */
+DAWN_API int dawn_sssp_tree(dawn_graph_t g, int32_t src, int32_t* dist, int32_t* parent, void* stream);
+
+/* Stream-ordered dawn_sssp_tree (no synchronization): dist_dev and parent_dev
+ * are device int32[n]; errors of the device wait are reported by
+ * dawn_graph_sync. */
+DAWN_API int dawn_sssp_tree_async(dawn_graph_t g, int32_t src, int32_t* dist_dev, int32_t* parent_dev,
+                                  void* stream);
+
 /* Synchronize `stream` and return (then clear) the sticky device status of g:
  * DAWN_OK, DAWN_E_TIMEOUT or DAWN_E_OVERFLOW. */
 DAWN_API int dawn_graph_sync(dawn_graph_t g, void* stream);

@@ -66,6 +66,7 @@ def _load():
             "oracle_certificate": [i32, vp, vp, i32, vp, vp],
             "oracle_wcc": [i32, vp, vp, vp],
             "oracle_msbfs": [i32, vp, vp, vp, i32, vp, vp, vp, vp],
+            "oracle_parents": [i32, vp, vp, vp, vp],
         }
         for name, args in sig.items():
             f = getattr(lib, name)
@@ -156,6 +157,16 @@ def wcc(row_ptr, col_idx):
     if _load().oracle_wcc(rp.size - 1, _p(rp), _p(ci), _p(lab)) != 0:
         raise MemoryError("oracle_wcc")
     return lab
+
+
+def parents(row_ptr, col_idx, dist):
+    """Smallest-id shortest-path tree for the exact distances `dist` (Fact 1)."""
+    rp, ci = _csr(row_ptr, col_idx)
+    d = np.ascontiguousarray(dist, dtype=np.int32)
+    par = np.empty(rp.size - 1, dtype=np.int32)
+    if _load().oracle_parents(rp.size - 1, _p(rp), _p(ci), _p(d), _p(par)) != 0:
+        raise ValueError("oracle_parents: bad input")
+    return par
 
 
 def msbfs(row_ptr, col_idx, sources, keep_dist: bool = True):

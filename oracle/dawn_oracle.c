@@ -31,6 +31,9 @@
  *   oracle_certificate   O(n+m) check that a distance vector is the exact
  *                        unweighted distance from src (Thm 1 with Fact 1).
  *   oracle_wcc           weakly connected component labels (union-find).
+ *   oracle_parents       shortest-path tree from exact distances (Fact 1 /
+ *                        Thm 1: a vertex at level d > 0 is entered from one at
+ *                        level d - 1), smallest-id tie-break.
  *   oracle_msbfs         APSP as SOVM from each listed source (Sec. 3.3,
  *                        "APSP repeats the SSSP per source"), plus per-source
  *                        eccentricity (largest finite distance, Table 1's
@@ -332,5 +335,26 @@ int oracle_msbfs(int32_t n, const int32_t* row_ptr, const int32_t* col_idx,
         if (dist_block) memcpy(dist_block + (size_t)s * n, dist, (size_t)n * sizeof(int32_t));
     }
     free(dist);
+    return 0;
+}
+
+/*
+ * Shortest-path tree (Fact 1 / Thm 1).  Given the exact distances from a
+ * source, a vertex v at distance d > 0 is entered on some shortest path from
+ * every u with an arc u->v and dist[u] = d - 1.  parent[v] is the smallest
+ * such u (the tie-break that makes the tree unique); -1 for the source and
+ * for unreached vertices.  Every CSR arc is examined, in CSR order.
+ */
+int oracle_parents(int32_t n, const int32_t* row_ptr, const int32_t* col_idx,
+                   const int32_t* dist, int32_t* parent) {
+    if (n < 0) return -1;
+    for (int32_t v = 0; v < n; ++v) parent[v] = -1;
+    for (int32_t u = 0; u < n; ++u) {
+        if (dist[u] < 0) continue;
+        for (int32_t j = row_ptr[u]; j < row_ptr[u + 1]; ++j) {
+            const int32_t v = col_idx[j];
+            if (dist[v] == dist[u] + 1 && (parent[v] < 0 || u < parent[v])) parent[v] = u;
+        }
+    }
     return 0;
 }

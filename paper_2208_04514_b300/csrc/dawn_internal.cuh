@@ -80,6 +80,7 @@ struct dawn_graph {
     int32_t* in_ptr = nullptr;        // CSC (== CSR when symmetric), device
     int32_t* in_idx = nullptr;
     uint32_t* excl = nullptr;         // bit v set: v has no in-arc (or v >= n)
+    int32_t in_sorted = 0;            // 1: every in-adjacency row is in ascending order
     // single-source work buffers
     uint32_t* vis[2] = {nullptr, nullptr};
     int2* queue[2] = {nullptr, nullptr};        // frontier entries {first arc, arc count}

@@ -132,6 +132,21 @@ __global__ void csc_scatter_kernel(const int32_t* __restrict__ rp, const int32_t
 
 // excl bit v = (v >= n) or v has no in-arc: such a vertex is never reached
 // from another vertex, so the pull step never scans it.
+// flag = 1 when some in-adjacency row is not in ascending order (one warp per row).
+__global__ void unsorted_rows_kernel(const int32_t* __restrict__ ptr, const int32_t* __restrict__ idx, int32_t n,
+                                     int* flag) {
+    const int lane = threadIdx.x & 31;
+    const long long warps = (long long)gridDim.x * (blockDim.x / 32);
+    for (long long v = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / 32; v < n; v += warps) {
+        const int ib = ptr[v], ie = ptr[v + 1];
+        bool bad = false;
+        for (int j = ib + lane; j + 1 < ie; j += 32) bad |= idx[j] > idx[j + 1];
+        if (__any_sync(0xffffffffu, bad)) {
+            if (lane == 0) *flag = 1;
+        }
+    }
+}
+
 __global__ void excl_kernel(const int32_t* __restrict__ in_ptr, int32_t n, int32_t nwords, uint32_t* excl) {
     const int stride = gridDim.x * blockDim.x;
     for (int w = blockIdx.x * blockDim.x + threadIdx.x; w < nwords; w += stride) {
@@ -288,8 +303,22 @@ int upload(const int32_t* row_ptr, const int32_t* col_idx, int32_t n, int64_t m,
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaMemsetAsync(g->ctl, 0, sizeof(Ctl), st);
+    // in-adjacency rows in ascending order let the tree pass stop at the first
+    // qualifying predecessor
+    int* unsorted = nullptr;
+    if (e == cudaSuccess) e = cudaMallocAsync((void**)&unsorted, sizeof(int), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(unsorted, 0, sizeof(int), st);
+    if (e == cudaSuccess && m > 0) {
+        unsorted_rows_kernel<<<grid_for((int64_t)n * 32, g->sms), kThreads, 0, st>>>(g->in_ptr, g->in_idx, n,
+                                                                                      unsorted);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(g->status_host, unsorted, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (unsorted) cudaFreeAsync(unsorted, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) { release(g); return cuda_fail(e, "graph setup", __FILE__, __LINE__); }
+    g->in_sorted = *g->status_host == 0;
+    *g->status_host = 0;
     int rc = sssp_occupancy(g);
     if (rc != DAWN_OK) { release(g); return rc; }
     *out = g;

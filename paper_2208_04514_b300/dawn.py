@@ -94,6 +94,8 @@ _SIGNATURES = {
     "dawn_sssp_ex": [_vp, _i32, _vp, _vp, _vp, _vp],
     "dawn_sssp_async": [_vp, _i32, _vp, _vp, _vp, _vp],
     "dawn_sssp_noalloc": [_vp, _vp, _i32, _i64, _i32, _vp, _vp],
+    "dawn_sssp_tree": [_vp, _i32, _vp, _vp, _vp],
+    "dawn_sssp_tree_async": [_vp, _i32, _vp, _vp, _vp],
     "dawn_msbfs": [_vp, _vp, _i32, _vp, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp],
     "dawn_msbfs_ex": [_vp, _vp, _i32, _vp, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp, _vp],
     "dawn_autotune": [_vp, _vp, _i32, _vp, _vp],
@@ -214,6 +216,16 @@ def dawn_sssp_ex(g: int, src: int, dist, opts: dict | None = None, stream=None) 
     _check(load().dawn_sssp_ex(g, int(src), _ptr(dist), ctypes.byref(o) if o else None,
                                ctypes.byref(st), _stream(stream)))
     return st.as_dict()
+
+
+def dawn_sssp_tree(g: int, src: int, dist, parent, stream=None) -> None:
+    """Distances and the min-id shortest-path tree (host or device int32[n] each)."""
+    _check(load().dawn_sssp_tree(g, int(src), _ptr(dist), _ptr(parent), _stream(stream)))
+
+
+def dawn_sssp_tree_async(g: int, src: int, dist_dev, parent_dev, stream=None) -> None:
+    """Enqueue dawn_sssp_tree on the stream (device outputs, no synchronization)."""
+    _check(load().dawn_sssp_tree_async(g, int(src), _ptr(dist_dev), _ptr(parent_dev), _stream(stream)))
 
 
 def dawn_sssp_async(g: int, src: int, dist_dev, opts: dict | None = None, stats_dev=None, stream=None) -> None:

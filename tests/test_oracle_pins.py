@@ -299,3 +299,118 @@ def parse_golden(path):
         elif key.startswith("dist"):
             cases.append((int(key.split()[1]), np.array(vals)))
     return n, arcs, cases
+
+
+# ------------------------------------------------- shortest-path tree pins --
+
+def lattice_parent_closed_form(w, src):
+    """Full w x w lattice (id = r*w + c): the in-neighbours one step closer to
+    src are the ones stepping toward it; the smallest id among them is
+    id - w (from above) if r > sr, else id - 1 if c > sc, else id + 1 if
+    c < sc, else id + w."""
+    ids = np.arange(w * w)
+    r, c = np.divmod(ids, w)
+    sr, sc = divmod(src, w)
+    want = np.where(r > sr, ids - w, np.where(c > sc, ids - 1, np.where(c < sc, ids + 1, ids + w)))
+    want[src] = -1
+    return want
+
+
+def test_tree_closed_forms():
+    # undirected path: the neighbour toward the source
+    n = 12
+    g = path_graph(n, directed=False)
+    for s in (0, 5, n - 1):
+        d = oracle.sssp_sovm(g.row_ptr, g.col_idx, s)
+        v = np.arange(n)
+        want = np.where(v > s, v - 1, v + 1)
+        want[s] = -1
+        np.testing.assert_array_equal(oracle.parents(g.row_ptr, g.col_idx, d), want)
+    # star: from the centre every leaf hangs on 0; from a leaf, 0 hangs on it
+    k = 9
+    leaves = np.arange(1, k)
+    star = gg.from_arcs(k, np.r_[np.zeros(k - 1, int), leaves], np.r_[leaves, np.zeros(k - 1, int)], symmetric=True)
+    d = oracle.sssp_sovm(star.row_ptr, star.col_idx, 0)
+    np.testing.assert_array_equal(oracle.parents(star.row_ptr, star.col_idx, d), np.r_[-1, np.zeros(k - 1, int)])
+    d = oracle.sssp_sovm(star.row_ptr, star.col_idx, 4)
+    want = np.zeros(k, int)
+    want[0], want[4] = 4, -1
+    np.testing.assert_array_equal(oracle.parents(star.row_ptr, star.col_idx, d), want)
+    # complete graph: everything hangs on the source
+    i, j = np.nonzero(~np.eye(k, dtype=bool))
+    comp = gg.from_arcs(k, i, j, symmetric=True)
+    d = oracle.sssp_sovm(comp.row_ptr, comp.col_idx, 6)
+    want = np.full(k, 6)
+    want[6] = -1
+    np.testing.assert_array_equal(oracle.parents(comp.row_ptr, comp.col_idx, d), want)
+    # binary heap tree from the root: (v - 1) // 2
+    m = 60
+    child = np.arange(1, m)
+    t = gg.from_arcs(m, np.r_[(child - 1) // 2, child], np.r_[child, (child - 1) // 2], symmetric=True)
+    d = oracle.sssp_sovm(t.row_ptr, t.col_idx, 0)
+    np.testing.assert_array_equal(oracle.parents(t.row_ptr, t.col_idx, d), np.r_[-1, (child - 1) // 2])
+    # bond-complete lattice, several sources (the tie-break matters everywhere off the axes)
+    w = 11
+    lat = gg.lattice(w, w, p_delete=0.0, seed=0)
+    for s in (0, w * w - 1, 3 * w + 7, 5 * w + 5):
+        d = oracle.sssp_sovm(lat.row_ptr, lat.col_idx, s)
+        np.testing.assert_array_equal(oracle.parents(lat.row_ptr, lat.col_idx, d), lattice_parent_closed_form(w, s))
+
+
+def brute_force_tree(g, s):
+    """Enumerate every simple path from s (tiny graphs): for each v, the least
+    length of a path s -> v and the set of vertices right before v on the
+    paths of that length; the tree takes the smallest of that set."""
+    adj = [sorted(set(g.col_idx[g.row_ptr[u]:g.row_ptr[u + 1]].tolist())) for u in range(g.n)]
+    best = {s: (0, set())}
+
+    def walk(path, on):
+        u = path[-1]
+        for v in adj[u]:
+            if v in on:
+                continue
+            length = len(path)
+            if v not in best or length < best[v][0]:
+                best[v] = (length, {u})
+            elif length == best[v][0]:
+                best[v][1].add(u)
+            on.add(v)
+            path.append(v)
+            walk(path, on)
+            path.pop()
+            on.discard(v)
+
+    walk([s], {s})
+    par = np.full(g.n, -1)
+    for v, (_, pre) in best.items():
+        if pre:
+            par[v] = min(pre)
+    return par
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_tree_vs_path_enumeration(seed):
+    rng = np.random.default_rng(900 + seed)
+    g = random_digraph(900 + seed, n=int(rng.integers(2, 9)), p=float(rng.uniform(0.15, 0.5)))
+    for s in range(g.n):
+        d = oracle.sssp_sovm(g.row_ptr, g.col_idx, s)
+        np.testing.assert_array_equal(oracle.parents(g.row_ptr, g.col_idx, d), brute_force_tree(g, s),
+                                      err_msg=f"seed {seed} source {s}")
+
+
+def test_tree_walks_back_to_source():
+    """Following parent from any reached vertex takes dist[v] arcs and ends at
+    the source (on a directed ER graph and an RMAT graph)."""
+    for g in (gg.erdos_renyi(1024, 8.0, seed=1), gg.rmat(10, seed=3, symmetrise=False)):
+        arcs = set(zip(np.repeat(np.arange(g.n), np.diff(g.row_ptr)).tolist(), g.col_idx.tolist()))
+        for s in (0, 17, 400):
+            d = oracle.sssp_sovm(g.row_ptr, g.col_idx, s)
+            par = oracle.parents(g.row_ptr, g.col_idx, d)
+            assert par[s] == -1 and (par[d < 0] == -1).all()
+            for v in np.nonzero(d > 0)[0][::7]:
+                x, steps = int(v), 0
+                while x != s:
+                    p = int(par[x])
+                    assert (p, x) in arcs
+                    x, steps = p, steps + 1
+                assert steps == d[v]
