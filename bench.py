@@ -345,6 +345,31 @@ def bench_batched(dawn, torch, flush, plain_sample=4096, k=0, lanes_list=(64, 12
     return out
 
 
+def bench_centrality(dawn, torch, flush, lanes=256):
+    """RMAT scale 16 (seed 4), all 65,536 sources: dawn_centrality (ecc,
+    distance sum, reached, closeness, harmonic per source, and the diameter /
+    radius summary) with no distance rows stored, against dawn_msbfs_ex with
+    its int16 rows, same lanes."""
+    from paper_2208_04514_b300 import graphgen as gg
+    g = gg.rmat(16, seed=4)
+    n = g.n
+    stream = torch.cuda.current_stream()
+    h = dawn.dawn_graph_upload(g.row_ptr, g.col_idx, flags=dawn.DAWN_SYMMETRIC, stream=stream)
+    srcs = torch.arange(n, dtype=torch.int32, device="cuda")
+    arrs = [torch.zeros(n, dtype=dt, device="cuda") for dt in (torch.int32, torch.int64, torch.int32,
+                                                                   torch.float64, torch.float64)]
+    dawn.dawn_centrality(h, srcs, n, *arrs, {"lanes": lanes})  # warm-up
+    _flush(flush, 3)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    summ = dawn.dawn_centrality(h, srcs, n, *arrs, {"lanes": lanes})
+    t = time.perf_counter() - t0
+    dawn.dawn_graph_free(h)
+    return {"workload": "rmat16_all_sources_centrality", "lanes": lanes, "sources_per_s": n / t, "ms": 1e3 * t,
+            "summary": summ, "outputs": "ecc, dsum, reached, closeness, harmonic (device); summary",
+            "timing": "wall clock of the synchronous call (inputs on the device), L2 flushed before"}
+
+
 def bench_serving(dawn, torch, nreq=48, seed=6):
     """Continuous-batching server on 8 resident graphs: RMAT scales 14, 16, 18,
     20, 22 (edge factor 16, symmetrised) and 1024^2, 2048^2, 4096^2 lattices
@@ -552,7 +577,8 @@ def run_gpu(args):
     if world == 1 and not args.no_secondary:
         line["secondary"] = {"lattice": bench_lattice(dawn, torch, flush),
                              "batched": bench_batched(dawn, torch, flush),
-                             "tree": bench_tree(dawn, torch, flush, g, srcs, peak)}
+                             "tree": bench_tree(dawn, torch, flush, g, srcs, peak),
+                             "centrality": bench_centrality(dawn, torch, flush)}
         del flush
         torch.cuda.empty_cache()
         line["secondary"]["serving"] = bench_serving(dawn, torch, nreq=args.serve_requests)
@@ -572,6 +598,8 @@ def run_one(args):
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.int32, device="cuda")
     if args.workload == "lattice":
         out = bench_lattice(dawn, torch, flush)
+    elif args.workload == "centrality":
+        out = bench_centrality(dawn, torch, flush)
     elif args.workload == "tree":
         g, srcs = build_workload()
         out = bench_tree(dawn, torch, flush, g, srcs, measured_peaks()[0])
@@ -597,7 +625,7 @@ def main():
                     help="use only the first N of the 64 sources (small profiling runs; not a bench value)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end host-buffer pass")
     ap.add_argument("--serve-requests", type=int, default=48, help="requests per arrival rate in the serving mix")
-    ap.add_argument("--workload", choices=["all", "lattice", "batched", "serving", "tree"], default="all",
+    ap.add_argument("--workload", choices=["all", "lattice", "batched", "serving", "tree", "centrality"], default="all",
                     help="run one secondary workload alone and print its figures (profiling runs; not a bench line)")
     ap.add_argument("--batched-k", type=int, default=0, help="with --workload batched: sources (0 = all)")
     ap.add_argument("--batched-lanes", type=int, default=0, help="with --workload batched: one lane width")

@@ -275,6 +275,33 @@ DAWN_API int dawn_msbfs_ex(dawn_graph_t g, const int32_t* sources, int32_t k, vo
                            int dist_bytes, int layout, int32_t* ecc, int64_t* dsum, int32_t* reached,
                            const dawn_msbfs_opts* opts, void* stream);
 
+/* Whole-run figures of dawn_centrality over the listed sources. */
+typedef struct {
+    int32_t diameter;    /* largest finite distance from a listed source (max ecc); the graph's
+                            diameter when every vertex is listed */
+    int32_t radius;      /* smallest ecc among listed sources that reach another vertex; -1 if none */
+    int64_t pairs;       /* ordered pairs (s, v), v != s, v reached from a listed s */
+    int64_t dist_total;  /* sum of their distances */
+} dawn_apsp_summary;
+
+/*
+ * Centrality from the batched level loop (Sec. 3.3's APSP, one bit lane per
+ * source, no distance rows written).  Per listed source s, all optional
+ * (NULL = not wanted; host or device memory, k entries each):
+ *   ecc[s]       largest finite distance (0 for an isolated source)
+ *   dsum[s]      sum of finite distances
+ *   reached[s]   vertices reached, s included
+ *   closeness[s] (reached - 1) / dsum, 0 when nothing else is reached
+ *   harmonic[s]  sum over reached v != s of 1 / d(s, v), computed as the sum
+ *                over distances d = 1, 2, ... of (vertices at distance d) / d
+ *                in ascending d, in IEEE double: the same value on any grid
+ *   summary      host struct (may be NULL): diameter, radius, pairs, total.
+ * The integer figures are exact.  opts: as dawn_msbfs_ex (lanes, spin_limit).
+ */
+DAWN_API int dawn_centrality(dawn_graph_t g, const int32_t* sources, int32_t k, int32_t* ecc, int64_t* dsum,
+                             int32_t* reached, double* closeness, double* harmonic, dawn_apsp_summary* summary,
+                             const dawn_msbfs_opts* opts, void* stream);
+
 /*
  * Continuous-batching server over several resident graphs (APSP-style
  * batching of Sec. 3.3 applied to a request stream; the paper has no

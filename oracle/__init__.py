@@ -67,6 +67,7 @@ def _load():
             "oracle_wcc": [i32, vp, vp, vp],
             "oracle_msbfs": [i32, vp, vp, vp, i32, vp, vp, vp, vp],
             "oracle_parents": [i32, vp, vp, vp, vp],
+            "oracle_centrality": [i32, vp, vp, vp, i32, vp, vp, vp, vp, vp, vp],
         }
         for name, args in sig.items():
             f = getattr(lib, name)
@@ -167,6 +168,24 @@ def parents(row_ptr, col_idx, dist):
     if _load().oracle_parents(rp.size - 1, _p(rp), _p(ci), _p(d), _p(par)) != 0:
         raise ValueError("oracle_parents: bad input")
     return par
+
+
+def centrality(row_ptr, col_idx, sources):
+    """Per source ecc, dsum, reached, closeness, harmonic; whole-run summary
+    {diameter, radius, pairs, dist_total}."""
+    rp, ci = _csr(row_ptr, col_idx)
+    src = np.ascontiguousarray(sources, dtype=np.int32)
+    k = src.size
+    out = {"ecc": np.empty(k, dtype=np.int32), "dsum": np.empty(k, dtype=np.int64),
+           "reached": np.empty(k, dtype=np.int32), "closeness": np.empty(k, dtype=np.float64),
+           "harmonic": np.empty(k, dtype=np.float64)}
+    summ = np.empty(4, dtype=np.int64)
+    rc = _load().oracle_centrality(rp.size - 1, _p(rp), _p(ci), _p(src), k, _p(out["ecc"]), _p(out["dsum"]),
+                                   _p(out["reached"]), _p(out["closeness"]), _p(out["harmonic"]), _p(summ))
+    if rc != 0:
+        raise ValueError("oracle_centrality: bad input")
+    out["summary"] = dict(zip(("diameter", "radius", "pairs", "dist_total"), (int(x) for x in summ)))
+    return out
 
 
 def msbfs(row_ptr, col_idx, sources, keep_dist: bool = True):

@@ -34,6 +34,9 @@
  *   oracle_parents       shortest-path tree from exact distances (Fact 1 /
  *                        Thm 1: a vertex at level d > 0 is entered from one at
  *                        level d - 1), smallest-id tie-break.
+ *   oracle_centrality    closeness, harmonic centrality and whole-run
+ *                        diameter / radius from the SOVM distances of each
+ *                        listed source (Sec. 3.3's APSP, Table 1's epsilon).
  *   oracle_msbfs         APSP as SOVM from each listed source (Sec. 3.3,
  *                        "APSP repeats the SSSP per source"), plus per-source
  *                        eccentricity (largest finite distance, Table 1's
@@ -356,5 +359,62 @@ int oracle_parents(int32_t n, const int32_t* row_ptr, const int32_t* col_idx,
             if (dist[v] == dist[u] + 1 && (parent[v] < 0 || u < parent[v])) parent[v] = u;
         }
     }
+    return 0;
+}
+
+/*
+ * Centrality of each listed source from its SOVM distances (Alg. 3 per
+ * source, Sec. 3.3).  With c_d = number of vertices at distance d:
+ *   ecc = largest d with c_d > 0 (0 if none), dsum = sum of d * c_d,
+ *   reached = 1 + sum of c_d, closeness = (reached - 1) / dsum (0 when
+ *   nothing else is reached), harmonic = sum over d = 1, 2, ... of c_d / d,
+ *   added in ascending d in double precision.
+ * summary (nullable) = {largest ecc, smallest ecc over the sources that reach
+ * another vertex (-1 if none), sum of (reached - 1), sum of dsum}.
+ * Any output pointer may be NULL.  Returns 0, or -1 on bad input.
+ */
+int oracle_centrality(int32_t n, const int32_t* row_ptr, const int32_t* col_idx,
+                      const int32_t* sources, int32_t k, int32_t* ecc, int64_t* dsum, int32_t* reached,
+                      double* closeness, double* harmonic, int64_t* summary) {
+    int32_t* dist = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+    int64_t* count = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+    if (!dist || !count) { free(dist); free(count); return -1; }
+    int64_t big = 0, small = -1, pairs = 0, total = 0;
+    for (int32_t i = 0; i < k; ++i) {
+        if (oracle_sssp_sovm(n, row_ptr, col_idx, sources[i], dist, NULL, NULL) != 0) {
+            free(dist); free(count);
+            return -1;
+        }
+        for (int32_t d = 0; d < n; ++d) count[d] = 0;
+        for (int32_t v = 0; v < n; ++v)
+            if (dist[v] > 0) count[dist[v]] += 1;
+        int32_t e = 0;
+        int64_t sum = 0, r = 1;
+        double h = 0.0;
+        for (int32_t d = 1; d < n; ++d) {
+            if (count[d] == 0) continue;
+            e = d;
+            sum += (int64_t)d * count[d];
+            r += count[d];
+            h += (double)count[d] / (double)d;
+        }
+        if (ecc) ecc[i] = e;
+        if (dsum) dsum[i] = sum;
+        if (reached) reached[i] = (int32_t)r;
+        if (closeness) closeness[i] = r > 1 ? (double)(r - 1) / (double)sum : 0.0;
+        if (harmonic) harmonic[i] = h;
+        if (e > big) big = e;
+        if (r > 1 && (small < 0 || e < small)) small = e;
+        pairs += r - 1;
+        total += sum;
+    }
+    if (summary) {
+        summary[0] = big;
+        summary[1] = small;
+        summary[2] = pairs;
+        summary[3] = total;
+    }
+    free(dist);
+    free(count);
     return 0;
 }

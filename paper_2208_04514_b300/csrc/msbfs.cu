@@ -73,6 +73,10 @@ struct MsArgs {
     int32_t bar_parity;
     long long* trace;                     // device, may be null: 4 int64 per level
     int32_t trace_cap;
+    int32_t nostore;                      // 1: no distance rows at all (reductions only)
+    int32_t* ring;                        // device, may be null: [3][kMsMaxLanes] vertices found per level
+    double* harm;                         // device, k: harmonic centrality (needs ring)
+    double* clos;                         // device, k, may be null: closeness
 };
 
 __device__ __forceinline__ unsigned ms_ld_acquire(const unsigned* p) {
@@ -137,6 +141,7 @@ __device__ __forceinline__ long long dist_index(const MsArgs& a, int s0, int s, 
 }
 
 __device__ __forceinline__ void store_dist(const MsArgs& a, int s0, int s, int v, int value) {
+    if (a.nostore) return;
     const long long idx = dist_index(a, s0, s, v);
     if (a.dist_bytes == 2) static_cast<int16_t*>(a.out)[idx] = (int16_t)value;
     else static_cast<int32_t*>(a.out)[idx] = value;
@@ -144,6 +149,7 @@ __device__ __forceinline__ void store_dist(const MsArgs& a, int s0, int s, int v
 
 // Fill the batch's distance cells with -1.
 __device__ void fill_batch(const MsArgs& a, int s0, int kb) {
+    if (a.nostore) return;
     const int n = a.n;
     if (a.layout == DAWN_SOURCE_MAJOR) {
         // one row per CTA at a time, 16-byte stores when the row allows it
@@ -248,6 +254,7 @@ __global__ void __launch_bounds__(kMsThreads, 1) msbfs_kernel(MsArgs a) {
     __shared__ int s_reached[kMsMaxLanes];
     __shared__ int s_ecc[kMsMaxLanes];
     __shared__ long long s_dsum[kMsMaxLanes];
+    __shared__ double s_harm[kMsMaxLanes];  // CTA 0: harmonic sums, added level by level
     __shared__ unsigned long long s_newmask[4];
     __shared__ int s_hcount;
     __shared__ int s_hv[kMsHeavyMax], s_hj[kMsHeavyMax], s_hie[kMsHeavyMax];
@@ -275,6 +282,7 @@ __global__ void __launch_bounds__(kMsThreads, 1) msbfs_kernel(MsArgs a) {
         s_reached[i] = 0;
         s_ecc[i] = 0;
         s_dsum[i] = 0;
+        s_harm[i] = 0.0;
     }
     if (threadIdx.x < 4) s_newmask[threadIdx.x] = 0;
     if (threadIdx.x == 0) { s_hcount = 0; s_need = 0; s_cover = 0; }
@@ -508,6 +516,7 @@ __global__ void __launch_bounds__(kMsThreads, 1) msbfs_kernel(MsArgs a) {
                     s_dsum[s] += (long long)c * t;
                     s_ecc[s] = t;
                     s_cnt[s] = 0;
+                    if (a.ring) atomicAdd(&a.ring[(t % 3) * kMsMaxLanes + s], c);
                 }
             }
             if (threadIdx.x < W && s_newmask[threadIdx.x]) {
@@ -523,6 +532,19 @@ __global__ void __launch_bounds__(kMsThreads, 1) msbfs_kernel(MsArgs a) {
             if (blockIdx.x == 0 && threadIdx.x >= 32 && threadIdx.x < 38)
                 ctl->lanes_new[(t + 1) % 3][threadIdx.x - 32] = 0ull;
             if (!ms_barrier(ctl, bar, bar_target, a.spin_limit, ctl->lanes_new[t % 3], 6, s_lanes)) return;
+            // harmonic centrality: CTA 0 adds (vertices at distance t) / t per
+            // lane, level after level, so the sum runs in ascending distance
+            // order whatever the grid; the slot is next used at level t + 3
+            if (a.ring && blockIdx.x == 0) {
+                int* slot = a.ring + (t % 3) * kMsMaxLanes;
+                for (int s = threadIdx.x; s < L; s += kMsThreads) {
+                    const int c = __ldcg(slot + s);
+                    if (c) {
+                        s_harm[s] += (double)c / (double)t;
+                        slot[s] = 0;
+                    }
+                }
+            }
             // next level: arc-parallel while most scanned vertices stay uncovered
             // and a good share of the lanes is still growing
             {
@@ -554,6 +576,12 @@ __global__ void __launch_bounds__(kMsThreads, 1) msbfs_kernel(MsArgs a) {
             if (done) break;
         }
         // ---- batch reductions: per-CTA partials, then one thread per lane
+        if (a.ring && blockIdx.x == 0) {
+            for (int s = threadIdx.x; s < L; s += kMsThreads) {
+                if (s < kb) a.harm[s0 + s] = s_harm[s];
+                s_harm[s] = 0.0;
+            }
+        }
         for (int s = threadIdx.x; s < L; s += kMsThreads) {
             a.part_i[((long long)blockIdx.x * 2 + 0) * kMsMaxLanes + s] = s_reached[s];
             a.part_i[((long long)blockIdx.x * 2 + 1) * kMsMaxLanes + s] = s_ecc[s];
@@ -575,6 +603,7 @@ __global__ void __launch_bounds__(kMsThreads, 1) msbfs_kernel(MsArgs a) {
             a.reached[s0 + s] = r;
             a.ecc[s0 + s] = e;
             a.dsum[s0 + s] = sum;
+            if (a.clos) a.clos[s0 + s] = r > 1 ? (double)(r - 1) / (double)sum : 0.0;
         }
         // the next batch's first barrier orders these reads before the partials are rewritten
     }
@@ -615,8 +644,44 @@ int ms_workspace(dawn_graph* g, int W) {
     return DAWN_OK;
 }
 
+// Whole-run figures over the listed sources: {largest ecc, smallest ecc among
+// sources that reach another vertex (-1 if none), pairs, distance total}.
+__global__ void apsp_summary_kernel(const int32_t* __restrict__ ecc, const long long* __restrict__ dsum,
+                                    const int32_t* __restrict__ reached, int32_t k, long long* out) {
+    __shared__ int s_max, s_min;
+    __shared__ unsigned long long s_pairs, s_total;
+    if (threadIdx.x == 0) {
+        s_max = 0;
+        s_min = INT_MAX;
+        s_pairs = 0ull;
+        s_total = 0ull;
+    }
+    __syncthreads();
+    int mx = 0, mn = INT_MAX;
+    unsigned long long pairs = 0ull, total = 0ull;
+    for (int i = threadIdx.x; i < k; i += blockDim.x) {
+        mx = max(mx, ecc[i]);
+        if (reached[i] > 1) mn = min(mn, ecc[i]);
+        pairs += (unsigned long long)(reached[i] - 1);
+        total += (unsigned long long)dsum[i];
+    }
+    atomicMax(&s_max, mx);
+    atomicMin(&s_min, mn);
+    atomicAdd(&s_pairs, pairs);
+    atomicAdd(&s_total, total);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        out[0] = s_max;
+        out[1] = s_min == INT_MAX ? -1 : s_min;
+        out[2] = (long long)s_pairs;
+        out[3] = (long long)s_total;
+    }
+}
+
 int msbfs_run(dawn_graph* g, const int32_t* sources, int32_t k, void* dist_block, int dist_bytes, int layout,
-              int32_t* ecc, int64_t* dsum, int32_t* reached, const dawn_msbfs_opts* opts, cudaStream_t st) {
+              int32_t* ecc, int64_t* dsum, int32_t* reached, const dawn_msbfs_opts* opts, cudaStream_t st,
+              double* closeness = nullptr, double* harmonic = nullptr, dawn_apsp_summary* summary = nullptr,
+              bool nostore = false) {
     if (!g) return fail(DAWN_E_INVALID, "graph is NULL");
     if (!sources || k < 1) return fail(DAWN_E_INVALID, "need k >= 1 sources (k = %d)", k);
     if (dist_bytes != 2 && dist_bytes != 4) return fail(DAWN_E_INVALID, "dist_bytes = %d: need 2 or 4", dist_bytes);
@@ -643,14 +708,20 @@ int msbfs_run(dawn_graph* g, const int32_t* sources, int32_t k, void* dist_block
     const bool out_dev = dist_block && is_device_ptr(dist_block);
     const bool ecc_dev = ecc && is_device_ptr(ecc), dsum_dev = dsum && is_device_ptr(dsum),
                reached_dev = reached && is_device_ptr(reached);
+    const bool clos_dev = closeness && is_device_ptr(closeness), harm_dev = harmonic && is_device_ptr(harmonic);
     // temporaries: device sources, reductions, distance staging
     void* tmp = nullptr;
     size_t off_src = 0, off_ecc = 256 * (((size_t)k * 4 + 255) / 256);
     size_t off_dsum = off_ecc + 256 * (((size_t)k * 4 + 255) / 256);
     size_t off_reached = off_dsum + 256 * (((size_t)k * 8 + 255) / 256);
-    size_t off_dist = off_reached + 256 * (((size_t)k * 4 + 255) / 256);
+    size_t off_clos = off_reached + 256 * (((size_t)k * 4 + 255) / 256);
+    size_t off_harm = off_clos + 256 * (((size_t)k * 8 + 255) / 256);
+    size_t off_ring = off_harm + 256 * (((size_t)k * 8 + 255) / 256);
+    size_t off_sum = off_ring + 256 * ((3 * kMsMaxLanes * sizeof(int32_t) + 255) / 256);
+    size_t off_dist = off_sum + 256;
     size_t dist_cells = 0;
-    if (!dist_block) dist_cells = (size_t)lanes * g->n;        // one pass's block, kept on the device
+    if (nostore) dist_cells = 0;                               // reductions only
+    else if (!dist_block) dist_cells = (size_t)lanes * g->n;   // one pass's block, kept on the device
     else if (!out_dev) dist_cells = (size_t)k * g->n;          // staging for a host block
     const size_t tmp_bytes = off_dist + dist_cells * cell + 256;
     DAWN_CUDA_TRY(cudaMallocAsync(&tmp, tmp_bytes, st));
@@ -660,7 +731,12 @@ int msbfs_run(dawn_graph* g, const int32_t* sources, int32_t k, void* dist_block
     long long* d_dsum = dsum_dev ? reinterpret_cast<long long*>(dsum) : reinterpret_cast<long long*>(t8 + off_dsum);
     int32_t* d_reached = reached_dev ? reached : reinterpret_cast<int32_t*>(t8 + off_reached);
     void* d_out = out_dev ? dist_block : static_cast<void*>(t8 + off_dist);
+    double* d_clos = closeness ? (clos_dev ? closeness : reinterpret_cast<double*>(t8 + off_clos)) : nullptr;
+    double* d_harm = harmonic ? (harm_dev ? harmonic : reinterpret_cast<double*>(t8 + off_harm)) : nullptr;
+    int32_t* d_ring = reinterpret_cast<int32_t*>(t8 + off_ring);
+    long long* d_sum = reinterpret_cast<long long*>(t8 + off_sum);
     cudaError_t e = cudaMemcpyAsync(d_src, hsrc.data(), sizeof(int32_t) * (size_t)k, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && d_harm) e = cudaMemsetAsync(d_ring, 0, 3 * kMsMaxLanes * sizeof(int32_t), st);
 
     MsArgs a;
     a.in_ptr = g->in_ptr;
@@ -692,6 +768,11 @@ int msbfs_run(dawn_graph* g, const int32_t* sources, int32_t k, void* dist_block
         return fail(DAWN_E_INVALID, "trace must be device memory with trace_cap >= 0");
     }
     a.out = d_out;
+    a.nostore = nostore ? 1 : 0;
+    a.ring = d_harm ? d_ring : nullptr;
+    a.harm = d_harm;
+    a.clos = d_clos;
+    if (nostore) a.dist_bytes = 4;  // nothing is stored: no int16 limit
     if (!dist_block) {
         // no caller block: every pass writes its rows into one device block of `lanes` rows
         a.layout = DAWN_SOURCE_MAJOR;
@@ -717,6 +798,16 @@ int msbfs_run(dawn_graph* g, const int32_t* sources, int32_t k, void* dist_block
         e = cudaMemcpyAsync(dsum, d_dsum, sizeof(long long) * (size_t)k, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess && lrc == DAWN_OK && reached && !reached_dev)
         e = cudaMemcpyAsync(reached, d_reached, sizeof(int32_t) * (size_t)k, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && lrc == DAWN_OK && closeness && !clos_dev)
+        e = cudaMemcpyAsync(closeness, d_clos, sizeof(double) * (size_t)k, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && lrc == DAWN_OK && harmonic && !harm_dev)
+        e = cudaMemcpyAsync(harmonic, d_harm, sizeof(double) * (size_t)k, cudaMemcpyDeviceToHost, st);
+    long long hsum[4] = {0, 0, 0, 0};
+    if (e == cudaSuccess && lrc == DAWN_OK && summary) {
+        apsp_summary_kernel<<<1, 1024, 0, st>>>(d_ecc, d_dsum, d_reached, k, d_sum);
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaMemcpyAsync(hsum, d_sum, sizeof(hsum), cudaMemcpyDeviceToHost, st);
+    }
     int status = 0;
     if (e == cudaSuccess && lrc == DAWN_OK)
         e = cudaMemcpyAsync(&status, &ctl->status, sizeof(int), cudaMemcpyDeviceToHost, st);
@@ -733,6 +824,12 @@ int msbfs_run(dawn_graph* g, const int32_t* sources, int32_t k, void* dist_block
         if (status == DEV_TIMEOUT) return fail(DAWN_E_TIMEOUT, "a grid-barrier wait on the device ran out of its spin budget");
         return fail(DAWN_E_CUDA, "unknown device status %d", status);
     }
+    if (summary) {
+        summary->diameter = (int32_t)hsum[0];
+        summary->radius = (int32_t)hsum[1];
+        summary->pairs = hsum[2];
+        summary->dist_total = hsum[3];
+    }
     return DAWN_OK;
 }
 
@@ -746,6 +843,13 @@ DAWN_API int dawn_msbfs_ex(dawn_graph_t g, const int32_t* sources, int32_t k, vo
                            const dawn_msbfs_opts* opts, void* stream) {
     return dawn::msbfs_run(g, sources, k, dist_block, dist_bytes, layout, ecc, dsum, reached, opts,
                            (cudaStream_t)stream);
+}
+
+DAWN_API int dawn_centrality(dawn_graph_t g, const int32_t* sources, int32_t k, int32_t* ecc, int64_t* dsum,
+                             int32_t* reached, double* closeness, double* harmonic, dawn_apsp_summary* summary,
+                             const dawn_msbfs_opts* opts, void* stream) {
+    return dawn::msbfs_run(g, sources, k, nullptr, 4, DAWN_SOURCE_MAJOR, ecc, dsum, reached, opts,
+                           (cudaStream_t)stream, closeness, harmonic, summary, true);
 }
 
 DAWN_API int dawn_msbfs(dawn_graph_t g, const int32_t* sources, int32_t k, void* dist_block,

@@ -81,6 +81,11 @@ class dawn_msbfs_opts(ctypes.Structure):
                 ("trace", ctypes.c_void_p)]
 
 
+class dawn_apsp_summary(ctypes.Structure):
+    _fields_ = [("diameter", ctypes.c_int32), ("radius", ctypes.c_int32), ("pairs", ctypes.c_int64),
+                ("dist_total", ctypes.c_int64)]
+
+
 _lib = None
 _vp, _i32, _i64, _u32, _u64, _sz = (ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32,
                                     ctypes.c_uint64, ctypes.c_size_t)
@@ -98,6 +103,7 @@ _SIGNATURES = {
     "dawn_sssp_tree_async": [_vp, _i32, _vp, _vp, _vp],
     "dawn_msbfs": [_vp, _vp, _i32, _vp, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp],
     "dawn_msbfs_ex": [_vp, _vp, _i32, _vp, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp, _vp],
+    "dawn_centrality": [_vp, _vp, _i32, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp],
     "dawn_autotune": [_vp, _vp, _i32, _vp, _vp],
     "dawn_set_tuning": [_vp, _vp],
     "dawn_serve_create": [_vp, ctypes.c_int, _sz, ctypes.c_int, ctypes.POINTER(_vp)],
@@ -270,6 +276,19 @@ def dawn_msbfs_ex(g: int, sources, k: int | None = None, dist_block=None, dist_b
     _check(load().dawn_msbfs_ex(g, _ptr(sources), k, _ptr(dist_block), dist_bytes, layout,
                                 _ptr(ecc), _ptr(dsum), _ptr(reached), ctypes.byref(o) if o else None,
                                 _stream(stream)))
+
+
+def dawn_centrality(g: int, sources, k: int | None = None, ecc=None, dsum=None, reached=None, closeness=None,
+                    harmonic=None, opts: dict | None = None, stream=None) -> dict:
+    """Batched level loop without distance rows; fills the given per-source
+    arrays (host or device) and returns the whole-run summary."""
+    k = int(sources.shape[0]) if k is None else k
+    o = _opts(opts, dawn_msbfs_opts)
+    summ = dawn_apsp_summary()
+    _check(load().dawn_centrality(g, _ptr(sources), k, _ptr(ecc), _ptr(dsum), _ptr(reached), _ptr(closeness),
+                                  _ptr(harmonic), ctypes.byref(summ), ctypes.byref(o) if o else None,
+                                  _stream(stream)))
+    return {f: getattr(summ, f) for f, _ in summ._fields_}
 
 
 # -------------------------------------------------------------- autotune --

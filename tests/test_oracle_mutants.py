@@ -33,6 +33,10 @@ MUTANTS = {
     "wcc_half_union": ("if (a < b) p[b] = a; else p[a] = b;", "if (a < b) p[b] = a;"),
     "msbfs_ecc_off_by_one": ("if (dist[v] > e) e = dist[v];", "if (dist[v] > e) e = dist[v] + 1;"),
     "msbfs_sum_counts": ("sum += dist[v];", "sum += 1;"),
+    "harmonic_next_level": ("h += (double)count[d] / (double)d;", "h += (double)count[d] / (double)(d + 1);"),
+    "closeness_counts_source": ("closeness[i] = r > 1 ? (double)(r - 1) / (double)sum : 0.0;",
+                                "closeness[i] = r > 1 ? (double)r / (double)sum : 0.0;"),
+    "radius_counts_isolated": ("if (r > 1 && (small < 0 || e < small)) small = e;", "if (small < 0 || e < small) small = e;"),
     "parents_largest_id": ("(parent[v] < 0 || u < parent[v])) parent[v] = u;", "(parent[v] < 0 || u > parent[v])) parent[v] = u;"),
     "parents_same_level_too": ("if (dist[v] == dist[u] + 1 && (parent[v] < 0", "if (dist[v] >= dist[u] && dist[v] > 0 && (parent[v] < 0"),
 }

@@ -414,3 +414,69 @@ def test_tree_walks_back_to_source():
                     assert (p, x) in arcs
                     x, steps = p, steps + 1
                 assert steps == d[v]
+
+
+# ------------------------------------------------------------ centrality pins --
+
+def test_centrality_closed_forms():
+    n = 13
+    allv = np.arange(n)
+    # path: from an end, harmonic = H_(n-1), closeness = 2 / n; diameter n-1, radius ceil((n-1)/2)
+    g = path_graph(n, directed=False)
+    c = oracle.centrality(g.row_ptr, g.col_idx, allv)
+    assert c["harmonic"][0] == pytest.approx(sum(1.0 / i for i in range(1, n)), rel=1e-15)
+    assert c["closeness"][0] == pytest.approx(2.0 / n, rel=1e-15)
+    assert c["summary"] == {"diameter": n - 1, "radius": (n - 1 + 1) // 2, "pairs": n * (n - 1),
+                            "dist_total": int(sum(abs(i - j) for i in range(n) for j in range(n)))}
+    # star: centre harmonic n-1 and closeness 1; leaf harmonic 1 + (n-2)/2; diameter 2, radius 1
+    leaves = np.arange(1, n)
+    star = gg.from_arcs(n, np.r_[np.zeros(n - 1, int), leaves], np.r_[leaves, np.zeros(n - 1, int)], symmetric=True)
+    c = oracle.centrality(star.row_ptr, star.col_idx, allv)
+    assert c["harmonic"][0] == n - 1 and c["closeness"][0] == 1.0
+    assert c["harmonic"][5] == pytest.approx(1 + (n - 2) / 2, rel=1e-15)
+    assert (c["summary"]["diameter"], c["summary"]["radius"]) == (2, 1)
+    # complete graph: harmonic n-1, closeness 1, diameter = radius = 1
+    i, j = np.nonzero(~np.eye(n, dtype=bool))
+    comp = gg.from_arcs(n, i, j, symmetric=True)
+    c = oracle.centrality(comp.row_ptr, comp.col_idx, allv)
+    assert (c["harmonic"] == n - 1).all() and (c["closeness"] == 1.0).all()
+    assert (c["summary"]["diameter"], c["summary"]["radius"]) == (1, 1)
+    # odd undirected cycle n = 2m + 1: every vertex has two at each distance 1..m
+    m = 6
+    cyc_n = 2 * m + 1
+    s_ = np.arange(cyc_n)
+    cyc = gg.from_arcs(cyc_n, np.r_[s_, (s_ + 1) % cyc_n], np.r_[(s_ + 1) % cyc_n, s_], symmetric=True)
+    c = oracle.centrality(cyc.row_ptr, cyc.col_idx, np.arange(cyc_n))
+    assert np.allclose(c["harmonic"], 2 * sum(1.0 / d for d in range(1, m + 1)), rtol=1e-15)
+    assert (c["summary"]["diameter"], c["summary"]["radius"]) == (m, m)
+    # isolated sources are left out of the radius; no edges at all: radius -1
+    iso = gg.from_arcs(4, np.array([0, 1]), np.array([1, 0]), symmetric=True)
+    c = oracle.centrality(iso.row_ptr, iso.col_idx, np.arange(4))
+    assert c["summary"] == {"diameter": 1, "radius": 1, "pairs": 2, "dist_total": 2}
+    assert c["harmonic"][3] == 0.0 and c["closeness"][3] == 0.0
+    empty = gg.from_arcs(3, np.array([], int), np.array([], int))
+    assert oracle.centrality(empty.row_ptr, empty.col_idx, np.arange(3))["summary"]["radius"] == -1
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_centrality_vs_scipy(seed):
+    g = random_digraph(1300 + seed)
+    n = g.n
+    a = sp.csr_matrix((np.ones(g.m), g.col_idx, g.row_ptr), shape=(n, n))
+    d = shortest_path(a, directed=True, unweighted=True)
+    c = oracle.centrality(g.row_ptr, g.col_idx, np.arange(n))
+    fin = np.isfinite(d)
+    np.fill_diagonal(fin, False)
+    for s in range(n):
+        ds = d[s][fin[s]]
+        assert c["ecc"][s] == (int(ds.max()) if ds.size else 0)
+        assert c["dsum"][s] == int(ds.sum())
+        assert c["reached"][s] == ds.size + 1
+        assert c["harmonic"][s] == pytest.approx(float((1.0 / ds).sum()) if ds.size else 0.0, rel=1e-12)
+        assert c["closeness"][s] == pytest.approx(ds.size / ds.sum() if ds.size else 0.0, rel=1e-15)
+    ecc = np.array([int(d[s][fin[s]].max()) if fin[s].any() else 0 for s in range(n)])
+    reaching = fin.any(axis=1)
+    assert c["summary"]["diameter"] == ecc.max()
+    assert c["summary"]["radius"] == (ecc[reaching].min() if reaching.any() else -1)
+    assert c["summary"]["pairs"] == fin.sum()
+    assert c["summary"]["dist_total"] == int(d[fin].sum())
