@@ -345,6 +345,46 @@ def bench_batched(dawn, torch, flush, plain_sample=4096, k=0, lanes_list=(64, 12
     return out
 
 
+def bench_modes(dawn, torch, flush, g_rmat, srcs_rmat, nsrc=16):
+    """The paper's two operators alone and the per-level choice, on dense
+    low-diameter graphs: SOVM push only (Alg. 3), BOVM pull only (Alg. 1) and
+    AUTO, on the headline RMAT scale-20 graph (16 of its sources) and on a
+    directed Erdos-Renyi graph with n = 2^18 and mean out-degree 128 (seed 11,
+    16 uniform sources).  Median microseconds per source and GTEPS, L2 flushed
+    between sources."""
+    from paper_2208_04514_b300 import graphgen as gg
+    stream = torch.cuda.current_stream()
+    out = {}
+    er = gg.erdos_renyi(1 << 18, 128.0, seed=11)
+    cases = [("rmat20", g_rmat, dawn.DAWN_SYMMETRIC, srcs_rmat[:nsrc]),
+             ("er262144_deg128", er, dawn.DAWN_DIRECTED, gg.sample_sources(er, nsrc, seed=12))]
+    for name, g, flags, srcs in cases:
+        h = dawn.dawn_graph_upload(g.row_ptr, g.col_idx, flags=flags, stream=stream)
+        dist = torch.empty(g.n, dtype=torch.int32, device="cuda")
+        stats = torch.zeros((len(srcs), dawn.STATS_WORDS), dtype=torch.int64, device="cuda")
+        res = {"n": g.n, "m": g.m}
+        for mode_name, mode in (("push_sovm", dawn.DAWN_MODE_PUSH), ("pull_bovm", dawn.DAWN_MODE_PULL),
+                                ("auto", dawn.DAWN_MODE_AUTO)):
+            opts = {"mode": mode}
+            dawn.dawn_sssp_async(h, int(srcs[0]), dist, opts, stats[0], stream)  # warm-up
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in srcs]
+            for i, sv in enumerate(srcs):
+                _flush(flush, i)
+                ev[i][0].record(stream)
+                dawn.dawn_sssp_async(h, int(sv), dist, opts, stats[i], stream)
+                ev[i][1].record(stream)
+            dawn.dawn_graph_sync(h, stream)
+            us = [a.elapsed_time(b) * 1e3 for a, b in ev]
+            st = [dawn.stats_from_words(r) for r in stats.cpu().numpy()]
+            edges = sum(x["edges"] for x in st)
+            res[mode_name] = {"us_per_source_median": statistics.median(us), "gteps": edges / (sum(us) * 1e-6) / 1e9,
+                              "levels_median": statistics.median(x["levels"] for x in st)}
+        dawn.dawn_graph_free(h)
+        out[name] = res
+    out["l2"] = "flushed between sources"
+    return out
+
+
 def bench_centrality(dawn, torch, flush, lanes=256):
     """RMAT scale 16 (seed 4), all 65,536 sources: dawn_centrality (ecc,
     distance sum, reached, closeness, harmonic per source, and the diameter /
@@ -578,7 +618,8 @@ def run_gpu(args):
         line["secondary"] = {"lattice": bench_lattice(dawn, torch, flush),
                              "batched": bench_batched(dawn, torch, flush),
                              "tree": bench_tree(dawn, torch, flush, g, srcs, peak),
-                             "centrality": bench_centrality(dawn, torch, flush)}
+                             "centrality": bench_centrality(dawn, torch, flush),
+                             "modes": bench_modes(dawn, torch, flush, g, srcs)}
         del flush
         torch.cuda.empty_cache()
         line["secondary"]["serving"] = bench_serving(dawn, torch, nreq=args.serve_requests)
@@ -598,6 +639,9 @@ def run_one(args):
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.int32, device="cuda")
     if args.workload == "lattice":
         out = bench_lattice(dawn, torch, flush)
+    elif args.workload == "modes":
+        g, srcs = build_workload()
+        out = bench_modes(dawn, torch, flush, g, srcs)
     elif args.workload == "centrality":
         out = bench_centrality(dawn, torch, flush)
     elif args.workload == "tree":
@@ -625,7 +669,7 @@ def main():
                     help="use only the first N of the 64 sources (small profiling runs; not a bench value)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end host-buffer pass")
     ap.add_argument("--serve-requests", type=int, default=48, help="requests per arrival rate in the serving mix")
-    ap.add_argument("--workload", choices=["all", "lattice", "batched", "serving", "tree", "centrality"], default="all",
+    ap.add_argument("--workload", choices=["all", "lattice", "batched", "serving", "tree", "centrality", "modes"], default="all",
                     help="run one secondary workload alone and print its figures (profiling runs; not a bench line)")
     ap.add_argument("--batched-k", type=int, default=0, help="with --workload batched: sources (0 = all)")
     ap.add_argument("--batched-lanes", type=int, default=0, help="with --workload batched: one lane width")
