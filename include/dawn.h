@@ -183,6 +183,20 @@ DAWN_API int dawn_sssp_tree(dawn_graph_t g, int32_t src, int32_t* dist, int32_t*
 DAWN_API int dawn_sssp_tree_async(dawn_graph_t g, int32_t src, int32_t* dist_dev, int32_t* parent_dev,
                                   void* stream);
 
+/*
+ * k single-source searches in one call (APSP by repetition, Sec. 3.3): row i
+ * of dist (k x n int32, source-major) receives the distances from
+ * sources[i], exactly as dawn_sssp_ex would (same options).  With host
+ * dist the rows are staged in two device buffers and each row's copy to the
+ * host overlaps the next source's level loop on a second stream; pinned host
+ * memory is needed for that overlap.  Device dist is written in place.
+ *   sources  host or device int32[k], each in [0, n) (DAWN_E_INVALID otherwise).
+ *   stats    host or device dawn_sssp_stats[k], or NULL.
+ * Synchronous: returns when every row is in dist (or on the first error).
+ */
+DAWN_API int dawn_sssp_many(dawn_graph_t g, const int32_t* sources, int32_t k, int32_t* dist,
+                            dawn_sssp_stats* stats, const dawn_sssp_opts* opts, void* stream);
+
 /* Synchronize `stream` and return (then clear) the sticky device status of g:
  * DAWN_OK, DAWN_E_TIMEOUT or DAWN_E_OVERFLOW. */
 DAWN_API int dawn_graph_sync(dawn_graph_t g, void* stream);

@@ -1,0 +1,85 @@
+// Many single-source searches in one call: k level loops back to back (the
+// SSSP of Alg. 3 / Alg. 1 per source, Sec. 3.3's APSP-by-repetition), each
+// writing its own distance row.  For host outputs the rows are staged in two
+// device buffers, and the device-to-host copy of source i runs on a copy
+// stream while the level loop of source i + 1 runs, so the transfer hides
+// behind the computation (pinned host memory is needed for the overlap).
+#include <vector>
+
+#include "dawn_internal.cuh"
+
+extern "C" {
+
+DAWN_API int dawn_sssp_many(dawn_graph_t g, const int32_t* sources, int32_t k, int32_t* dist,
+                            dawn_sssp_stats* stats, const dawn_sssp_opts* opts, void* stream) {
+    using namespace dawn;
+    if (!g) return fail(DAWN_E_INVALID, "graph is NULL");
+    if (!sources || k < 1) return fail(DAWN_E_INVALID, "need k >= 1 sources (k = %d)", k);
+    if (!dist) return fail(DAWN_E_INVALID, "dist is NULL");
+    cudaStream_t st = (cudaStream_t)stream;
+    std::vector<int32_t> src((size_t)k);
+    DAWN_CUDA_TRY(cudaMemcpy(src.data(), sources, sizeof(int32_t) * (size_t)k, cudaMemcpyDefault));
+    for (int32_t i = 0; i < k; ++i)
+        if (src[i] < 0 || src[i] >= g->n) return fail(DAWN_E_INVALID, "sources[%d] = %d outside [0, %d)", i, src[i], g->n);
+    const size_t row = (size_t)g->n;
+    const bool ddev = is_device_ptr(dist);
+    const bool sdev = stats && is_device_ptr(stats);
+    // per-source statistics land in device memory first
+    dawn_sssp_stats* st_dev = sdev ? stats : nullptr;
+    int32_t* stage = nullptr;
+    cudaStream_t cs = nullptr;
+    cudaEvent_t done[2] = {nullptr, nullptr}, copied[2] = {nullptr, nullptr};
+    cudaError_t e = cudaSuccess;
+    if (stats && !sdev) e = cudaMallocAsync((void**)&st_dev, sizeof(dawn_sssp_stats) * (size_t)k, st);
+    if (e == cudaSuccess && !ddev) {
+        e = cudaMallocAsync((void**)&stage, sizeof(int32_t) * 2 * row, st);
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+        for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
+            e = cudaEventCreateWithFlags(&done[b], cudaEventDisableTiming);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&copied[b], cudaEventDisableTiming);
+        }
+    }
+    int rc = e == cudaSuccess ? DAWN_OK : cuda_fail(e, "dawn_sssp_many (set-up)", __FILE__, __LINE__);
+    for (int32_t i = 0; i < k && rc == DAWN_OK; ++i) {
+        dawn_sssp_stats* si = st_dev ? st_dev + i : nullptr;
+        if (ddev) {
+            rc = sssp_launch(g, src[i], dist + (size_t)i * row, opts, si, st);
+            continue;
+        }
+        const int b = i & 1;
+        int32_t* buf = stage + (size_t)b * row;
+        // the copy of source i - 2 must have read this buffer
+        if (i >= 2 && (e = cudaStreamWaitEvent(st, copied[b], 0)) != cudaSuccess) break;
+        rc = sssp_launch(g, src[i], buf, opts, si, st);
+        if (rc != DAWN_OK) break;
+        if ((e = cudaEventRecord(done[b], st)) != cudaSuccess) break;
+        if ((e = cudaStreamWaitEvent(cs, done[b], 0)) != cudaSuccess) break;
+        if ((e = cudaMemcpyAsync(dist + (size_t)i * row, buf, sizeof(int32_t) * row, cudaMemcpyDeviceToHost, cs)) !=
+            cudaSuccess)
+            break;
+        if ((e = cudaEventRecord(copied[b], cs)) != cudaSuccess) break;
+    }
+    if (rc == DAWN_OK && e != cudaSuccess) rc = cuda_fail(e, "dawn_sssp_many", __FILE__, __LINE__);
+    if (cs) {
+        // the main stream waits for the last copies before the buffers go
+        for (int b = 0; b < 2; ++b)
+            if (copied[b]) cudaEventRecord(copied[b], cs);
+        for (int b = 0; b < 2; ++b)
+            if (copied[b]) cudaStreamWaitEvent(st, copied[b], 0);
+    }
+    if (rc == DAWN_OK && stats && !sdev) {
+        e = cudaMemcpyAsync(stats, st_dev, sizeof(dawn_sssp_stats) * (size_t)k, cudaMemcpyDeviceToHost, st);
+        if (e != cudaSuccess) rc = cuda_fail(e, "dawn_sssp_many (stats)", __FILE__, __LINE__);
+    }
+    if (stage) cudaFreeAsync(stage, st);
+    if (stats && !sdev && st_dev) cudaFreeAsync(st_dev, st);
+    const int rs = graph_sync_status(g, st);
+    if (cs) cudaStreamDestroy(cs);
+    for (int b = 0; b < 2; ++b) {
+        if (done[b]) cudaEventDestroy(done[b]);
+        if (copied[b]) cudaEventDestroy(copied[b]);
+    }
+    return rc != DAWN_OK ? rc : rs;
+}
+
+}  // extern "C"

@@ -99,6 +99,7 @@ _SIGNATURES = {
     "dawn_sssp_ex": [_vp, _i32, _vp, _vp, _vp, _vp],
     "dawn_sssp_async": [_vp, _i32, _vp, _vp, _vp, _vp],
     "dawn_sssp_noalloc": [_vp, _vp, _i32, _i64, _i32, _vp, _vp],
+    "dawn_sssp_many": [_vp, _vp, _i32, _vp, _vp, _vp, _vp],
     "dawn_sssp_tree": [_vp, _i32, _vp, _vp, _vp],
     "dawn_sssp_tree_async": [_vp, _i32, _vp, _vp, _vp],
     "dawn_msbfs": [_vp, _vp, _i32, _vp, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp],
@@ -222,6 +223,15 @@ def dawn_sssp_ex(g: int, src: int, dist, opts: dict | None = None, stream=None) 
     _check(load().dawn_sssp_ex(g, int(src), _ptr(dist), ctypes.byref(o) if o else None,
                                ctypes.byref(st), _stream(stream)))
     return st.as_dict()
+
+
+def dawn_sssp_many(g: int, sources, k: int | None = None, dist=None, stats=None, opts: dict | None = None,
+                   stream=None) -> None:
+    """k sources, one distance row each (dist: host or device, k x n int32)."""
+    k = int(sources.shape[0]) if k is None else k
+    o = _opts(opts, dawn_sssp_opts)
+    _check(load().dawn_sssp_many(g, _ptr(sources), k, _ptr(dist), _ptr(stats), ctypes.byref(o) if o else None,
+                                 _stream(stream)))
 
 
 def dawn_sssp_tree(g: int, src: int, dist, parent, stream=None) -> None:

@@ -268,3 +268,33 @@ def test_lattice_4096_full_size(dawn):
             assert st["levels"] > 4000
     finally:
         dawn.dawn_graph_free(h)
+
+
+@pytest.mark.parametrize("where", ["host_pinned", "host_pageable", "device"])
+def test_many_sources_rows(dawn, where):
+    """dawn_sssp_many: every row equals the oracle (and the single-source
+    call), for pinned / pageable host rows and device rows, with statistics;
+    an odd k exercises both staging buffers unevenly."""
+    g = gg.rmat(13, seed=7)
+    h = dawn.dawn_graph_upload(g.row_ptr, g.col_idx, flags=dawn.DAWN_SYMMETRIC)
+    try:
+        srcs = gg.sample_sources(g, 7, seed=3)
+        if where == "device":
+            dist = torch.full((7, g.n), 99, dtype=torch.int32, device="cuda")
+            stats = torch.zeros((7, dawn.STATS_WORDS), dtype=torch.int64, device="cuda")
+            dawn.dawn_sssp_many(h, torch.from_numpy(srcs).cuda(), dist=dist, stats=stats)
+            rows, st = dist.cpu().numpy(), stats.cpu().numpy()
+        else:
+            dist = torch.full((7, g.n), 99, dtype=torch.int32, pin_memory=(where == "host_pinned"))
+            stats = np.zeros((7, dawn.STATS_WORDS), dtype=np.int64)
+            dawn.dawn_sssp_many(h, srcs, dist=dist, stats=stats)
+            rows, st = dist.numpy(), stats
+        for i, s in enumerate(srcs):
+            want = oracle.sssp_sovm(g.row_ptr, g.col_idx, int(s))
+            np.testing.assert_array_equal(rows[i], want)
+            assert dawn.stats_from_words(st[i])["reached"] == int((want >= 0).sum())
+        with pytest.raises(dawn.DawnError) as ei:
+            dawn.dawn_sssp_many(h, np.array([0, g.n], dtype=np.int32), dist=np.zeros((2, g.n), dtype=np.int32))
+        assert ei.value.code == dawn.DAWN_E_INVALID
+    finally:
+        dawn.dawn_graph_free(h)
