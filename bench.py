@@ -193,7 +193,8 @@ def run_reference(args):
         tot_n += d
         tot_t += t
     gteps = tot_e / tot_t / 1e9
-    sample = f"{tot_n} of the 64 sources over {args.steps} steps (each step stops after {budget_s:.0f} s)"
+    sample = (f"{tot_n} single-source runs over {args.steps} steps, taken in order from the 64 sources "
+              f"(a step stops after {budget_s:.0f} s or all 64); literal Alg. 3, one core")
     line = {
         "impl": "reference", "metric": METRIC, "value": gteps, "unit": "GTEPS",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
