@@ -129,9 +129,11 @@ typedef struct {
     int64_t spin_limit;    /* grid-barrier spin budget in SM clock cycles; 0 = default (~2 s) */
     int64_t* trace;        /* device memory or NULL: one record of 4 int64 per grid barrier,
                               {kind, step, count, globaltimer ns}; kind 0 = kernel entry,
-                              1 = init done, 2 = push level, 3 = pull level, 4 = bitmap-to-queue
-                              conversion; count = vertices the level reached (entries queued
-                              for kind 4); records past trace_cap are dropped */
+                              1 = init done, 2 = push level, 3 = pull level over the bitmap,
+                              4 = bitmap-to-queue conversion, 5 = pull level over the lists of
+                              candidates a previous pull left unreached; count = vertices the
+                              level reached (entries queued for kind 4); records past trace_cap
+                              are dropped */
     int32_t trace_cap;     /* records that fit in trace */
     int32_t pull_serial;   /* in-neighbours a lane tests on its own in a pull level before
                               the warp takes the rest of the row; 0 = tuned or 8 */

@@ -43,7 +43,8 @@ struct alignas(128) CtrSlot {
     unsigned long long qpack;  // queue size: entries (high 32 bits) | arcs (low 32 bits)
     unsigned long long nf;     // vertices first reached at this level
     unsigned long long mf;     // sum of their out-degrees
-    unsigned long long pad[13];
+    unsigned long long nc;     // pull levels: vertices still unreached (candidate lists)
+    unsigned long long pad[12];
 };
 
 // Arrival counter of the grid barrier, on its own 128-byte line.
@@ -87,6 +88,8 @@ struct dawn_graph {
     int32_t* queue_off[2] = {nullptr, nullptr}; // each entry's arc offset within its level
     int64_t queue_cap = 0;
     int32_t* dist_tmp = nullptr;      // result staging for host outputs
+    int32_t* cand[2] = {nullptr, nullptr};  // per-CTA lists of unreached pull candidates
+    int64_t cand_cap = 0;             // entries per list
     dawn::Ctl* ctl = nullptr;         // device control block
     dawn_sssp_stats* stats_dev = nullptr;
     dawn_sssp_stats* stats_host = nullptr;  // pinned

@@ -187,6 +187,8 @@ void release(dawn_graph* g) {
     f(g->queue_off[0]);
     f(g->queue_off[1]);
     f(g->dist_tmp);
+    f(g->cand[0]);
+    f(g->cand[1]);
     f(g->ctl);
     f(g->stats_dev);
     f(g->ms_vis[0]);
@@ -282,6 +284,9 @@ int upload(const int32_t* row_ptr, const int32_t* col_idx, int32_t n, int64_t m,
 
     // ---- work buffers of the single-source level loop
     g->queue_cap = (int64_t)n + m / kEntryArcs + 64;
+    // each CTA of the level loop owns ceil(words / warps) words per warp of the
+    // grid's bitmap; with at most 2 CTAs of 32 warps per SM this bounds the lists
+    g->cand_cap = (int64_t)n + 64 + (int64_t)g->sms * 2 * 32 * 32;
     if ((e = alloc((void**)&g->excl, wb)) != cudaSuccess ||
         (e = alloc((void**)&g->vis[0], wb)) != cudaSuccess ||
         (e = alloc((void**)&g->vis[1], wb)) != cudaSuccess ||
@@ -290,6 +295,8 @@ int upload(const int32_t* row_ptr, const int32_t* col_idx, int32_t n, int64_t m,
         (e = alloc((void**)&g->queue_off[0], sizeof(int32_t) * (size_t)g->queue_cap)) != cudaSuccess ||
         (e = alloc((void**)&g->queue_off[1], sizeof(int32_t) * (size_t)g->queue_cap)) != cudaSuccess ||
         (e = alloc((void**)&g->dist_tmp, sizeof(int32_t) * (size_t)n)) != cudaSuccess ||
+        (e = alloc((void**)&g->cand[0], sizeof(int32_t) * (size_t)g->cand_cap)) != cudaSuccess ||
+        (e = alloc((void**)&g->cand[1], sizeof(int32_t) * (size_t)g->cand_cap)) != cudaSuccess ||
         (e = alloc((void**)&g->ctl, sizeof(Ctl))) != cudaSuccess ||
         (e = alloc((void**)&g->stats_dev, sizeof(dawn_sssp_stats))) != cudaSuccess ||
         (e = cudaMallocHost((void**)&g->stats_host, sizeof(dawn_sssp_stats))) != cudaSuccess ||

@@ -81,6 +81,9 @@ struct SsspArgs {
     int32_t pull_serial;     // in-neighbours a lane tests alone in a pull level
     int32_t bar_parity;      // which of the two barrier counters this launch uses
     int32_t smem_words;      // > 0: pull levels copy the bitmap (this many words) to shared memory
+    int32_t* cand0;          // per-CTA lists of unreached pull candidates (null: none)
+    int32_t* cand1;
+    long long cand_cap;      // entries per list
 };
 
 // A frontier queue: entries {first arc, arc count} and, in a parallel array,
@@ -94,10 +97,6 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
     unsigned v;
     asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
-}
-
-__device__ __forceinline__ void st_release(unsigned* p, unsigned v) {
-    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
 __device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long* p) {
@@ -165,6 +164,7 @@ __device__ bool grid_barrier(Ctl* ctl, unsigned* count, unsigned& target, long l
             s_snap[0] = ld_relaxed_u64(&snap->qpack);
             s_snap[1] = ld_relaxed_u64(&snap->nf);
             s_snap[2] = ld_relaxed_u64(&snap->mf);
+            s_snap[3] = ld_relaxed_u64(&snap->nc);
         }
         s_ok = ok;
     }
@@ -208,8 +208,9 @@ __device__ __forceinline__ void warp_enqueue(bool has, int rb, int re, int lane,
     }
 }
 
-// Sum (nf, mf) over the CTA and add them to the level's counters.
-__device__ __forceinline__ void flush_counts(long long nf, long long mf, CtrSlot* out) {
+// Sum (nf, mf) over the CTA and add them to the level's counters (and the
+// CTA's count of candidates left for the next pull, when given).
+__device__ __forceinline__ void flush_counts(long long nf, long long mf, CtrSlot* out, const int* s_cn = nullptr) {
     __shared__ long long s_nf[kWarps], s_mf[kWarps];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
@@ -224,7 +225,19 @@ __device__ __forceinline__ void flush_counts(long long nf, long long mf, CtrSlot
         for (int i = 0; i < kWarps; ++i) { a += s_nf[i]; b += s_mf[i]; }
         if (a) atomicAdd(&out->nf, (unsigned long long)a);
         if (b) atomicAdd(&out->mf, (unsigned long long)b);
+        if (s_cn && *s_cn) atomicAdd(&out->nc, (unsigned long long)*s_cn);
     }
+}
+
+// Append v (lanes with `keep`) to this CTA's candidate list: one shared
+// reservation per warp.  Must be reached by the full warp.
+__device__ __forceinline__ void warp_keep(bool keep, int v, int lane, int32_t* list, int* s_cn) {
+    const unsigned b = __ballot_sync(kFull, keep);
+    if (!b) return;
+    int base = 0;
+    if (lane == 0) base = atomicAdd(s_cn, __popc(b));
+    base = __shfl_sync(kFull, base, 0);
+    if (keep) list[base + __popc(b & ((1u << lane) - 1u))] = v;
 }
 
 // Load the 32 queue entries starting at slot b (one per lane).
@@ -415,9 +428,12 @@ __device__ __forceinline__ uint32_t bm_word(const uint32_t* vcur, int w) {
     return __ldcg(vcur + w);
 }
 
+// BOVM pull over the whole bitmap (Alg. 1 / Eq. 4).  With `keep` (this
+// CTA's region of a candidate list) every candidate left unreached is
+// appended to it, for list pulls at the following levels.
 template <bool kSmem>
 __device__ void pull_level(const SsspArgs& a, int step, const uint32_t* vcur, uint32_t* vnext,
-                           long long& nf, long long& mf) {
+                           long long& nf, long long& mf, int32_t* keep, int* s_cn) {
     constexpr int U = 2;  // bitmap words per warp per round
     const int lane = threadIdx.x & 31;
     const int gw = blockIdx.x * kWarps + (threadIdx.x >> 5);
@@ -526,7 +542,86 @@ __device__ void pull_level(const SsspArgs& a, int step, const uint32_t* vcur, ui
                 mf += symmetric ? (ie[u] - ib[u]) : (__ldg(a.row_ptr + v + 1) - __ldg(a.row_ptr + v));
             }
             if (lane == 0) vnext[w] = cur[u] | newbits;
+            if (keep) warp_keep(cand[u] && !found[u], (w << 5) + lane, lane, keep, s_cn);
         }
+    }
+}
+
+// BOVM pull over this CTA's list of candidates (the vertices a pull left
+// unreached), instead of the whole bitmap.  The step-start visited test reads
+// the distances: 0 <= dist[u] < step exactly when u was reached before this
+// level (vertices found now carry dist = step), so found vertices can be set
+// in the visited bitmap in place.  Found rows go straight to the push queue
+// (a push level may follow); candidates still unreached move to `keep`.
+__device__ __noinline__ void list_pull_level(const SsspArgs& a, int step, uint32_t* vis, const int32_t* cand, int ncand,
+                                int32_t* keep, int* s_cn, Queue qout, unsigned long long* qpack, long long& nf,
+                                long long& mf) {
+    const int lane = threadIdx.x & 31;
+    const bool symmetric = a.in_ptr == a.row_ptr;
+    // one candidate per thread and round; the loop bound is the same for the whole warp
+    for (int base = threadIdx.x & ~31; base < ncand; base += kThreads) {
+        const int i = base + lane;
+        const bool has = i < ncand;
+        const int v = has ? __ldcg(cand + i) : 0;
+        int ib = 0, ie = 0;
+        if (has) {
+            ib = __ldg(a.in_ptr + v);
+            ie = __ldg(a.in_ptr + v + 1);
+        }
+        int j = ib;
+        bool found = false;
+        const int jl = min(ie, ib + a.pull_serial);
+        while (!found && j < jl) {
+            int uu[4], du[4];
+#pragma unroll
+            for (int x = 0; x < 4; ++x) uu[x] = j + x < jl ? __ldg(a.in_idx + j + x) : -1;
+#pragma unroll
+            for (int x = 0; x < 4; ++x) du[x] = uu[x] >= 0 ? __ldcg(a.dist + uu[x]) : -1;
+#pragma unroll
+            for (int x = 0; x < 4; ++x) found |= du[x] >= 0 && du[x] < step;
+            j = min(j + 4, jl);
+        }
+        // rows with in-arcs left: packed 32 at a time across the warp, as in pull_level
+        while (true) {
+            const int rem = (has && !found) ? ie - j : 0;
+            const int incl = warp_inclusive_scan(rem, lane);
+            const int total = __shfl_sync(kFull, incl, 31);
+            if (total == 0) break;
+            const int ex = incl - rem;
+            int o = 0;
+#pragma unroll
+            for (int bb = 16; bb > 0; bb >>= 1) {
+                const int cidx = o + bb;
+                const int pv = __shfl_sync(kFull, ex, cidx);
+                if (pv <= lane) o = cidx;
+            }
+            const int oj = __shfl_sync(kFull, j, o);
+            const int oex = __shfl_sync(kFull, ex, o);
+            bool hh = false;
+            if (lane < total) {
+                const int x = __ldg(a.in_idx + oj + (lane - oex));
+                const int dx = __ldcg(a.dist + x);
+                hh = dx >= 0 && dx < step;
+            }
+            const unsigned hits = __ballot_sync(kFull, hh);
+            if (rem > 0 && ex < 32) {
+                const int hi = min(32, ex + rem);
+                const unsigned seg = (hi >= 32 ? kFull : ((1u << hi) - 1u)) & ~((1u << ex) - 1u);
+                if (hits & seg) found = true;
+                j += hi - ex;
+            }
+        }
+        int rb = 0, re = 0;
+        if (found) {
+            a.dist[v] = step;
+            atomicOr(vis + (v >> 5), 1u << (v & 31));
+            rb = symmetric ? ib : __ldg(a.row_ptr + v);
+            re = symmetric ? ie : __ldg(a.row_ptr + v + 1);
+            nf += 1;
+            mf += re - rb;
+        }
+        warp_enqueue(found, rb, re, lane, qout, qpack);
+        warp_keep(has && !found, v, lane, keep, s_cn);
     }
 }
 
@@ -558,7 +653,8 @@ __device__ void bitmap_to_queue(const SsspArgs& a, const uint32_t* vnow, const u
 
 __global__ void __launch_bounds__(kThreads, DAWN_SSSP_MIN_CTAS) sssp_kernel(SsspArgs a) {
     Ctl* ctl = a.ctl;
-    __shared__ unsigned long long s_snap[3];  // {qpack, nf, mf} of the level just finished
+    __shared__ unsigned long long s_snap[4];  // {qpack, nf, mf, nc} of the level just finished
+    __shared__ int s_cn, s_cin;               // this CTA's candidates: being kept / to test
     __shared__ int s_status;
     if (threadIdx.x == 0) s_status = ld_relaxed_s32(&ctl->status);
     __syncthreads();
@@ -612,8 +708,18 @@ __global__ void __launch_bounds__(kThreads, DAWN_SSSP_MIN_CTAS) sssp_kernel(Sssp
     long long prev_nf = 0;
     long long reached = 0, edges = 0;
     int pushes = 0, pulls = 0;
-    bool last_pull = false;
+    // level kinds: push (SOVM), pull over the bitmap, pull over the candidate lists
+    enum { kPush = 0, kBitmapPull = 1, kListPull = 2 };
+    int last = kPush;
     int step = 0;
+    // this CTA's region of the candidate lists: the bitmap words its warps scan
+    const int nwarps = gridDim.x * kWarps;
+    const long long region = (long long)kWarps * ((a.nwords + nwarps - 1) / nwarps) * 32;
+    const bool lists = a.cand0 != nullptr && region * gridDim.x <= a.cand_cap;
+    int32_t* cl[2] = {a.cand0 + blockIdx.x * region, a.cand1 + blockIdx.x * region};
+    int cpar = 0;  // the list the next list pull reads
+    if (threadIdx.x == 0) s_cn = s_cin = 0;
+    __syncthreads();
     while (true) {
         CtrSlot* cur = &ctl->ctr[step % 3];
         // the frontier found at step s lives in queue (s & 1)
@@ -626,16 +732,21 @@ __global__ void __launch_bounds__(kThreads, DAWN_SSSP_MIN_CTAS) sssp_kernel(Sssp
         reached += nf_cur;
         edges += mf_cur;
         mu -= mf_cur;
-        bool pull;
-        if (a.mode == DAWN_MODE_PUSH) pull = false;
-        else if (a.mode == DAWN_MODE_PULL) pull = true;
-        else if (!last_pull) pull = mf_cur * a.alpha > mu;
-        else pull = !(nf_cur * a.beta < a.n && nf_cur < prev_nf);
+        const long long nc_cur = (long long)s_snap[3];  // unreached candidates, after a pull
+        int kind;
+        if (a.mode == DAWN_MODE_PUSH) kind = kPush;
+        else if (a.mode == DAWN_MODE_PULL) kind = (last != kPush && lists) ? kListPull : kBitmapPull;
+        else if (last == kPush) kind = mf_cur * a.alpha > mu ? kBitmapPull : kPush;
+        // after a pull: test only the candidates left while they are few
+        // next to the frontier's arcs; otherwise the push / pull rule
+        else if (lists && nc_cur <= 4 * mf_cur) kind = kListPull;
+        else kind = (nf_cur * a.beta < a.n && nf_cur < prev_nf) ? kPush : kBitmapPull;
+        const bool pull = kind != kPush;
         prev_nf = nf_cur;
         if (blockIdx.x == 0 && threadIdx.x < (int)(sizeof(CtrSlot) / 8))
             reinterpret_cast<unsigned long long*>(&ctl->ctr[(step + 2) % 3])[threadIdx.x] = 0;
 
-        if (!pull && last_pull) {
+        if (kind == kPush && last == kBitmapPull) {
             // the frontier exists only as a bitmap difference: turn it into a queue
             bitmap_to_queue(a, vcur, vnext, qcur, &cur->qpack);
             if (!grid_barrier(ctl, bar, bar_target, a.spin_limit, cur, s_snap)) return;
@@ -644,23 +755,35 @@ __global__ void __launch_bounds__(kThreads, DAWN_SSSP_MIN_CTAS) sssp_kernel(Sssp
         }
         CtrSlot* out = &ctl->ctr[(step + 1) % 3];
         long long nf = 0, mf = 0;
-        if (pull) {
-            if (a.smem_words > 0) pull_level<true>(a, step + 1, vcur, vnext, nf, mf);
-            else pull_level<false>(a, step + 1, vcur, vnext, nf, mf);
+        if (kind == kBitmapPull) {
+            int32_t* keep = lists ? cl[cpar] : nullptr;
+            if (a.smem_words > 0) pull_level<true>(a, step + 1, vcur, vnext, nf, mf, keep, &s_cn);
+            else pull_level<false>(a, step + 1, vcur, vnext, nf, mf, keep, &s_cn);
+            ++pulls;
+        } else if (kind == kListPull) {
+            list_pull_level(a, step + 1, vcur, cl[cpar], s_cin, cl[cpar ^ 1], &s_cn, qnext, &out->qpack, nf, mf);
+            cpar ^= 1;
             ++pulls;
         } else {
             push_level(a, step + 1, vcur, qcur, qpack, qnext, out, nf, mf);
             ++pushes;
         }
-        flush_counts(nf, mf, out);
+        flush_counts(nf, mf, out, pull ? &s_cn : nullptr);
         if (!grid_barrier(ctl, bar, bar_target, a.spin_limit, out, s_snap)) return;
-        if (tracer) trace_rec(a, tslot, pull ? 3 : 2, step + 1, (long long)s_snap[1]);
         if (pull) {
+            if (threadIdx.x == 0) {
+                s_cin = s_cn;  // the list just written is the one the next list pull reads
+                s_cn = 0;
+            }
+            __syncthreads();
+        }
+        if (tracer) trace_rec(a, tslot, kind == kPush ? 2 : (kind == kBitmapPull ? 3 : 5), step + 1, (long long)s_snap[1]);
+        if (kind == kBitmapPull) {
             uint32_t* t = vcur;
             vcur = vnext;
             vnext = t;
         }
-        last_pull = pull;
+        last = kind;
         ++step;
     }
     if (gtid == 0 && a.stats) {
@@ -727,6 +850,9 @@ int sssp_launch(dawn_graph* g, int32_t src, int32_t* dist_dev, const dawn_sssp_o
     int bps = g->sssp_blocks_per_sm;
     if (opts && opts->blocks_per_sm > 0 && opts->blocks_per_sm < bps) bps = opts->blocks_per_sm;
     a.smem_words = g->sssp_smem_bytes / 4;
+    a.cand0 = g->cand[0];
+    a.cand1 = g->cand[1];
+    a.cand_cap = g->cand_cap;
     a.bar_parity = (int32_t)(g->sssp_launches & 1u);
     dim3 grid(g->sms * bps), block(kThreads);
     void* args[] = {&a};
@@ -865,6 +991,9 @@ int sssp_noalloc(const int32_t* row_ptr, const int32_t* col_idx, int32_t n, int6
     a.mode = DAWN_MODE_PUSH;
     a.bar_parity = 0;  // the whole control block was just zeroed
     a.smem_words = 0;
+    a.cand0 = nullptr;  // push only: no candidate lists
+    a.cand1 = nullptr;
+    a.cand_cap = 0;
     a.alpha = 15;
     a.beta = 18;
     a.pull_serial = 8;
