@@ -735,7 +735,8 @@ __global__ void __launch_bounds__(kThreads, DAWN_SSSP_MIN_CTAS) sssp_kernel(Sssp
         const long long nc_cur = (long long)s_snap[3];  // unreached candidates, after a pull
         int kind;
         if (a.mode == DAWN_MODE_PUSH) kind = kPush;
-        else if (a.mode == DAWN_MODE_PULL) kind = (last != kPush && lists) ? kListPull : kBitmapPull;
+        else if (a.mode == DAWN_MODE_PULL)
+            kind = (last != kPush && lists && nc_cur <= 4 * mf_cur) ? kListPull : kBitmapPull;
         else if (last == kPush) kind = mf_cur * a.alpha > mu ? kBitmapPull : kPush;
         // after a pull: test only the candidates left while they are few
         // next to the frontier's arcs; otherwise the push / pull rule
