@@ -81,6 +81,15 @@ extern "C" {
 #define DAWN_REQ_DONE    2 /* every distance row is in the caller's buffer */
 #define DAWN_REQ_FAILED  3 /* the request ended with an error (see dawn_serve_poll's return) */
 
+/* Where one source's level loop runs (dawn_sssp_opts.engine). */
+#define DAWN_ENGINE_AUTO    0 /* CLUSTER for low-degree graphs (m < 8n) whose visited bitmap fits the
+                                 cluster's shared memory, in AUTO or PUSH mode without a trace; else GRID */
+#define DAWN_ENGINE_GRID    1 /* one persistent cooperative grid over every SM, grid barrier per level */
+#define DAWN_ENGINE_CLUSTER 2 /* one thread-block cluster (16 CTAs, or 8): visited bitmap in distributed
+                                 shared memory, frontier lists in shared memory, cluster barrier per
+                                 level; SOVM push only (Alg. 3); DAWN_E_INVALID when the bitmap does not
+                                 fit (n above about 24 M) or with DAWN_MODE_PULL or a trace */
+
 /* Per-graph server step (dawn_serve_create_ex). */
 #define DAWN_SERVE_AUTO     0 /* FRONTIER when the average out-degree m / n is below 8, else DENSE */
 #define DAWN_SERVE_DENSE    1 /* every iteration pulls every vertex (bit-lane Alg. 1 over the CSC) */
@@ -137,6 +146,8 @@ typedef struct {
     int32_t trace_cap;     /* records that fit in trace */
     int32_t pull_serial;   /* in-neighbours a lane tests on its own in a pull level before
                               the warp takes the rest of the row; 0 = tuned or 8 */
+    int32_t engine;        /* DAWN_ENGINE_*; 0 = AUTO */
+    int32_t reserved;      /* 0 */
 } dawn_sssp_opts;
 
 typedef struct {

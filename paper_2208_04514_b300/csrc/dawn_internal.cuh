@@ -89,6 +89,13 @@ struct dawn_graph {
     int64_t queue_cap = 0;
     int32_t* dist_tmp = nullptr;      // result staging for host outputs
     int32_t* cand[2] = {nullptr, nullptr};  // per-CTA lists of unreached pull candidates
+    // cluster engine (set up on first use): CTAs per cluster (0 = not yet, -1 = unavailable),
+    // dynamic shared memory per CTA, frontier entries per CTA list, overflow lists + counters
+    int cl_size = 0;
+    int cl_smem = 0;
+    int cl_qcap = 0;
+    int32_t* cl_ovf = nullptr;        // 3 lists of n entries
+    unsigned* cl_ovf_n = nullptr;     // their 3 counts
     int64_t cand_cap = 0;             // entries per list
     dawn::Ctl* ctl = nullptr;         // device control block
     dawn_sssp_stats* stats_dev = nullptr;
@@ -117,4 +124,7 @@ int sssp_launch(dawn_graph* g, int32_t src, int32_t* dist_dev, const dawn_sssp_o
 int sssp_occupancy(dawn_graph* g);
 // graph.cu
 int graph_sync_status(dawn_graph* g, cudaStream_t stream);
+// cluster.cu: one source on a single thread-block cluster; DAWN_E_INVALID when unavailable
+int cluster_launch(dawn_graph* g, int32_t src, int32_t* dist_dev, const dawn_sssp_opts* opts,
+                   dawn_sssp_stats* stats_dev, cudaStream_t st);
 }  // namespace dawn

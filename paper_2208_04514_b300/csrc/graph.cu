@@ -189,6 +189,8 @@ void release(dawn_graph* g) {
     f(g->dist_tmp);
     f(g->cand[0]);
     f(g->cand[1]);
+    f(g->cl_ovf);
+    f(g->cl_ovf_n);
     f(g->ctl);
     f(g->stats_dev);
     f(g->ms_vis[0]);

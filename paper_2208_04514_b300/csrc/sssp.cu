@@ -817,6 +817,17 @@ int sssp_occupancy(dawn_graph* g) {
 
 int sssp_launch(dawn_graph* g, int32_t src, int32_t* dist_dev, const dawn_sssp_opts* opts,
                 dawn_sssp_stats* stats_dev, cudaStream_t st) {
+    const int engine = opts ? opts->engine : DAWN_ENGINE_AUTO;
+    if (engine < DAWN_ENGINE_AUTO || engine > DAWN_ENGINE_CLUSTER) return fail(DAWN_E_INVALID, "unknown engine %d", engine);
+    if (opts && (opts->mode < DAWN_MODE_AUTO || opts->mode > DAWN_MODE_PULL))
+        return fail(DAWN_E_INVALID, "unknown mode %d", opts->mode);
+    if (engine == DAWN_ENGINE_CLUSTER) return cluster_launch(g, src, dist_dev, opts, stats_dev, st);
+    if (engine == DAWN_ENGINE_AUTO && g->m < 8 * (int64_t)g->n && g->cl_size >= 0 &&
+        (!opts || (opts->mode != DAWN_MODE_PULL && !opts->trace))) {
+        // low-degree graph: many levels with small frontiers, one cluster runs them
+        const int rc = cluster_launch(g, src, dist_dev, opts, stats_dev, st);
+        if (rc == DAWN_OK || g->cl_size >= 0) return rc;  // else unavailable: the grid below
+    }
     SsspArgs a;
     a.row_ptr = g->row_ptr;
     a.col_idx = g->col_idx;

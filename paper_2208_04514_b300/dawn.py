@@ -40,6 +40,10 @@ DAWN_REQ_RUNNING = 1
 DAWN_REQ_DONE = 2
 DAWN_REQ_FAILED = 3
 
+DAWN_ENGINE_AUTO = 0
+DAWN_ENGINE_GRID = 1
+DAWN_ENGINE_CLUSTER = 2
+
 DAWN_SERVE_AUTO = 0
 DAWN_SERVE_DENSE = 1
 DAWN_SERVE_FRONTIER = 2
@@ -57,7 +61,8 @@ class DawnError(RuntimeError):
 class dawn_sssp_opts(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int32), ("alpha", ctypes.c_int32), ("beta", ctypes.c_int32),
                 ("blocks_per_sm", ctypes.c_int32), ("spin_limit", ctypes.c_int64),
-                ("trace", ctypes.c_void_p), ("trace_cap", ctypes.c_int32), ("pull_serial", ctypes.c_int32)]
+                ("trace", ctypes.c_void_p), ("trace_cap", ctypes.c_int32), ("pull_serial", ctypes.c_int32),
+                ("engine", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class dawn_sssp_stats(ctypes.Structure):

@@ -16,7 +16,11 @@ from paper_2208_04514_b300 import graphgen as gg
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-MODES = [0, 1, 2]  # auto, push only (Alg. 3), pull only (Alg. 1)
+# traversal modes (auto, push only = Alg. 3, pull only = Alg. 1) on both
+# engines (the grid-wide loop and the single-cluster loop, push only), and the
+# automatic choice of both
+MODES = [{"mode": 0, "engine": 1}, {"mode": 1, "engine": 1}, {"mode": 2, "engine": 1},
+         {"mode": 0, "engine": 2}, {"mode": 1, "engine": 2}, {"mode": 0, "engine": 0}]
 
 
 def upload(dawn, g):
@@ -24,13 +28,14 @@ def upload(dawn, g):
     return dawn.dawn_graph_upload(g.row_ptr, g.col_idx, flags=flags)
 
 
-def gpu_sssp(dawn, h, n, src, mode=0, host=False):
+def gpu_sssp(dawn, h, n, src, opts=None, host=False):
+    opts = opts or {}
     if host:
         d = np.full(n, -7, dtype=np.int32)
-        st = dawn.dawn_sssp_ex(h, src, d, {"mode": mode})
+        st = dawn.dawn_sssp_ex(h, src, d, opts)
         return d, st
     d = torch.full((n,), -7, dtype=torch.int32, device="cuda")
-    st = dawn.dawn_sssp_ex(h, src, d, {"mode": mode})
+    st = dawn.dawn_sssp_ex(h, src, d, opts)
     return d.cpu().numpy(), st
 
 
@@ -183,6 +188,10 @@ def test_invalid_inputs(dawn):
             assert ei.value.code == dawn.DAWN_E_INVALID
         with pytest.raises(dawn.DawnError):
             dawn.dawn_sssp_ex(h, 0, d, {"mode": 7})
+        with pytest.raises(dawn.DawnError):
+            dawn.dawn_sssp_ex(h, 0, d, {"engine": 7})
+        with pytest.raises(dawn.DawnError):
+            dawn.dawn_sssp_ex(h, 0, d, {"engine": 2, "mode": 2})
     finally:
         dawn.dawn_graph_free(h)
 
@@ -266,6 +275,10 @@ def test_lattice_4096_full_size(dawn):
             assert oracle.certificate(g.row_ptr, g.col_idx, int(s), dh) == (0, -1)
             check_stats(g, dh, st)
             assert st["levels"] > 4000
+            # the grid-wide engine on the same source (AUTO takes the cluster here)
+            st = dawn.dawn_sssp_ex(h, int(s), d, {"engine": 1})
+            np.testing.assert_array_equal(d.cpu().numpy(), dh)
+            check_stats(g, dh, st)
     finally:
         dawn.dawn_graph_free(h)
 
