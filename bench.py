@@ -229,11 +229,12 @@ def _flush(buf, i):
     buf.fill_(i)
 
 
-def bench_lattice(dawn, torch, flush, nsrc=16):
+def bench_lattice(dawn, torch, flush, nsrc=16, side=4096):
     """4096^2 lattice, bonds deleted with p = 0.1 (seed 3), 16 uniform sources
-    (seed 7): GTEPS and microseconds per level of the persistent level loop."""
+    (seed 7): GTEPS and microseconds per level of the level loop (AUTO: the
+    single-cluster engine on this low-degree graph)."""
     from paper_2208_04514_b300 import graphgen as gg
-    g = gg.lattice(4096, 4096, 0.1, seed=3)
+    g = gg.lattice(side, side, 0.1, seed=3)
     srcs = gg.uniform_vertices(g.n, nsrc, seed=7)
     stream = torch.cuda.current_stream()
     h = dawn.dawn_graph_upload(g.row_ptr, g.col_idx, flags=dawn.DAWN_SYMMETRIC, stream=stream)
@@ -252,7 +253,7 @@ def bench_lattice(dawn, torch, flush, nsrc=16):
     dawn.dawn_graph_free(h)
     edges = sum(x["edges"] for x in st)
     levels = sum(x["levels"] for x in st)
-    return {"workload": "lattice4096_p0.1_sssp_16src", "n": g.n, "m": g.m,
+    return {"workload": f"lattice{side}_p0.1_sssp_{nsrc}src", "n": g.n, "m": g.m,
             "gteps": edges / (sum(ms) * 1e-3) / 1e9, "ms_per_source": sum(ms) / nsrc,
             "us_per_level": 1e3 * sum(ms) / levels, "levels_median": statistics.median(x["levels"] for x in st),
             "l2": "flushed between sources"}
@@ -645,7 +646,7 @@ def run_one(args):
     torch.cuda.set_device(0)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.int32, device="cuda")
     if args.workload == "lattice":
-        out = bench_lattice(dawn, torch, flush)
+        out = bench_lattice(dawn, torch, flush, nsrc=args.lattice_sources, side=args.lattice_side)
     elif args.workload == "modes":
         g, srcs = build_workload()
         out = bench_modes(dawn, torch, flush, g, srcs)
@@ -679,6 +680,8 @@ def main():
     ap.add_argument("--workload", choices=["all", "lattice", "batched", "serving", "tree", "centrality", "modes"], default="all",
                     help="run one secondary workload alone and print its figures (profiling runs; not a bench line)")
     ap.add_argument("--batched-k", type=int, default=0, help="with --workload batched: sources (0 = all)")
+    ap.add_argument("--lattice-side", type=int, default=4096, help="with --workload lattice: side of the lattice")
+    ap.add_argument("--lattice-sources", type=int, default=16, help="with --workload lattice: sources")
     ap.add_argument("--batched-lanes", type=int, default=0, help="with --workload batched: one lane width")
     ap.add_argument("--no-secondary", action="store_true",
                     help="skip the lattice, batched and serving workloads reported beside the headline")
