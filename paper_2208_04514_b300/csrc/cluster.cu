@@ -258,17 +258,20 @@ int cluster_launch(dawn_graph* g, int32_t src, int32_t* dist_dev, const dawn_sss
         int dev_smem = 0;
         DAWN_CUDA_TRY(cudaDeviceGetAttribute(&dev_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, g->device));
         DAWN_CUDA_TRY(cudaFuncSetAttribute(cluster_sssp_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+        // the dynamic shared memory limit belongs to the kernel, not to the graph:
+        // raise it once to all the kernel can take, so that graphs set up later
+        // never lower it under an earlier graph's launches
+        cudaFuncAttributes fa;
+        DAWN_CUDA_TRY(cudaFuncGetAttributes(&fa, cluster_sssp_kernel));
+        const int dyn_max = dev_smem - (int)fa.sharedSizeBytes;
+        DAWN_CUDA_TRY(cudaFuncSetAttribute(cluster_sssp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_max));
         for (int C : {16, 8}) {
             const long long S = ((long long)g->nwords + C - 1) / C;
             const long long room = (long long)dev_smem - (long long)sizeof(ClShared) - 1024 - S * 4;
             const long long qcap = std::min<long long>(8192, room / 8);
             if (qcap < 1024) continue;
             const int smem = (int)(S * 4 + qcap * 8);
-            if (cudaFuncSetAttribute(cluster_sssp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
-                cudaSuccess) {
-                cudaGetLastError();
-                continue;
-            }
+            if (smem > dyn_max) continue;
             cudaLaunchConfig_t cfg = {};
             cudaLaunchAttribute attr[1];
             attr[0].id = cudaLaunchAttributeClusterDimension;

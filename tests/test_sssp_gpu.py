@@ -311,3 +311,21 @@ def test_many_sources_rows(dawn, where):
         assert ei.value.code == dawn.DAWN_E_INVALID
     finally:
         dawn.dawn_graph_free(h)
+
+
+def test_cluster_engine_graphs_of_different_sizes(dawn):
+    """The cluster engine's shared-memory limit belongs to the kernel: setting
+    up a smaller graph after a larger one must not break the larger one's
+    launches (they need more dynamic shared memory)."""
+    big = gg.lattice(1024, 1024, 0.1, seed=3)
+    small = gg.lattice(40, 40, 0.1, seed=4)
+    hb, hs = upload(dawn, big), upload(dawn, small)
+    try:
+        opts = {"engine": 2}
+        for h, g, s in ((hb, big, 0), (hs, small, 0), (hb, big, 777), (hs, small, 99)):
+            d, st = gpu_sssp(dawn, h, g.n, s, opts)
+            np.testing.assert_array_equal(d, oracle.bfs_queue(g.row_ptr, g.col_idx, s))
+            check_stats(g, d, st)
+    finally:
+        dawn.dawn_graph_free(hb)
+        dawn.dawn_graph_free(hs)
