@@ -210,6 +210,15 @@ DAWN_API int dawn_sssp_tree_async(dawn_graph_t g, int32_t src, int32_t* dist_dev
 DAWN_API int dawn_sssp_many(dawn_graph_t g, const int32_t* sources, int32_t k, int32_t* dist,
                             dawn_sssp_stats* stats, const dawn_sssp_opts* opts, void* stream);
 
+/*
+ * Diagnostic (no counterpart in the paper): this GPU's L2 read bandwidth in
+ * GB/s, the denominator for kernels whose working set stays in L2.  A device
+ * buffer of `bytes` (>= 1 MiB; pick one that fits in L2) is read `passes`
+ * times with 16-byte loads by every SM after one untimed pass; *gbs receives
+ * bytes * passes / time.  Synchronizes `stream`.
+ */
+DAWN_API int dawn_l2_read_gbs(int64_t bytes, int32_t passes, double* gbs, void* stream);
+
 /* Synchronize `stream` and return (then clear) the sticky device status of g:
  * DAWN_OK, DAWN_E_TIMEOUT or DAWN_E_OVERFLOW. */
 DAWN_API int dawn_graph_sync(dawn_graph_t g, void* stream);

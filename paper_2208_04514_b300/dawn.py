@@ -119,6 +119,7 @@ _SIGNATURES = {
     "dawn_serve_times": [_vp, _u64, _vp, _vp],
     "dawn_serve_drain": [_vp, _i64],
     "dawn_serve_destroy": [_vp],
+    "dawn_l2_read_gbs": [_i64, _i32, _vp, _vp],
     "dawn_last_error": [],
     "dawn_version": [],
 }
@@ -304,6 +305,13 @@ def dawn_centrality(g: int, sources, k: int | None = None, ecc=None, dsum=None, 
                                   _ptr(harmonic), ctypes.byref(summ), ctypes.byref(o) if o else None,
                                   _stream(stream)))
     return {f: getattr(summ, f) for f, _ in summ._fields_}
+
+
+def dawn_l2_read_gbs(nbytes: int = 64 << 20, passes: int = 50, stream=None) -> float:
+    """This GPU's L2 read bandwidth (GB/s) from an L2-resident buffer."""
+    out = ctypes.c_double(0.0)
+    _check(load().dawn_l2_read_gbs(nbytes, passes, ctypes.byref(out), _stream(stream)))
+    return out.value
 
 
 # -------------------------------------------------------------- autotune --
