@@ -459,6 +459,37 @@ def bench_modes(dawn, torch, flush, g_rmat, srcs_rmat, nsrc=16):
     return out
 
 
+def bench_many_graph(dawn, torch, g, srcs):
+    """dawn_sssp_many with device rows on the headline graph and sources: the
+    first call captures the 64 level-loop launches as a CUDA graph, the next
+    calls replay it; against the same 64 launches issued one by one (warm L2,
+    no flush: a launch-overhead comparison)."""
+    stream = torch.cuda.current_stream()
+    h = dawn.dawn_graph_upload(g.row_ptr, g.col_idx, flags=dawn.DAWN_SYMMETRIC, stream=stream)
+    src_dev = torch.from_numpy(np.ascontiguousarray(srcs, dtype=np.int32)).cuda()
+    rows = torch.empty((len(srcs), g.n), dtype=torch.int32, device="cuda")
+    stats = torch.zeros((len(srcs), dawn.STATS_WORDS), dtype=torch.int64, device="cuda")
+    dawn.dawn_sssp_many(h, src_dev, dist=rows, stats=stats, stream=stream)  # capture
+    torch.cuda.synchronize()
+    reps = 5
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        dawn.dawn_sssp_many(h, src_dev, dist=rows, stats=stats, stream=stream)  # replays
+    torch.cuda.synchronize()
+    t_graph = (time.perf_counter() - t0) / reps
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        for i, s in enumerate(srcs):
+            dawn.dawn_sssp_async(h, int(s), rows[i], None, stats[i], stream)
+        dawn.dawn_graph_sync(h, stream)
+    t_direct = (time.perf_counter() - t0) / reps
+    edges = sum(dawn.stats_from_words(r)["edges"] for r in stats.cpu().numpy())
+    dawn.dawn_graph_free(h)
+    return {"workload": "rmat20_sssp_many_64src_device_rows", "gteps_graph_replay": edges / t_graph / 1e9,
+            "gteps_direct_launches": edges / t_direct / 1e9, "us_per_source_graph": 1e6 * t_graph / len(srcs),
+            "us_per_source_direct": 1e6 * t_direct / len(srcs), "timing": "wall clock per call, warm L2"}
+
+
 def bench_centrality(dawn, torch, flush, lanes=256):
     """RMAT scale 16 (seed 4), all 65,536 sources: dawn_centrality (ecc,
     distance sum, reached, closeness, harmonic per source, and the diameter /
@@ -717,7 +748,8 @@ def run_gpu(args):
                              "batched": bench_batched(dawn, torch, flush),
                              "tree": bench_tree(dawn, torch, flush, g, srcs, peak),
                              "centrality": bench_centrality(dawn, torch, flush),
-                             "modes": bench_modes(dawn, torch, flush, g, srcs)}
+                             "modes": bench_modes(dawn, torch, flush, g, srcs),
+                             "many_graph": bench_many_graph(dawn, torch, g, srcs)}
         del flush
         torch.cuda.empty_cache()
         line["secondary"]["serving"] = bench_serving(dawn, torch, nreq=args.serve_requests)
@@ -737,6 +769,9 @@ def run_one(args):
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.int32, device="cuda")
     if args.workload == "lattice":
         out = bench_lattice(dawn, torch, flush, nsrc=args.lattice_sources, side=args.lattice_side)
+    elif args.workload == "many":
+        g, srcs = build_workload()
+        out = bench_many_graph(dawn, torch, g, srcs)
     elif args.workload == "modes":
         g, srcs = build_workload()
         out = bench_modes(dawn, torch, flush, g, srcs)
@@ -767,7 +802,7 @@ def main():
                     help="use only the first N of the 64 sources (small profiling runs; not a bench value)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end host-buffer pass")
     ap.add_argument("--serve-requests", type=int, default=48, help="requests per arrival rate in the serving mix")
-    ap.add_argument("--workload", choices=["all", "lattice", "batched", "serving", "tree", "centrality", "modes"], default="all",
+    ap.add_argument("--workload", choices=["all", "lattice", "batched", "serving", "tree", "centrality", "modes", "many"], default="all",
                     help="run one secondary workload alone and print its figures (profiling runs; not a bench line)")
     ap.add_argument("--batched-k", type=int, default=0, help="with --workload batched: sources (0 = all)")
     ap.add_argument("--lattice-side", type=int, default=4096, help="with --workload lattice: side of the lattice")

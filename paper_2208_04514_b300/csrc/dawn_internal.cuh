@@ -96,6 +96,7 @@ struct dawn_graph {
     int cl_qcap = 0;
     int32_t* cl_ovf = nullptr;        // 3 lists of n entries
     unsigned* cl_ovf_n = nullptr;     // their 3 counts
+    void* many_graph = nullptr;       // dawn_sssp_many: last captured CUDA graph of launches (many.cu)
     int64_t cand_cap = 0;             // entries per list
     dawn::Ctl* ctl = nullptr;         // device control block
     dawn_sssp_stats* stats_dev = nullptr;
@@ -124,6 +125,8 @@ int sssp_launch(dawn_graph* g, int32_t src, int32_t* dist_dev, const dawn_sssp_o
 int sssp_occupancy(dawn_graph* g);
 // graph.cu
 int graph_sync_status(dawn_graph* g, cudaStream_t stream);
+// many.cu: release the captured graph of dawn_sssp_many
+void many_release(dawn_graph* g);
 // cluster.cu: one source on a single thread-block cluster; DAWN_E_INVALID when unavailable
 int cluster_launch(dawn_graph* g, int32_t src, int32_t* dist_dev, const dawn_sssp_opts* opts,
                    dawn_sssp_stats* stats_dev, cudaStream_t st);

@@ -191,6 +191,7 @@ void release(dawn_graph* g) {
     f(g->cand[1]);
     f(g->cl_ovf);
     f(g->cl_ovf_n);
+    many_release(g);
     f(g->ctl);
     f(g->stats_dev);
     f(g->ms_vis[0]);

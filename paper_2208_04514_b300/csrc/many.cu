@@ -4,9 +4,86 @@
 // device buffers, and the device-to-host copy of source i runs on a copy
 // stream while the level loop of source i + 1 runs, so the transfer hides
 // behind the computation (pinned host memory is needed for the overlap).
+// With device rows the k launches are captured once as a CUDA graph and the
+// graph is replayed while the same call repeats.
+#include <cstring>
 #include <vector>
 
 #include "dawn_internal.cuh"
+
+namespace dawn {
+namespace {
+
+// The k launches of a device-row call, captured once as a CUDA graph and
+// replayed while the same call repeats (same sources, rows, statistics and
+// options).  Consecutive grid launches alternate between two barrier
+// counters, so a replay is valid only when the next launch would start on the
+// parity the capture started on; the host's launch count then advances by k.
+struct ManyGraph {
+    cudaGraphExec_t exec = nullptr;
+    std::vector<int32_t> src;
+    int32_t* dist = nullptr;
+    dawn_sssp_stats* stats = nullptr;
+    dawn_sssp_opts opts;
+    bool has_opts = false;
+    unsigned parity0 = 0;
+    unsigned launches = 0;  // grid launches in the graph
+};
+
+bool same_opts(const ManyGraph& c, const dawn_sssp_opts* o) {
+    if (c.has_opts != (o != nullptr)) return false;
+    return !o || std::memcmp(&c.opts, o, sizeof(dawn_sssp_opts)) == 0;
+}
+
+// Capture the k launches into a new graph (on a private stream, so that the
+// caller's stream may be the legacy default stream).  nullptr when capture
+// is not possible; the launch count is then left unchanged.
+ManyGraph* capture(dawn_graph* g, const std::vector<int32_t>& src, int32_t* dist, dawn_sssp_stats* stats,
+                   const dawn_sssp_opts* opts) {
+    cudaStream_t cs = nullptr;
+    if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    const unsigned before = g->sssp_launches;
+    ManyGraph* c = new ManyGraph();
+    c->parity0 = before & 1u;
+    cudaGraph_t graph = nullptr;
+    bool ok = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    for (size_t i = 0; ok && i < src.size(); ++i)
+        ok = sssp_launch(g, src[i], dist + i * (size_t)g->n, opts, stats ? stats + i : nullptr, cs) == DAWN_OK;
+    const bool ended = cudaStreamEndCapture(cs, &graph) == cudaSuccess;
+    ok = ok && ended && graph && cudaGraphInstantiate(&c->exec, graph, 0) == cudaSuccess;
+    if (graph) cudaGraphDestroy(graph);
+    cudaStreamDestroy(cs);
+    c->launches = g->sssp_launches - before;
+    g->sssp_launches = before;  // nothing ran yet: the count advances when the graph is launched
+    if (!ok) {
+        cudaGetLastError();
+        if (c->exec) cudaGraphExecDestroy(c->exec);
+        delete c;
+        return nullptr;
+    }
+    c->src = src;
+    c->dist = dist;
+    c->stats = stats;
+    c->has_opts = opts != nullptr;
+    if (opts) c->opts = *opts;
+    return c;
+}
+
+}  // namespace
+
+void many_release(dawn_graph* g) {
+    ManyGraph* c = static_cast<ManyGraph*>(g->many_graph);
+    if (c) {
+        if (c->exec) cudaGraphExecDestroy(c->exec);
+        delete c;
+    }
+    g->many_graph = nullptr;
+}
+
+}  // namespace dawn
 
 extern "C" {
 
@@ -40,7 +117,28 @@ DAWN_API int dawn_sssp_many(dawn_graph_t g, const int32_t* sources, int32_t k, i
         }
     }
     int rc = e == cudaSuccess ? DAWN_OK : cuda_fail(e, "dawn_sssp_many (set-up)", __FILE__, __LINE__);
-    for (int32_t i = 0; i < k && rc == DAWN_OK; ++i) {
+    // device rows on the grid engine: replay (or capture) the launches as one CUDA graph
+    const bool cluster = (opts && opts->engine == DAWN_ENGINE_CLUSTER) ||
+                         ((!opts || opts->engine == DAWN_ENGINE_AUTO) && g->m < 8 * (int64_t)g->n &&
+                          (!opts || (opts->mode != DAWN_MODE_PULL && !opts->trace)));
+    int32_t direct = k;  // launches issued one by one below
+    if (rc == DAWN_OK && ddev && !cluster && (!stats || sdev)) {
+        ManyGraph* c = static_cast<ManyGraph*>(g->many_graph);
+        const bool hit = c && c->src == src && c->dist == dist && c->stats == st_dev && same_opts(*c, opts) &&
+                         c->parity0 == (g->sssp_launches & 1u);
+        if (!hit) {
+            many_release(g);
+            c = capture(g, src, dist, st_dev, opts);
+            g->many_graph = c;
+        }
+        if (c) {
+            e = cudaGraphLaunch(c->exec, st);
+            if (e != cudaSuccess) rc = cuda_fail(e, "dawn_sssp_many (graph launch)", __FILE__, __LINE__);
+            else g->sssp_launches += c->launches;
+            direct = 0;  // every launch is in the graph
+        }
+    }
+    for (int32_t i = 0; i < direct && rc == DAWN_OK; ++i) {
         dawn_sssp_stats* si = st_dev ? st_dev + i : nullptr;
         if (ddev) {
             rc = sssp_launch(g, src[i], dist + (size_t)i * row, opts, si, st);

@@ -329,3 +329,27 @@ def test_cluster_engine_graphs_of_different_sizes(dawn):
     finally:
         dawn.dawn_graph_free(hb)
         dawn.dawn_graph_free(hs)
+
+
+def test_many_device_rows_graph_replay(dawn):
+    """Device rows on the grid engine: the first call captures the launches as
+    a CUDA graph, a repeated call replays it.  A direct launch in between
+    changes the barrier-counter parity, so the next call must not replay a
+    graph captured on the other parity: every result stays exact."""
+    g = gg.rmat(14, seed=2)  # high degree: grid engine
+    h = dawn.dawn_graph_upload(g.row_ptr, g.col_idx, flags=dawn.DAWN_SYMMETRIC)
+    try:
+        srcs = gg.sample_sources(g, 9, seed=8)
+        src_dev = torch.from_numpy(srcs).cuda()
+        want = np.stack([oracle.sssp_sovm(g.row_ptr, g.col_idx, int(s)) for s in srcs])
+        dist = torch.full((9, g.n), -7, dtype=torch.int32, device="cuda")
+        one = torch.empty(g.n, dtype=torch.int32, device="cuda")
+        for rep in range(5):
+            dist.fill_(-7)
+            dawn.dawn_sssp_many(h, src_dev, dist=dist)
+            np.testing.assert_array_equal(dist.cpu().numpy(), want, err_msg=f"call {rep}")
+            if rep in (1, 3):
+                dawn.dawn_sssp(h, int(srcs[0]), one)  # one direct launch: the parity flips
+                np.testing.assert_array_equal(one.cpu().numpy(), want[0])
+    finally:
+        dawn.dawn_graph_free(h)
