@@ -34,6 +34,7 @@ _DIR = Path(__file__).resolve().parent
 _SRC = _DIR / "dawn_oracle.c"
 _SO = _DIR / "_lib" / "libdawn_oracle.so"
 _lib = None
+CFLAGS = ["-O2", "-std=c11", "-fPIC", "-shared"]
 
 
 def build(force: bool = False) -> Path:
@@ -41,7 +42,7 @@ def build(force: bool = False) -> Path:
     if force or not _SO.exists() or _SO.stat().st_mtime < _SRC.stat().st_mtime:
         _SO.parent.mkdir(parents=True, exist_ok=True)
         tmp = _SO.with_suffix(".so.tmp")
-        cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", str(tmp), str(_SRC)]
+        cmd = ["gcc", *CFLAGS, "-o", str(tmp), str(_SRC)]
         res = subprocess.run(cmd, capture_output=True, text=True)
         if res.returncode != 0:
             raise RuntimeError(f"oracle build failed:\n{res.stderr}")
