@@ -82,6 +82,7 @@ struct dawn_graph {
     int32_t* in_idx = nullptr;
     uint32_t* excl = nullptr;         // bit v set: v has no in-arc (or v >= n)
     int32_t in_sorted = 0;            // 1: every in-adjacency row is in ascending order
+    int32_t* pull_idx = nullptr;      // in-adjacency rows ordered by out-degree, largest first (pull levels)
     // single-source work buffers
     uint32_t* vis[2] = {nullptr, nullptr};
     int2* queue[2] = {nullptr, nullptr};        // frontier entries {first arc, arc count}

@@ -132,6 +132,76 @@ __global__ void csc_scatter_kernel(const int32_t* __restrict__ rp, const int32_t
 
 // excl bit v = (v >= n) or v has no in-arc: such a vertex is never reached
 // from another vertex, so the pull step never scans it.
+// Pull order: a copy of the in-adjacency whose rows are ordered by the
+// neighbour's out-degree, largest first (smallest id on ties).  Pull levels
+// stop at the first reached in-neighbour, and on skewed graphs the
+// high-degree vertices are reached in the first levels, so this order makes
+// the stop come early.  Key of an arc: (~out-degree, id), sorted ascending.
+__device__ __forceinline__ unsigned long long pull_key(const int32_t* __restrict__ row_ptr, int u) {
+    return ((unsigned long long)(0xffffffffu - (unsigned)(row_ptr[u + 1] - row_ptr[u])) << 32) | (unsigned)u;
+}
+
+// Rows of at most 32 arcs: one warp per row, bitonic sort in registers.
+__global__ void pull_order_warp_kernel(const int32_t* __restrict__ in_ptr, const int32_t* __restrict__ in_idx,
+                                       const int32_t* __restrict__ row_ptr, int32_t n, int32_t* out) {
+    const int lane = threadIdx.x & 31;
+    const long long warps = (long long)gridDim.x * (blockDim.x / 32);
+    for (long long v = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / 32; v < n; v += warps) {
+        const int ib = in_ptr[v], len = in_ptr[v + 1] - ib;
+        if (len > 32) continue;  // warp-uniform
+        unsigned long long key = lane < len ? pull_key(row_ptr, in_idx[ib + lane]) : ~0ull;
+#pragma unroll
+        for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+            for (int jj = k >> 1; jj > 0; jj >>= 1) {
+                const unsigned long long other = __shfl_xor_sync(0xffffffffu, key, jj);
+                const bool up = (lane & k) == 0;
+                const bool lower = (lane & jj) == 0;
+                const bool take_min = up == lower;
+                key = take_min ? (key < other ? key : other) : (key > other ? key : other);
+            }
+        }
+        if (lane < len) out[ib + lane] = (int32_t)(key & 0xffffffffull);
+    }
+}
+
+// Longer rows: one CTA per row, bitonic sort in shared memory over chunks of
+// kPullChunk arcs (rows up to a chunk are fully ordered; longer ones chunk by chunk).
+constexpr int kPullChunk = 2048;
+__global__ void pull_order_cta_kernel(const int32_t* __restrict__ in_ptr, const int32_t* __restrict__ in_idx,
+                                      const int32_t* __restrict__ row_ptr, int32_t n, int32_t* out) {
+    __shared__ unsigned long long sk[kPullChunk];
+    for (long long v = blockIdx.x; v < n; v += gridDim.x) {
+        const int ib = in_ptr[v], ie = in_ptr[v + 1];
+        if (ie - ib <= 32) continue;  // the warp kernel's rows (CTA-uniform)
+        for (int cb = ib; cb < ie; cb += kPullChunk) {
+            const int len = min(kPullChunk, ie - cb);
+            int p2 = 64;
+            while (p2 < len) p2 <<= 1;
+            for (int i = threadIdx.x; i < p2; i += blockDim.x) sk[i] = i < len ? pull_key(row_ptr, in_idx[cb + i]) : ~0ull;
+            __syncthreads();
+            for (int k = 2; k <= p2; k <<= 1) {
+                for (int jj = k >> 1; jj > 0; jj >>= 1) {
+                    for (int i = threadIdx.x; i < p2; i += blockDim.x) {
+                        const int ixj = i ^ jj;
+                        if (ixj > i) {
+                            const unsigned long long x = sk[i], y = sk[ixj];
+                            const bool up = (i & k) == 0;
+                            if ((x > y) == up) {
+                                sk[i] = y;
+                                sk[ixj] = x;
+                            }
+                        }
+                    }
+                    __syncthreads();
+                }
+            }
+            for (int i = threadIdx.x; i < len; i += blockDim.x) out[cb + i] = (int32_t)(sk[i] & 0xffffffffull);
+            __syncthreads();
+        }
+    }
+}
+
 // flag = 1 when some in-adjacency row is not in ascending order (one warp per row).
 __global__ void unsorted_rows_kernel(const int32_t* __restrict__ ptr, const int32_t* __restrict__ idx, int32_t n,
                                      int* flag) {
@@ -187,6 +257,7 @@ void release(dawn_graph* g) {
     f(g->queue_off[0]);
     f(g->queue_off[1]);
     f(g->dist_tmp);
+    f(g->pull_idx);
     f(g->cand[0]);
     f(g->cand[1]);
     f(g->cl_ovf);
@@ -298,6 +369,7 @@ int upload(const int32_t* row_ptr, const int32_t* col_idx, int32_t n, int64_t m,
         (e = alloc((void**)&g->queue_off[0], sizeof(int32_t) * (size_t)g->queue_cap)) != cudaSuccess ||
         (e = alloc((void**)&g->queue_off[1], sizeof(int32_t) * (size_t)g->queue_cap)) != cudaSuccess ||
         (e = alloc((void**)&g->dist_tmp, sizeof(int32_t) * (size_t)n)) != cudaSuccess ||
+        (e = alloc((void**)&g->pull_idx, sizeof(int32_t) * (size_t)(m > 0 ? m : 1))) != cudaSuccess ||
         (e = alloc((void**)&g->cand[0], sizeof(int32_t) * (size_t)g->cand_cap)) != cudaSuccess ||
         (e = alloc((void**)&g->cand[1], sizeof(int32_t) * (size_t)g->cand_cap)) != cudaSuccess ||
         (e = alloc((void**)&g->ctl, sizeof(Ctl))) != cudaSuccess ||
@@ -318,6 +390,15 @@ int upload(const int32_t* row_ptr, const int32_t* col_idx, int32_t n, int64_t m,
     int* unsorted = nullptr;
     if (e == cudaSuccess) e = cudaMallocAsync((void**)&unsorted, sizeof(int), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(unsorted, 0, sizeof(int), st);
+    if (e == cudaSuccess && m > 0) {
+        pull_order_warp_kernel<<<grid_for((int64_t)n * 32, g->sms), kThreads, 0, st>>>(g->in_ptr, g->in_idx,
+                                                                                       g->row_ptr, n, g->pull_idx);
+        e = cudaGetLastError();
+        if (e == cudaSuccess) {
+            pull_order_cta_kernel<<<g->sms * 2, 1024, 0, st>>>(g->in_ptr, g->in_idx, g->row_ptr, n, g->pull_idx);
+            e = cudaGetLastError();
+        }
+    }
     if (e == cudaSuccess && m > 0) {
         unsorted_rows_kernel<<<grid_for((int64_t)n * 32, g->sms), kThreads, 0, st>>>(g->in_ptr, g->in_idx, n,
                                                                                       unsorted);

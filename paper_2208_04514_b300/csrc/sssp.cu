@@ -81,6 +81,7 @@ struct SsspArgs {
     int32_t pull_serial;     // in-neighbours a lane tests alone in a pull level
     int32_t bar_parity;      // which of the two barrier counters this launch uses
     int32_t smem_words;      // > 0: pull levels copy the bitmap (this many words) to shared memory
+    const int32_t* __restrict__ pull_idx;  // in-adjacency rows ordered by out-degree, largest first
     int32_t* cand0;          // per-CTA lists of unreached pull candidates (null: none)
     int32_t* cand1;
     long long cand_cap;      // entries per list
@@ -483,7 +484,7 @@ __device__ void pull_level(const SsspArgs& a, int step, const uint32_t* vcur, ui
             for (int u = 0; u < U; ++u) {
                 const int jl = min(ie[u], ib[u] + a.pull_serial);
 #pragma unroll
-                for (int x = 0; x < 4; ++x) uu[u][x] = (cand[u] && !found[u] && j[u] + x < jl) ? __ldg(a.in_idx + j[u] + x) : -1;
+                for (int x = 0; x < 4; ++x) uu[u][x] = (cand[u] && !found[u] && j[u] + x < jl) ? __ldg(a.pull_idx + j[u] + x) : -1;
             }
 #pragma unroll
             for (int u = 0; u < U; ++u) {
@@ -523,7 +524,7 @@ __device__ void pull_level(const SsspArgs& a, int step, const uint32_t* vcur, ui
                 const int oex = __shfl_sync(kFull, ex, o);
                 bool hh = false;
                 if (lane < total) {
-                    const int x = __ldg(a.in_idx + oj + (lane - oex));
+                    const int x = __ldg(a.pull_idx + oj + (lane - oex));
                     hh = (bm_word<kSmem>(vcur, x >> 5) >> (x & 31)) & 1u;
                 }
                 const unsigned hits = __ballot_sync(kFull, hh);
@@ -574,7 +575,7 @@ __device__ __noinline__ void list_pull_level(const SsspArgs& a, int step, uint32
         while (!found && j < jl) {
             int uu[4], du[4];
 #pragma unroll
-            for (int x = 0; x < 4; ++x) uu[x] = j + x < jl ? __ldg(a.in_idx + j + x) : -1;
+            for (int x = 0; x < 4; ++x) uu[x] = j + x < jl ? __ldg(a.pull_idx + j + x) : -1;
 #pragma unroll
             for (int x = 0; x < 4; ++x) du[x] = uu[x] >= 0 ? __ldcg(a.dist + uu[x]) : -1;
 #pragma unroll
@@ -599,7 +600,7 @@ __device__ __noinline__ void list_pull_level(const SsspArgs& a, int step, uint32
             const int oex = __shfl_sync(kFull, ex, o);
             bool hh = false;
             if (lane < total) {
-                const int x = __ldg(a.in_idx + oj + (lane - oex));
+                const int x = __ldg(a.pull_idx + oj + (lane - oex));
                 const int dx = __ldcg(a.dist + x);
                 hh = dx >= 0 && dx < step;
             }
@@ -862,6 +863,7 @@ int sssp_launch(dawn_graph* g, int32_t src, int32_t* dist_dev, const dawn_sssp_o
     int bps = g->sssp_blocks_per_sm;
     if (opts && opts->blocks_per_sm > 0 && opts->blocks_per_sm < bps) bps = opts->blocks_per_sm;
     a.smem_words = g->sssp_smem_bytes / 4;
+    a.pull_idx = g->pull_idx;
     a.cand0 = g->cand[0];
     a.cand1 = g->cand[1];
     a.cand_cap = g->cand_cap;
@@ -1003,6 +1005,7 @@ int sssp_noalloc(const int32_t* row_ptr, const int32_t* col_idx, int32_t n, int6
     a.mode = DAWN_MODE_PUSH;
     a.bar_parity = 0;  // the whole control block was just zeroed
     a.smem_words = 0;
+    a.pull_idx = nullptr;  // push only
     a.cand0 = nullptr;  // push only: no candidate lists
     a.cand1 = nullptr;
     a.cand_cap = 0;
