@@ -188,6 +188,49 @@ __device__ __forceinline__ int warp_inclusive_scan(int x, int lane) {
 // offset in the level's concatenated arc list grows with its slot index.
 // The low word cannot carry into the high one: a level's arcs total at most
 // m < 2^31.  Must be reached by the full warp.
+// Write the warp's queue entries when some lane has many (a long row): the
+// warp writes 32 entries per pass over its concatenated entry list, each lane
+// finding the owner of its entry by a search over the inclusive scan of the
+// lanes' entry counts, instead of every lane looping over its own entries.
+// rb / re / has describe each lane's up-to-G rows; slot0 / aoff0 are the
+// warp's first queue slot and first arc offset.  Must be reached by the full warp.
+template <int G>
+__device__ __noinline__ void warp_write_entries(const int* rb, const int* re, unsigned has, int cnt, int cincl,
+                                                int ctot, int lane, int slot0, int aoff0, int dincl, int deg,
+                                                Queue q) {
+    for (int e0 = 0; e0 < ctot; e0 += 32) {
+        const int e = e0 + lane;
+        int o = 0;
+#pragma unroll
+        for (int bb = 16; bb > 0; bb >>= 1)
+            if (__shfl_sync(kFull, cincl, o + bb - 1) <= e) o += bb;
+        const int ofirst = __shfl_sync(kFull, cincl - cnt, min(o, 31));
+        int aoff = __shfl_sync(kFull, dincl - deg, min(o, 31));
+        const unsigned ohas = __shfl_sync(kFull, has, min(o, 31));
+        int orb[G], ore[G];
+#pragma unroll
+        for (int i = 0; i < G; ++i) {
+            orb[i] = __shfl_sync(kFull, rb[i], min(o, 31));
+            ore[i] = __shfl_sync(kFull, re[i], min(o, 31));
+        }
+        if (e >= ctot) continue;
+        int k = e - ofirst;
+#pragma unroll
+        for (int i = 0; i < G; ++i) {
+            if (!((ohas >> i) & 1u)) continue;
+            const int d = ore[i] - orb[i];
+            const int c = (d + kEntryArcs - 1) / kEntryArcs;
+            if (k >= 0 && k < c) {
+                const int s0 = orb[i] + k * kEntryArcs;
+                q.ent[slot0 + e] = make_int2(s0, min(kEntryArcs, ore[i] - s0));
+                q.off[slot0 + e] = aoff0 + aoff + k * kEntryArcs;
+            }
+            k -= c;
+            aoff += d;
+        }
+    }
+}
+
 __device__ __forceinline__ void warp_enqueue(bool has, int rb, int re, int lane, Queue q,
                                              unsigned long long* qpack) {
     const int deg = has ? re - rb : 0;
@@ -200,6 +243,12 @@ __device__ __forceinline__ void warp_enqueue(bool has, int rb, int re, int lane,
     unsigned long long base = 0;
     if (lane == 31) base = atomicAdd(qpack, ((unsigned long long)ctot << 32) | (unsigned)dtot);
     base = __shfl_sync(kFull, base, 31);
+    if (__reduce_max_sync(kFull, (unsigned)cnt) > 4u) {  // a long row: write cooperatively
+        const int rbv[1] = {rb}, rev[1] = {re};
+        warp_write_entries<1>(rbv, rev, has ? 1u : 0u, cnt, cincl, ctot, lane, (int)(base >> 32),
+                              (int)(base & 0xffffffffu), dincl, deg, q);
+        return;
+    }
     const int pos = (int)(base >> 32) + cincl - cnt;
     const int aoff = (int)(base & 0xffffffffu) + dincl - deg;
     for (int k = 0; k < cnt; ++k) {
@@ -271,6 +320,11 @@ __device__ __forceinline__ void warp_enqueue_group(unsigned has, const int* rb, 
     unsigned long long base = 0;
     if (lane == 31) base = atomicAdd(qpack, ((unsigned long long)ctot << 32) | (unsigned)dtot);
     base = __shfl_sync(kFull, base, 31);
+    if (__reduce_max_sync(kFull, (unsigned)cnt) > 4u) {  // a long row: write cooperatively
+        warp_write_entries<kPushGroup>(rb, re, has, cnt, cincl, ctot, lane, (int)(base >> 32),
+                                       (int)(base & 0xffffffffu), dincl, deg, q);
+        return;
+    }
     int pos = (int)(base >> 32) + cincl - cnt;
     int aoff = (int)(base & 0xffffffffu) + dincl - deg;
 #pragma unroll
