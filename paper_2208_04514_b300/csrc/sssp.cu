@@ -791,11 +791,13 @@ __global__ void __launch_bounds__(kThreads, DAWN_SSSP_MIN_CTAS) sssp_kernel(Sssp
         int kind;
         if (a.mode == DAWN_MODE_PUSH) kind = kPush;
         else if (a.mode == DAWN_MODE_PULL)
-            kind = (last != kPush && lists && nc_cur <= 4 * mf_cur) ? kListPull : kBitmapPull;
+            kind = (last != kPush && lists && nc_cur <= 4 * mf_cur && 4 * nc_cur <= a.n) ? kListPull : kBitmapPull;
         else if (last == kPush) kind = mf_cur * a.alpha > mu ? kBitmapPull : kPush;
         // after a pull: test only the candidates left while they are few
-        // next to the frontier's arcs; otherwise the push / pull rule
-        else if (lists && nc_cur <= 4 * mf_cur) kind = kListPull;
+        // (next to the frontier's arcs, and at most a quarter of the
+        // vertices: a larger list is cheaper as a bitmap pull with its
+        // tests in shared memory); otherwise the push / pull rule
+        else if (lists && nc_cur <= 4 * mf_cur && 4 * nc_cur <= a.n) kind = kListPull;
         else kind = (nf_cur * a.beta < a.n && nf_cur < prev_nf) ? kPush : kBitmapPull;
         const bool pull = kind != kPush;
         prev_nf = nf_cur;
