@@ -32,8 +32,8 @@ enum DeviceStatus : int {
     DEV_OVERFLOW = 2,  // an int16 distance would exceed 32767
 };
 
-// Frontier work entries cover at most this many arcs, so that one
-// high-degree vertex is spread over many warps.
+// A push level whose queue holds a row longer than this splits its work by
+// arcs (a search over the record offsets), not by record index.
 constexpr int kEntryArcs = 256;
 
 // One counter slot per level, padded to its own 128-byte line.  Levels use
@@ -44,7 +44,8 @@ struct alignas(128) CtrSlot {
     unsigned long long nf;     // vertices first reached at this level
     unsigned long long mf;     // sum of their out-degrees
     unsigned long long nc;     // pull levels: vertices still unreached (candidate lists)
-    unsigned long long pad[12];
+    unsigned long long lr;     // nonzero when a queued row has more than kEntryArcs arcs
+    unsigned long long pad[11];
 };
 
 // Arrival counter of the grid barrier, on its own 128-byte line.

@@ -8,13 +8,13 @@
 // level in one of two directions:
 //
 //  * push (SOVM, Alg. 3): the union of the CSR rows of the frontier
-//    vertices (Eq. 7).  The frontier is a queue of work entries
-//    {first arc, arc count <= kEntryArcs}; a warp takes 32 entries, scans
-//    their arc counts and walks the concatenated arcs 32 at a time, so every
-//    load of col_idx is a coalesced run.  A target is claimed with atomicOr
-//    on the visited bitmap; the lane whose atomicOr flipped the bit writes
-//    dist and appends the target's own row to the next queue (one atomic per
-//    warp).
+//    vertices (Eq. 7).  The frontier is a queue of row records
+//    {first arc, arc count} with their offsets in the level's concatenated
+//    arc list; the arcs are cut into equal ranges, one per warp, which walks
+//    its range 32 arcs at a time, so every load of col_idx is a coalesced
+//    run.  A target is claimed with atomicOr on the visited bitmap; the lane
+//    whose atomicOr flipped the bit writes dist and appends the target's own
+//    row to the next queue (one atomic per warp).
 //  * pull (BOVM, Alg. 1): every vertex not yet reached evaluates the
 //    compressed inner product of Eq. 4 over its in-neighbours and stops at
 //    the first in-neighbour already reached.  The test reads the visited
@@ -141,7 +141,7 @@ __device__ __forceinline__ void red_release_add(unsigned* p, unsigned v) {
 // Returns false (in every thread of the CTA) when the wait ran out or
 // another CTA reported a failure.  `target` lives in thread 0.  With `snap`,
 // thread 0 also reads that counter slot after the acquire and leaves
-// {qpack, nf, mf} in s_snap for the whole CTA: one L2 request per CTA
+// {qpack, nf, mf, nc, lr} in s_snap for the whole CTA: one L2 request per CTA
 // instead of one per warp on a single hot line.
 __device__ bool grid_barrier(Ctl* ctl, unsigned* count, unsigned& target, long long spin_limit,
                              const CtrSlot* snap = nullptr, unsigned long long* s_snap = nullptr) {
@@ -166,6 +166,7 @@ __device__ bool grid_barrier(Ctl* ctl, unsigned* count, unsigned& target, long l
             s_snap[1] = ld_relaxed_u64(&snap->nf);
             s_snap[2] = ld_relaxed_u64(&snap->mf);
             s_snap[3] = ld_relaxed_u64(&snap->nc);
+            s_snap[4] = ld_relaxed_u64(&snap->lr);
         }
         s_ok = ok;
     }
@@ -182,79 +183,28 @@ __device__ __forceinline__ int warp_inclusive_scan(int x, int lane) {
     return x;
 }
 
-// Append the CSR row [rb, re) of each lane with `has` set to the queue, split
-// into entries of at most kEntryArcs arcs.  One 64-bit atomic reserves the
-// warp's entries (high word) and arcs (low word) together, so each entry's
-// offset in the level's concatenated arc list grows with its slot index.
-// The low word cannot carry into the high one: a level's arcs total at most
-// m < 2^31.  Must be reached by the full warp.
-// Write the warp's queue entries when some lane has many (a long row): the
-// warp writes 32 entries per pass over its concatenated entry list, each lane
-// finding the owner of its entry by a search over the inclusive scan of the
-// lanes' entry counts, instead of every lane looping over its own entries.
-// rb / re / has describe each lane's up-to-G rows; slot0 / aoff0 are the
-// warp's first queue slot and first arc offset.  Must be reached by the full warp.
-template <int G>
-__device__ __noinline__ void warp_write_entries(const int* rb, const int* re, unsigned has, int cnt, int cincl,
-                                                int ctot, int lane, int slot0, int aoff0, int dincl, int deg,
-                                                Queue q) {
-    for (int e0 = 0; e0 < ctot; e0 += 32) {
-        const int e = e0 + lane;
-        int o = 0;
-#pragma unroll
-        for (int bb = 16; bb > 0; bb >>= 1)
-            if (__shfl_sync(kFull, cincl, o + bb - 1) <= e) o += bb;
-        const int ofirst = __shfl_sync(kFull, cincl - cnt, min(o, 31));
-        int aoff = __shfl_sync(kFull, dincl - deg, min(o, 31));
-        const unsigned ohas = __shfl_sync(kFull, has, min(o, 31));
-        int orb[G], ore[G];
-#pragma unroll
-        for (int i = 0; i < G; ++i) {
-            orb[i] = __shfl_sync(kFull, rb[i], min(o, 31));
-            ore[i] = __shfl_sync(kFull, re[i], min(o, 31));
-        }
-        if (e >= ctot) continue;
-        int k = e - ofirst;
-#pragma unroll
-        for (int i = 0; i < G; ++i) {
-            if (!((ohas >> i) & 1u)) continue;
-            const int d = ore[i] - orb[i];
-            const int c = (d + kEntryArcs - 1) / kEntryArcs;
-            if (k >= 0 && k < c) {
-                const int s0 = orb[i] + k * kEntryArcs;
-                q.ent[slot0 + e] = make_int2(s0, min(kEntryArcs, ore[i] - s0));
-                q.off[slot0 + e] = aoff0 + aoff + k * kEntryArcs;
-            }
-            k -= c;
-            aoff += d;
-        }
-    }
-}
-
-__device__ __forceinline__ void warp_enqueue(bool has, int rb, int re, int lane, Queue q,
-                                             unsigned long long* qpack) {
+// Append the CSR row [rb, re) of each lane with `has` set to the queue as one
+// record {first arc, arc count} (empty rows are left out), with the record's
+// offset in the level's concatenated arc list.  One 64-bit atomic reserves
+// the warp's records (high word) and arcs (low word) together, so offsets
+// grow with the slot index.  The low word cannot carry into the high one: a
+// level's arcs total at most m < 2^31.  A row of more than kEntryArcs arcs
+// sets the level's long-row flag, which keeps the next push from splitting
+// its work by record index.  Must be reached by the full warp.
+__device__ __forceinline__ void warp_enqueue(bool has, int rb, int re, int lane, Queue q, CtrSlot* out) {
     const int deg = has ? re - rb : 0;
-    const int cnt = (deg + kEntryArcs - 1) / kEntryArcs;
-    const int cincl = warp_inclusive_scan(cnt, lane);
-    const int ctot = __shfl_sync(kFull, cincl, 31);
-    if (ctot == 0) return;
+    const unsigned rows = __ballot_sync(kFull, deg > 0);
+    if (!rows) return;
     const int dincl = warp_inclusive_scan(deg, lane);
     const int dtot = __shfl_sync(kFull, dincl, 31);
     unsigned long long base = 0;
-    if (lane == 31) base = atomicAdd(qpack, ((unsigned long long)ctot << 32) | (unsigned)dtot);
-    base = __shfl_sync(kFull, base, 31);
-    if (__reduce_max_sync(kFull, (unsigned)cnt) > 4u) {  // a long row: write cooperatively
-        const int rbv[1] = {rb}, rev[1] = {re};
-        warp_write_entries<1>(rbv, rev, has ? 1u : 0u, cnt, cincl, ctot, lane, (int)(base >> 32),
-                              (int)(base & 0xffffffffu), dincl, deg, q);
-        return;
-    }
-    const int pos = (int)(base >> 32) + cincl - cnt;
-    const int aoff = (int)(base & 0xffffffffu) + dincl - deg;
-    for (int k = 0; k < cnt; ++k) {
-        const int s = rb + k * kEntryArcs;
-        q.ent[pos + k] = make_int2(s, min(kEntryArcs, re - s));
-        q.off[pos + k] = aoff + k * kEntryArcs;
+    if (lane == 0) base = atomicAdd(&out->qpack, ((unsigned long long)__popc(rows) << 32) | (unsigned)dtot);
+    base = __shfl_sync(kFull, base, 0);
+    if (__any_sync(kFull, deg > kEntryArcs) && lane == 0) atomicOr(&out->lr, 1ull);
+    if (deg > 0) {
+        const int pos = (int)(base >> 32) + __popc(rows & ((1u << lane) - 1u));
+        q.ent[pos] = make_int2(rb, deg);
+        q.off[pos] = (int)(base & 0xffffffffu) + dincl - deg;
     }
 }
 
@@ -298,18 +248,19 @@ __device__ __forceinline__ void load_batch(const Queue& q, int qn, int b, int la
 }
 
 // Append up to kPushGroup claimed rows per lane with one reservation per warp
-// (same layout rules as warp_enqueue; a lane's rows keep their order).
+// (same record layout as warp_enqueue; a lane's rows keep their order).
 constexpr int kPushGroup = 4;
 
 __device__ __forceinline__ void warp_enqueue_group(unsigned has, const int* rb, const int* re, int lane, Queue q,
-                                                   unsigned long long* qpack) {
-    int cnt = 0, deg = 0;
+                                                   CtrSlot* out) {
+    int cnt = 0, deg = 0, dmax = 0;
 #pragma unroll
     for (int i = 0; i < kPushGroup; ++i) {
         if ((has >> i) & 1u) {
             const int d = re[i] - rb[i];
+            cnt += d > 0;
             deg += d;
-            cnt += (d + kEntryArcs - 1) / kEntryArcs;
+            dmax = max(dmax, d);
         }
     }
     const int cincl = warp_inclusive_scan(cnt, lane);
@@ -318,49 +269,46 @@ __device__ __forceinline__ void warp_enqueue_group(unsigned has, const int* rb, 
     const int dincl = warp_inclusive_scan(deg, lane);
     const int dtot = __shfl_sync(kFull, dincl, 31);
     unsigned long long base = 0;
-    if (lane == 31) base = atomicAdd(qpack, ((unsigned long long)ctot << 32) | (unsigned)dtot);
+    if (lane == 31) base = atomicAdd(&out->qpack, ((unsigned long long)ctot << 32) | (unsigned)dtot);
     base = __shfl_sync(kFull, base, 31);
-    if (__reduce_max_sync(kFull, (unsigned)cnt) > 4u) {  // a long row: write cooperatively
-        warp_write_entries<kPushGroup>(rb, re, has, cnt, cincl, ctot, lane, (int)(base >> 32),
-                                       (int)(base & 0xffffffffu), dincl, deg, q);
-        return;
-    }
+    if (__any_sync(kFull, dmax > kEntryArcs) && lane == 31) atomicOr(&out->lr, 1ull);
     int pos = (int)(base >> 32) + cincl - cnt;
     int aoff = (int)(base & 0xffffffffu) + dincl - deg;
 #pragma unroll
     for (int i = 0; i < kPushGroup; ++i) {
         if (!((has >> i) & 1u)) continue;
-        for (int s = rb[i]; s < re[i]; s += kEntryArcs) {
-            q.ent[pos] = make_int2(s, min(kEntryArcs, re[i] - s));
-            q.off[pos] = aoff + (s - rb[i]);
-            ++pos;
-        }
-        aoff += re[i] - rb[i];
+        const int d = re[i] - rb[i];
+        if (d <= 0) continue;
+        q.ent[pos] = make_int2(rb[i], d);
+        q.off[pos] = aoff;
+        ++pos;
+        aoff += d;
     }
 }
 
 // SOVM push: expand the frontier's rows (Eq. 7: the new vector is the union
 // of the CSR rows of the frontier).  The level's E arcs are cut into equal
 // ranges, a multiple of 32 long, one per warp of the grid; a warp finds the
-// entry holding its first arc with a 32-ary search over the sorted entry
+// record holding its first arc with a 32-ary search over the sorted record
 // offsets, then walks its range in groups of kPushGroup windows of 32
 // consecutive arcs.  Within a group the col_idx loads, the bitmap tests, the
 // atomicOr claims and the row_ptr loads of all windows are issued back to back,
 // so a warp waits for one chain of memory round trips per group, not per
 // window.
 __device__ void push_level(const SsspArgs& a, int step, uint32_t* vis, Queue qin, unsigned long long pack,
-                           Queue qout, CtrSlot* out, long long& nf, long long& mf) {
+                           bool qlong, Queue qout, CtrSlot* out, long long& nf, long long& mf) {
     const int lane = threadIdx.x & 31;
     const int qn = (int)(pack >> 32);
     const long long E = (long long)(pack & 0xffffffffull);
     const long long nw = (long long)gridDim.x * kWarps;
     const long long gw = (long long)blockIdx.x * kWarps + (threadIdx.x >> 5);
     if (E == 0) return;
-    // Light levels (entries of at most 8 arcs on average, e.g. a lattice
-    // frontier): each warp takes whole entries by index, so its first entry
-    // is known without a search, and claims without a read-only pre-test.
-    // Heavy levels (hub rows): equal arc ranges found by a 32-ary search.
-    const bool light = E <= 8LL * qn;
+    // Light levels (rows of at most 8 arcs on average and none longer than
+    // kEntryArcs, e.g. a lattice frontier): each warp takes whole records by
+    // index, so its first record is known without a search, and claims
+    // without a read-only pre-test.  Heavy levels (hub rows): equal arc
+    // ranges found by a 32-ary search.
+    const bool light = E <= 8LL * qn && !qlong;
     long long a0, a1;
     int bstart;
     int2 e;
@@ -461,7 +409,7 @@ __device__ void push_level(const SsspArgs& a, int step, uint32_t* vis, Queue qin
                 mf += re[q] - rb[q];
             }
         }
-        warp_enqueue_group(claimed, rb, re, lane, qout, &out->qpack);
+        warp_enqueue_group(claimed, rb, re, lane, qout, out);
     }
 }
 
@@ -609,7 +557,7 @@ __device__ void pull_level(const SsspArgs& a, int step, const uint32_t* vcur, ui
 // in the visited bitmap in place.  Found rows go straight to the push queue
 // (a push level may follow); candidates still unreached move to `keep`.
 __device__ __noinline__ void list_pull_level(const SsspArgs& a, int step, uint32_t* vis, const int32_t* cand, int ncand,
-                                int32_t* keep, int* s_cn, Queue qout, unsigned long long* qpack, long long& nf,
+                                int32_t* keep, int* s_cn, Queue qout, CtrSlot* out, long long& nf,
                                 long long& mf) {
     const int lane = threadIdx.x & 31;
     const bool symmetric = a.in_ptr == a.row_ptr;
@@ -675,14 +623,14 @@ __device__ __noinline__ void list_pull_level(const SsspArgs& a, int step, uint32
             nf += 1;
             mf += re - rb;
         }
-        warp_enqueue(found, rb, re, lane, qout, qpack);
+        warp_enqueue(found, rb, re, lane, qout, out);
         warp_keep(has && !found, v, lane, keep, s_cn);
     }
 }
 
 // After a pull level: queue the vertices it reached (bits of vnow not in vold).
 __device__ void bitmap_to_queue(const SsspArgs& a, const uint32_t* vnow, const uint32_t* vold,
-                                Queue qout, unsigned long long* qpack) {
+                                Queue qout, CtrSlot* out) {
     const int lane = threadIdx.x & 31;
     const int gw = blockIdx.x * kWarps + (threadIdx.x >> 5);
     const int nw = gridDim.x * kWarps;
@@ -701,14 +649,14 @@ __device__ void bitmap_to_queue(const SsspArgs& a, const uint32_t* vnow, const u
                 rb = __ldg(a.row_ptr + v);
                 re = __ldg(a.row_ptr + v + 1);
             }
-            warp_enqueue(has, rb, re, lane, qout, qpack);
+            warp_enqueue(has, rb, re, lane, qout, out);
         }
     }
 }
 
 __global__ void __launch_bounds__(kThreads, DAWN_SSSP_MIN_CTAS) sssp_kernel(SsspArgs a) {
     Ctl* ctl = a.ctl;
-    __shared__ unsigned long long s_snap[4];  // {qpack, nf, mf, nc} of the level just finished
+    __shared__ unsigned long long s_snap[5];  // {qpack, nf, mf, nc, lr} of the level just finished
     __shared__ int s_cn, s_cin;               // this CTA's candidates: being kept / to test
     __shared__ int s_status;
     if (threadIdx.x == 0) s_status = ld_relaxed_s32(&ctl->status);
@@ -743,7 +691,7 @@ __global__ void __launch_bounds__(kThreads, DAWN_SSSP_MIN_CTAS) sssp_kernel(Sssp
             reinterpret_cast<unsigned long long*>(ctl->ctr)[i] = 0;
         __syncwarp();
         const int rb = __ldg(a.row_ptr + src), re = __ldg(a.row_ptr + src + 1);
-        warp_enqueue(lane == 0, rb, re, lane, Queue{a.q0, a.q0off}, &ctl->ctr[0].qpack);
+        warp_enqueue(lane == 0, rb, re, lane, Queue{a.q0, a.q0off}, &ctl->ctr[0]);
         if (lane == 0) {
             ctl->ctr[0].nf = 1;
             ctl->ctr[0].mf = (unsigned long long)(re - rb);
@@ -781,6 +729,7 @@ __global__ void __launch_bounds__(kThreads, DAWN_SSSP_MIN_CTAS) sssp_kernel(Sssp
         const Queue qcur = (step & 1) ? Queue{a.q1, a.q1off} : Queue{a.q0, a.q0off};
         const Queue qnext = (step & 1) ? Queue{a.q0, a.q0off} : Queue{a.q1, a.q1off};
         unsigned long long qpack = s_snap[0];
+        bool qlong = s_snap[4] != 0;  // the queue holds a row of more than kEntryArcs arcs
         const long long nf_cur = (long long)s_snap[1];
         const long long mf_cur = (long long)s_snap[2];
         if (nf_cur == 0 || step >= a.n) break;
@@ -806,9 +755,10 @@ __global__ void __launch_bounds__(kThreads, DAWN_SSSP_MIN_CTAS) sssp_kernel(Sssp
 
         if (kind == kPush && last == kBitmapPull) {
             // the frontier exists only as a bitmap difference: turn it into a queue
-            bitmap_to_queue(a, vcur, vnext, qcur, &cur->qpack);
+            bitmap_to_queue(a, vcur, vnext, qcur, cur);
             if (!grid_barrier(ctl, bar, bar_target, a.spin_limit, cur, s_snap)) return;
             qpack = s_snap[0];
+            qlong = s_snap[4] != 0;
             if (tracer) trace_rec(a, tslot, 4, step, (long long)(qpack >> 32));
         }
         CtrSlot* out = &ctl->ctr[(step + 1) % 3];
@@ -819,11 +769,11 @@ __global__ void __launch_bounds__(kThreads, DAWN_SSSP_MIN_CTAS) sssp_kernel(Sssp
             else pull_level<false>(a, step + 1, vcur, vnext, nf, mf, keep, &s_cn);
             ++pulls;
         } else if (kind == kListPull) {
-            list_pull_level(a, step + 1, vcur, cl[cpar], s_cin, cl[cpar ^ 1], &s_cn, qnext, &out->qpack, nf, mf);
+            list_pull_level(a, step + 1, vcur, cl[cpar], s_cin, cl[cpar ^ 1], &s_cn, qnext, out, nf, mf);
             cpar ^= 1;
             ++pulls;
         } else {
-            push_level(a, step + 1, vcur, qcur, qpack, qnext, out, nf, mf);
+            push_level(a, step + 1, vcur, qcur, qpack, qlong, qnext, out, nf, mf);
             ++pushes;
         }
         flush_counts(nf, mf, out, pull ? &s_cn : nullptr);
