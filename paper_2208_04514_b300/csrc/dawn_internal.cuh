@@ -5,6 +5,7 @@
 
 #include <cstdint>
 #include <cstdio>
+#include <vector>
 
 #include "dawn.h"
 
@@ -38,7 +39,10 @@ constexpr int kEntryArcs = 256;
 
 // One counter slot per level, padded to its own 128-byte line.  Levels use
 // slots (step % 3): written during step s, read after the barrier that ends
-// step s, reset during step s + 1 (see the level loop in sssp.cu).
+// step s, reset during step s + 1 (see the level loop in sssp.cu).  Launches
+// alternate between two sets of three slots (the barrier counter's parity);
+// each launch zeroes the other set for the next one, so a launch finds its
+// own slots zero on entry.
 struct alignas(128) CtrSlot {
     unsigned long long qpack;  // queue size: entries (high 32 bits) | arcs (low 32 bits)
     unsigned long long nf;     // vertices first reached at this level
@@ -61,7 +65,7 @@ struct alignas(128) Ctl {
     BarCounter bar[2];
     int status;                // sticky DeviceStatus
     int pad2[31];
-    CtrSlot ctr[3];
+    CtrSlot ctr[2][3];         // [launch parity][step % 3]
 };
 
 // Default barrier spin budget in SM clock cycles (~2 s at 2 GHz).
@@ -78,6 +82,7 @@ struct dawn_graph {
     uint32_t flags = 0;
     int32_t nwords = 0;               // ceil(n / 32), bitmap words
     int32_t* row_ptr = nullptr;       // CSR, device
+    std::vector<int32_t> row_ptr_host;  // copy of row_ptr: the source row bounds travel as launch arguments
     int32_t* col_idx = nullptr;
     int32_t* in_ptr = nullptr;        // CSC (== CSR when symmetric), device
     int32_t* in_idx = nullptr;

@@ -410,6 +410,9 @@ int upload(const int32_t* row_ptr, const int32_t* col_idx, int32_t n, int64_t m,
     if (e != cudaSuccess) { release(g); return cuda_fail(e, "graph setup", __FILE__, __LINE__); }
     g->in_sorted = *g->status_host == 0;
     *g->status_host = 0;
+    g->row_ptr_host.resize((size_t)n + 1);
+    e = cudaMemcpy(g->row_ptr_host.data(), g->row_ptr, sizeof(int32_t) * ((size_t)n + 1), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) { release(g); return cuda_fail(e, "graph setup (row_ptr copy)", __FILE__, __LINE__); }
     int rc = sssp_occupancy(g);
     if (rc != DAWN_OK) { release(g); return rc; }
     *out = g;

@@ -74,6 +74,7 @@ struct SsspArgs {
     int32_t n;
     int32_t nwords;
     int32_t src;
+    int32_t srb, sre;        // the source row [srb, sre) of col_idx; srb < 0: read from row_ptr
     int32_t mode;
     int32_t alpha;
     int32_t beta;
@@ -654,14 +655,57 @@ __device__ void bitmap_to_queue(const SsspArgs& a, const uint32_t* vnow, const u
     }
 }
 
+// Init and level 1 together (see the kernel): clear this CTA's vertex range,
+// then claim the source's out-neighbours inside it and queue their rows.
+// Must be reached by the whole CTA.
+__device__ __noinline__ void fused_init_level1(const SsspArgs& a, int srb, int sdeg, CtrSlot* out) {
+    const int lane = threadIdx.x & 31;
+    const int32_t src = a.src;
+    const bool d16 = (((uintptr_t)a.dist) & 15u) == 0;
+    // ranges of a multiple of 128 vertices: whole int4 groups and bitmap words
+    const long long per = (((long long)a.n + gridDim.x - 1) / gridDim.x + 127) & ~127LL;
+    const long long v0 = (long long)blockIdx.x * per;
+    const long long v1 = min((long long)a.n, v0 + per);
+    // this thread's arc of the source row, loaded while the range is cleared
+    const int c = threadIdx.x < sdeg ? __ldg(a.col_idx + srb + threadIdx.x) : -1;
+    if (v0 < v1) {
+        if (d16) {
+            int4* d4 = reinterpret_cast<int4*>(a.dist);
+            const long long e4 = v1 >> 2;
+            for (long long i = (v0 >> 2) + threadIdx.x; i < e4; i += kThreads) d4[i] = make_int4(-1, -1, -1, -1);
+            for (long long i = (e4 << 2) + threadIdx.x; i < v1; i += kThreads) a.dist[i] = -1;
+        } else {
+            for (long long i = v0 + threadIdx.x; i < v1; i += kThreads) a.dist[i] = -1;
+        }
+        const long long w1 = min((long long)a.nwords, (v1 + 31) >> 5);
+        for (long long w = (v0 >> 5) + threadIdx.x; w < w1; w += kThreads)
+            a.vis0[w] = (w == (src >> 5)) ? (1u << (src & 31)) : 0u;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && src >= v0 && src < v1) a.dist[src] = 0;
+    bool claimed = false;
+    int rb = 0, re = 0;
+    if (c >= v0 && c < v1) {
+        rb = __ldg(a.row_ptr + c);
+        re = __ldg(a.row_ptr + c + 1);
+        const uint32_t bit = 1u << (c & 31);
+        claimed = !(atomicOr(&a.vis0[c >> 5], bit) & bit);
+        if (claimed) a.dist[c] = 1;
+    }
+    warp_enqueue(claimed, rb, re, lane, Queue{a.q1, a.q1off}, out);
+    flush_counts(claimed ? 1 : 0, claimed ? re - rb : 0, out);
+}
+
 __global__ void __launch_bounds__(kThreads, DAWN_SSSP_MIN_CTAS) sssp_kernel(SsspArgs a) {
     Ctl* ctl = a.ctl;
     __shared__ unsigned long long s_snap[5];  // {qpack, nf, mf, nc, lr} of the level just finished
     __shared__ int s_cn, s_cin;               // this CTA's candidates: being kept / to test
     __shared__ int s_status;
+    // an earlier call that failed leaves the barrier state inconsistent: this
+    // launch then stops before its first barrier (its outputs are undefined,
+    // and the host clears the control block when it reports the failure).
+    // The status load overlaps the clearing below.
     if (threadIdx.x == 0) s_status = ld_relaxed_s32(&ctl->status);
-    __syncthreads();
-    if (s_status != DEV_OK) return;  // an earlier call failed: stay idle
     const int lane = threadIdx.x & 31;
     const bool tracer = blockIdx.x == 0 && threadIdx.x == 0;
     int tslot = 0;
@@ -671,50 +715,73 @@ __global__ void __launch_bounds__(kThreads, DAWN_SSSP_MIN_CTAS) sssp_kernel(Sssp
     const long long gtid = (long long)blockIdx.x * kThreads + threadIdx.x;
     const long long gthreads = (long long)gridDim.x * kThreads;
 
-    // ---- init: dist = -1 except dist[src] = 0; visited = {src}; queue = {src}
+    // this launch's counter slots (zero on entry); zero the next launch's
+    CtrSlot* ctr = ctl->ctr[a.bar_parity];
+    if (blockIdx.x == gridDim.x - 1 && threadIdx.x < 3 * (int)(sizeof(CtrSlot) / 8))
+        reinterpret_cast<unsigned long long*>(ctl->ctr[a.bar_parity ^ 1])[threadIdx.x] = 0;
+
+    // ---- init: dist = -1 except dist[src] = 0; visited = {src}
     const int32_t src = a.src;
-    if ((((uintptr_t)a.dist) & 15u) == 0) {
-        int4* d4 = reinterpret_cast<int4*>(a.dist);
-        const long long n4 = a.n >> 2;
-        for (long long i = gtid; i < n4; i += gthreads) d4[i] = make_int4(-1, -1, -1, -1);
-        for (long long i = (n4 << 2) + gtid; i < a.n; i += gthreads) a.dist[i] = -1;
+    const int srb = a.srb >= 0 ? a.srb : __ldg(a.row_ptr + src);
+    const int sre = a.srb >= 0 ? a.sre : __ldg(a.row_ptr + src + 1);
+    const int sdeg = sre - srb;
+    // Level 1 (the push of the source row) joins the init when the rule would
+    // push and the row fits one pass of the CTA: each CTA clears a contiguous
+    // vertex range of its own and then claims the source's out-neighbours in
+    // that range, so only __syncthreads orders the clearing before the claims
+    // and the first grid barrier already ends level 1.
+    const bool fused = a.mode != DAWN_MODE_PULL && sdeg <= kThreads &&
+                       (a.mode == DAWN_MODE_PUSH || (long long)sdeg * a.alpha <= a.m - sdeg);
+    const bool d16 = (((uintptr_t)a.dist) & 15u) == 0;
+    if (fused) {
+        fused_init_level1(a, srb, sdeg, &ctr[1]);  // ends with __syncthreads
+        if (s_status != DEV_OK) return;
+        if (!grid_barrier(ctl, bar, bar_target, a.spin_limit, &ctr[1], s_snap)) return;
+        if (gtid == 0) ctl->bar[a.bar_parity ^ 1].count = 0;  // the next launch's counter
+        if (tracer) {
+            trace_rec(a, tslot, 1, 0, 1);
+            trace_rec(a, tslot, 2, 1, (long long)s_snap[1]);
+        }
     } else {
-        for (long long i = gtid; i < a.n; i += gthreads) a.dist[i] = -1;
-    }
-    for (long long w = gtid; w < a.nwords; w += gthreads)
-        a.vis0[w] = (w == (src >> 5)) ? (1u << (src & 31)) : 0u;
-    if (blockIdx.x == 0 && threadIdx.x < 32) {
-        if (lane < 3 * (int)(sizeof(CtrSlot) / 8)) {
-            reinterpret_cast<unsigned long long*>(ctl->ctr)[lane] = 0;
+        if (d16) {
+            int4* d4 = reinterpret_cast<int4*>(a.dist);
+            const long long n4 = a.n >> 2;
+            for (long long i = gtid; i < n4; i += gthreads) d4[i] = make_int4(-1, -1, -1, -1);
+            for (long long i = (n4 << 2) + gtid; i < a.n; i += gthreads) a.dist[i] = -1;
+        } else {
+            for (long long i = gtid; i < a.n; i += gthreads) a.dist[i] = -1;
         }
-        for (int i = lane + 32; i < 3 * (int)(sizeof(CtrSlot) / 8); i += 32)
-            reinterpret_cast<unsigned long long*>(ctl->ctr)[i] = 0;
-        __syncwarp();
-        const int rb = __ldg(a.row_ptr + src), re = __ldg(a.row_ptr + src + 1);
-        warp_enqueue(lane == 0, rb, re, lane, Queue{a.q0, a.q0off}, &ctl->ctr[0]);
-        if (lane == 0) {
-            ctl->ctr[0].nf = 1;
-            ctl->ctr[0].mf = (unsigned long long)(re - rb);
+        for (long long w = gtid; w < a.nwords; w += gthreads)
+            a.vis0[w] = (w == (src >> 5)) ? (1u << (src & 31)) : 0u;
+        if (blockIdx.x == 0 && threadIdx.x < 32) {  // level 0: the source, queue = {src}
+            warp_enqueue(lane == 0, srb, sre, lane, Queue{a.q0, a.q0off}, &ctr[0]);
+            if (lane == 0) {
+                ctr[0].nf = 1;
+                ctr[0].mf = (unsigned long long)sdeg;
+            }
         }
+        __syncthreads();
+        if (s_status != DEV_OK) return;
+        // dist[src] = 0 after the fill; the barrier orders it after every -1 store
+        if (!grid_barrier(ctl, bar, bar_target, a.spin_limit, &ctr[0], s_snap)) return;
+        if (gtid == 0) {
+            a.dist[src] = 0;
+            ctl->bar[a.bar_parity ^ 1].count = 0;  // the next launch's counter
+        }
+        if (tracer) trace_rec(a, tslot, 1, 0, 1);
     }
-    // dist[src] = 0 after the fill; the barrier orders it after every -1 store
-    if (!grid_barrier(ctl, bar, bar_target, a.spin_limit, &ctl->ctr[0], s_snap)) return;
-    if (gtid == 0) {
-        a.dist[src] = 0;
-        ctl->bar[a.bar_parity ^ 1].count = 0;  // the next launch's counter
-    }
-    if (tracer) trace_rec(a, tslot, 1, 0, 1);
 
     uint32_t* vcur = a.vis0;
     uint32_t* vnext = a.vis1;
-    long long mu = a.m;         // arcs out of vertices not yet reached
-    long long prev_nf = 0;
-    long long reached = 0, edges = 0;
-    int pushes = 0, pulls = 0;
     // level kinds: push (SOVM), pull over the bitmap, pull over the candidate lists
     enum { kPush = 0, kBitmapPull = 1, kListPull = 2 };
+    // the loop starts after level 0 (the source), or after level 1 when fused
+    long long mu = a.m - (fused ? sdeg : 0);  // arcs out of vertices not yet reached
+    long long prev_nf = fused ? 1 : 0;
+    long long reached = fused ? 1 : 0, edges = fused ? sdeg : 0;
+    int pushes = fused ? 1 : 0, pulls = 0;
     int last = kPush;
-    int step = 0;
+    int step = fused ? 1 : 0;
     // this CTA's region of the candidate lists: the bitmap words its warps scan
     const int nwarps = gridDim.x * kWarps;
     const long long region = (long long)kWarps * ((a.nwords + nwarps - 1) / nwarps) * 32;
@@ -724,7 +791,7 @@ __global__ void __launch_bounds__(kThreads, DAWN_SSSP_MIN_CTAS) sssp_kernel(Sssp
     if (threadIdx.x == 0) s_cn = s_cin = 0;
     __syncthreads();
     while (true) {
-        CtrSlot* cur = &ctl->ctr[step % 3];
+        CtrSlot* cur = &ctr[step % 3];
         // the frontier found at step s lives in queue (s & 1)
         const Queue qcur = (step & 1) ? Queue{a.q1, a.q1off} : Queue{a.q0, a.q0off};
         const Queue qnext = (step & 1) ? Queue{a.q0, a.q0off} : Queue{a.q1, a.q1off};
@@ -751,7 +818,7 @@ __global__ void __launch_bounds__(kThreads, DAWN_SSSP_MIN_CTAS) sssp_kernel(Sssp
         const bool pull = kind != kPush;
         prev_nf = nf_cur;
         if (blockIdx.x == 0 && threadIdx.x < (int)(sizeof(CtrSlot) / 8))
-            reinterpret_cast<unsigned long long*>(&ctl->ctr[(step + 2) % 3])[threadIdx.x] = 0;
+            reinterpret_cast<unsigned long long*>(&ctr[(step + 2) % 3])[threadIdx.x] = 0;
 
         if (kind == kPush && last == kBitmapPull) {
             // the frontier exists only as a bitmap difference: turn it into a queue
@@ -761,7 +828,7 @@ __global__ void __launch_bounds__(kThreads, DAWN_SSSP_MIN_CTAS) sssp_kernel(Sssp
             qlong = s_snap[4] != 0;
             if (tracer) trace_rec(a, tslot, 4, step, (long long)(qpack >> 32));
         }
-        CtrSlot* out = &ctl->ctr[(step + 1) % 3];
+        CtrSlot* out = &ctr[(step + 1) % 3];
         long long nf = 0, mf = 0;
         if (kind == kBitmapPull) {
             int32_t* keep = lists ? cl[cpar] : nullptr;
@@ -824,6 +891,7 @@ int sssp_occupancy(dawn_graph* g) {
 
 int sssp_launch(dawn_graph* g, int32_t src, int32_t* dist_dev, const dawn_sssp_opts* opts,
                 dawn_sssp_stats* stats_dev, cudaStream_t st) {
+    if (src < 0 || src >= g->n) return fail(DAWN_E_INVALID, "source %d outside [0, %d)", src, g->n);
     const int engine = opts ? opts->engine : DAWN_ENGINE_AUTO;
     if (engine < DAWN_ENGINE_AUTO || engine > DAWN_ENGINE_CLUSTER) return fail(DAWN_E_INVALID, "unknown engine %d", engine);
     if (opts && (opts->mode < DAWN_MODE_AUTO || opts->mode > DAWN_MODE_PULL))
@@ -854,6 +922,8 @@ int sssp_launch(dawn_graph* g, int32_t src, int32_t* dist_dev, const dawn_sssp_o
     a.n = g->n;
     a.nwords = g->nwords;
     a.src = src;
+    a.srb = g->row_ptr_host[src];
+    a.sre = g->row_ptr_host[src + 1];
     a.mode = opts ? opts->mode : DAWN_MODE_AUTO;
     a.alpha = (opts && opts->alpha > 0) ? opts->alpha : (g->tuning.alpha > 0 ? g->tuning.alpha : 15);
     a.beta = (opts && opts->beta > 0) ? opts->beta : (g->tuning.beta > 0 ? g->tuning.beta : 18);
@@ -1008,6 +1078,7 @@ int sssp_noalloc(const int32_t* row_ptr, const int32_t* col_idx, int32_t n, int6
     a.n = n;
     a.nwords = (int32_t)(((int64_t)n + 31) / 32);
     a.src = src;
+    a.srb = a.sre = -1;  // the caller's CSR: read on the device
     a.mode = DAWN_MODE_PUSH;
     a.bar_parity = 0;  // the whole control block was just zeroed
     a.smem_words = 0;
