@@ -89,6 +89,7 @@ struct dawn_graph {
     uint32_t* excl = nullptr;         // bit v set: v has no in-arc (or v >= n)
     int32_t in_sorted = 0;            // 1: every in-adjacency row is in ascending order
     int32_t* pull_idx = nullptr;      // in-adjacency rows ordered by out-degree, largest first (pull levels)
+    int2* first2 = nullptr;           // the first two entries of each pull_idx row (-1 where the row is shorter)
     // single-source work buffers
     uint32_t* vis[2] = {nullptr, nullptr};
     int2* queue[2] = {nullptr, nullptr};        // frontier entries {first arc, arc count}

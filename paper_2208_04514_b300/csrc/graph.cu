@@ -202,6 +202,17 @@ __global__ void pull_order_cta_kernel(const int32_t* __restrict__ in_ptr, const 
     }
 }
 
+// first2[v] = the first two in-neighbours of v in pull order (-1 past the row's
+// end): a pull tests them from one coalesced load per warp, before any
+// scattered read of the row itself.
+__global__ void first2_kernel(const int32_t* __restrict__ ptr, const int32_t* __restrict__ idx, int32_t n,
+                              int2* __restrict__ first2) {
+    for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (long long)gridDim.x * blockDim.x) {
+        const int b = ptr[v], e = ptr[v + 1];
+        first2[v] = make_int2(e > b ? idx[b] : -1, e > b + 1 ? idx[b + 1] : -1);
+    }
+}
+
 // flag = 1 when some in-adjacency row is not in ascending order (one warp per row).
 __global__ void unsorted_rows_kernel(const int32_t* __restrict__ ptr, const int32_t* __restrict__ idx, int32_t n,
                                      int* flag) {
@@ -258,6 +269,7 @@ void release(dawn_graph* g) {
     f(g->queue_off[1]);
     f(g->dist_tmp);
     f(g->pull_idx);
+    f(g->first2);
     f(g->cand[0]);
     f(g->cand[1]);
     f(g->cl_ovf);
@@ -369,7 +381,9 @@ int upload(const int32_t* row_ptr, const int32_t* col_idx, int32_t n, int64_t m,
         (e = alloc((void**)&g->queue_off[0], sizeof(int32_t) * (size_t)g->queue_cap)) != cudaSuccess ||
         (e = alloc((void**)&g->queue_off[1], sizeof(int32_t) * (size_t)g->queue_cap)) != cudaSuccess ||
         (e = alloc((void**)&g->dist_tmp, sizeof(int32_t) * (size_t)n)) != cudaSuccess ||
-        (e = alloc((void**)&g->pull_idx, sizeof(int32_t) * (size_t)(m > 0 ? m : 1))) != cudaSuccess ||
+        // rounded up to whole 16-byte groups: the pull levels read it with aligned int4 loads
+        (e = alloc((void**)&g->pull_idx, sizeof(int32_t) * (size_t)((m + 3) / 4 * 4 + 4))) != cudaSuccess ||
+        (e = alloc((void**)&g->first2, sizeof(int2) * (size_t)n)) != cudaSuccess ||
         (e = alloc((void**)&g->cand[0], sizeof(int32_t) * (size_t)g->cand_cap)) != cudaSuccess ||
         (e = alloc((void**)&g->cand[1], sizeof(int32_t) * (size_t)g->cand_cap)) != cudaSuccess ||
         (e = alloc((void**)&g->ctl, sizeof(Ctl))) != cudaSuccess ||
@@ -398,6 +412,10 @@ int upload(const int32_t* row_ptr, const int32_t* col_idx, int32_t n, int64_t m,
             pull_order_cta_kernel<<<g->sms * 2, 1024, 0, st>>>(g->in_ptr, g->in_idx, g->row_ptr, n, g->pull_idx);
             e = cudaGetLastError();
         }
+    }
+    if (e == cudaSuccess) {
+        first2_kernel<<<grid_for(n, g->sms), kThreads, 0, st>>>(g->in_ptr, g->pull_idx, n, g->first2);
+        e = cudaGetLastError();
     }
     if (e == cudaSuccess && m > 0) {
         unsorted_rows_kernel<<<grid_for((int64_t)n * 32, g->sms), kThreads, 0, st>>>(g->in_ptr, g->in_idx, n,

@@ -83,6 +83,7 @@ struct SsspArgs {
     int32_t bar_parity;      // which of the two barrier counters this launch uses
     int32_t smem_words;      // > 0: pull levels copy the bitmap (this many words) to shared memory
     const int32_t* __restrict__ pull_idx;  // in-adjacency rows ordered by out-degree, largest first
+    const int2* __restrict__ first2;       // the first two entries of each pull_idx row (-1 past its end)
     int32_t* cand0;          // per-CTA lists of unreached pull candidates (null: none)
     int32_t* cand1;
     long long cand_cap;      // entries per list
@@ -469,36 +470,68 @@ __device__ void pull_level(const SsspArgs& a, int step, const uint32_t* vcur, ui
                 cand[u] = !((skip >> lane) & 1u);
             }
         }
+        // words without a candidate (all reached or without in-arcs) only
+        // carry their bitmap word over
+        bool anyc = false;
+#pragma unroll
+        for (int u = 0; u < U; ++u) anyc |= cand[u];
+        if (!__any_sync(kFull, anyc)) {
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+                if (lane == 0 && w0 + u * nw < a.nwords) vnext[w0 + u * nw] = cur[u];
+            continue;
+        }
+        // the first two in-neighbours (the likeliest to be reached: rows are in
+        // descending degree order) come from one coalesced load per word
+        int2 f2[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
+            f2[u] = make_int2(-1, -1);
             if (cand[u]) {
                 const int v = ((w0 + u * nw) << 5) + lane;
                 ib[u] = __ldg(a.in_ptr + v);
                 ie[u] = __ldg(a.in_ptr + v + 1);
-                j[u] = ib[u];
+                f2[u] = __ldg(a.first2 + v);
             }
         }
-        // own tests, 4 in-neighbours at a time, both words' loads in flight
-        bool more = true;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if (cand[u]) {
+                uint32_t h = 0;
+                if (f2[u].x >= 0) h |= (bm_word<kSmem>(vcur, f2[u].x >> 5) >> (f2[u].x & 31)) & 1u;
+                if (f2[u].y >= 0) h |= (bm_word<kSmem>(vcur, f2[u].y >> 5) >> (f2[u].y & 31)) & 1u;
+                found[u] = h != 0;
+                j[u] = min(ib[u] + 2, ie[u]);
+            }
+        }
+        // own tests: the aligned group of 4 in-neighbours holding j, one
+        // 16-byte load per lane (scattered 4-byte loads cost a cache
+        // wavefront each), both words' loads in flight
+        bool more = false;
+#pragma unroll
+        for (int u = 0; u < U; ++u) more |= cand[u] && !found[u] && j[u] < min(ie[u], ib[u] + a.pull_serial);
         for (int r = 0; more; ++r) {
             more = false;
-            int uu[U][4];
+            int4 uu[U];
 #pragma unroll
             for (int u = 0; u < U; ++u) {
                 const int jl = min(ie[u], ib[u] + a.pull_serial);
-#pragma unroll
-                for (int x = 0; x < 4; ++x) uu[u][x] = (cand[u] && !found[u] && j[u] + x < jl) ? __ldg(a.pull_idx + j[u] + x) : -1;
+                uu[u] = (cand[u] && !found[u] && j[u] < jl)
+                            ? __ldg(reinterpret_cast<const int4*>(a.pull_idx + (j[u] & ~3)))
+                            : make_int4(-1, -1, -1, -1);
             }
 #pragma unroll
             for (int u = 0; u < U; ++u) {
                 const int jl = min(ie[u], ib[u] + a.pull_serial);
-                uint32_t h = 0;
-#pragma unroll
-                for (int x = 0; x < 4; ++x)
-                    if (uu[u][x] >= 0) h |= (bm_word<kSmem>(vcur, uu[u][x] >> 5) >> (uu[u][x] & 31)) & 1u;
                 if (cand[u] && !found[u] && j[u] < jl) {
+                    const int g0 = j[u] & ~3;
+                    const int xs[4] = {uu[u].x, uu[u].y, uu[u].z, uu[u].w};
+                    uint32_t h = 0;
+#pragma unroll
+                    for (int x = 0; x < 4; ++x)
+                        if (g0 + x >= j[u] && g0 + x < jl) h |= (bm_word<kSmem>(vcur, xs[x] >> 5) >> (xs[x] & 31)) & 1u;
                     found[u] = h != 0;
-                    j[u] = min(j[u] + 4, jl);
+                    j[u] = min(g0 + 4, jl);
                     more |= !found[u] && j[u] < jl;
                 }
             }
@@ -510,7 +543,8 @@ __device__ void pull_level(const SsspArgs& a, int step, const uint32_t* vcur, ui
             // rows with in-arcs left: each round packs the unresolved rows of
             // the warp end to end, tests their next 32 in-arcs (one per lane)
             // and resolves every owner from one ballot; found rows drop out
-            while (true) {
+            const bool left = __any_sync(kFull, cand[u] && !found[u] && j[u] < ie[u]);
+            while (left) {
                 const int rem = (cand[u] && !found[u]) ? ie[u] - j[u] : 0;
                 const int incl = warp_inclusive_scan(rem, lane);
                 const int total = __shfl_sync(kFull, incl, 31);
@@ -568,22 +602,32 @@ __device__ __noinline__ void list_pull_level(const SsspArgs& a, int step, uint32
         const bool has = i < ncand;
         const int v = has ? __ldcg(cand + i) : 0;
         int ib = 0, ie = 0;
+        int2 f2 = make_int2(-1, -1);
         if (has) {
             ib = __ldg(a.in_ptr + v);
             ie = __ldg(a.in_ptr + v + 1);
+            f2 = __ldg(a.first2 + v);  // in parallel with the row bounds
         }
-        int j = ib;
+        // the first two in-neighbours first (rows are in descending degree order)
         bool found = false;
+        {
+            const int d0 = f2.x >= 0 ? __ldcg(a.dist + f2.x) : -1;
+            const int d1 = f2.y >= 0 ? __ldcg(a.dist + f2.y) : -1;
+            found = (d0 >= 0 && d0 < step) || (d1 >= 0 && d1 < step);
+        }
+        int j = min(ib + 2, ie);
         const int jl = min(ie, ib + a.pull_serial);
         while (!found && j < jl) {
-            int uu[4], du[4];
+            // the aligned group of 4 in-neighbours holding j, one 16-byte load
+            const int g0 = j & ~3;
+            const int4 q = __ldg(reinterpret_cast<const int4*>(a.pull_idx + g0));
+            const int uu[4] = {q.x, q.y, q.z, q.w};
+            int du[4];
 #pragma unroll
-            for (int x = 0; x < 4; ++x) uu[x] = j + x < jl ? __ldg(a.pull_idx + j + x) : -1;
-#pragma unroll
-            for (int x = 0; x < 4; ++x) du[x] = uu[x] >= 0 ? __ldcg(a.dist + uu[x]) : -1;
+            for (int x = 0; x < 4; ++x) du[x] = (g0 + x >= j && g0 + x < jl) ? __ldcg(a.dist + uu[x]) : -1;
 #pragma unroll
             for (int x = 0; x < 4; ++x) found |= du[x] >= 0 && du[x] < step;
-            j = min(j + 4, jl);
+            j = min(g0 + 4, jl);
         }
         // rows with in-arcs left: packed 32 at a time across the warp, as in pull_level
         while (true) {
@@ -940,6 +984,7 @@ int sssp_launch(dawn_graph* g, int32_t src, int32_t* dist_dev, const dawn_sssp_o
     if (opts && opts->blocks_per_sm > 0 && opts->blocks_per_sm < bps) bps = opts->blocks_per_sm;
     a.smem_words = g->sssp_smem_bytes / 4;
     a.pull_idx = g->pull_idx;
+    a.first2 = g->first2;
     a.cand0 = g->cand[0];
     a.cand1 = g->cand[1];
     a.cand_cap = g->cand_cap;
@@ -1083,6 +1128,7 @@ int sssp_noalloc(const int32_t* row_ptr, const int32_t* col_idx, int32_t n, int6
     a.bar_parity = 0;  // the whole control block was just zeroed
     a.smem_words = 0;
     a.pull_idx = nullptr;  // push only
+    a.first2 = nullptr;
     a.cand0 = nullptr;  // push only: no candidate lists
     a.cand1 = nullptr;
     a.cand_cap = 0;
