@@ -222,12 +222,18 @@ __device__ __forceinline__ void flush_counts(long long nf, long long mf, CtrSlot
     }
     if (lane == 0) { s_nf[w] = nf; s_mf[w] = mf; }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        long long a = 0, b = 0;
-        for (int i = 0; i < kWarps; ++i) { a += s_nf[i]; b += s_mf[i]; }
-        if (a) atomicAdd(&out->nf, (unsigned long long)a);
-        if (b) atomicAdd(&out->mf, (unsigned long long)b);
-        if (s_cn && *s_cn) atomicAdd(&out->nc, (unsigned long long)*s_cn);
+    if (w == 0) {  // warp 0 sums the warps' partial counts
+        long long a = lane < kWarps ? s_nf[lane] : 0, b = lane < kWarps ? s_mf[lane] : 0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            a += __shfl_down_sync(kFull, a, o);
+            b += __shfl_down_sync(kFull, b, o);
+        }
+        if (lane == 0) {
+            if (a) atomicAdd(&out->nf, (unsigned long long)a);
+            if (b) atomicAdd(&out->mf, (unsigned long long)b);
+            if (s_cn && *s_cn) atomicAdd(&out->nc, (unsigned long long)*s_cn);
+        }
     }
 }
 
@@ -436,116 +442,129 @@ __device__ __forceinline__ uint32_t bm_word(const uint32_t* vcur, int w) {
 // BOVM pull over the whole bitmap (Alg. 1 / Eq. 4).  With `keep` (this
 // CTA's region of a candidate list) every candidate left unreached is
 // appended to it, for list pulls at the following levels.
+//
+// A warp takes kPullChunk of its bitmap words at a time, in two passes.
+// Pass 1: every candidate of the chunk tests its first two in-neighbours
+// (the likeliest to be reached: rows are in descending degree order), all
+// words' loads issued together and coalesced (first2 holds them densely);
+// most found vertices are settled here.  Pass 2: the candidates still open,
+// packed 32 to a round through a per-warp list in shared memory, test the rest
+// of their rows: up to pull_serial in-neighbours each, in aligned 16-byte
+// groups, then the rows left are packed end to end across the warp, 32
+// in-arcs per round, so that one long row does not hold 31 idle lanes.
+constexpr int kPullChunk = 4;
+__shared__ int s_pull_open[kWarps][kPullChunk * 32];  // pass 2 work, per warp (both instantiations)
+
 template <bool kSmem>
 __device__ void pull_level(const SsspArgs& a, int step, const uint32_t* vcur, uint32_t* vnext,
                            long long& nf, long long& mf, int32_t* keep, int* s_cn) {
-    constexpr int U = 2;  // bitmap words per warp per round
     const int lane = threadIdx.x & 31;
     const int gw = blockIdx.x * kWarps + (threadIdx.x >> 5);
     const int nw = gridDim.x * kWarps;
     const bool symmetric = a.in_ptr == a.row_ptr;
+    const unsigned below = (1u << lane) - 1u;
+    int* open = s_pull_open[threadIdx.x >> 5];
     if (kSmem) {
         const uint4* src4 = reinterpret_cast<const uint4*>(vcur);
         for (int i = threadIdx.x; i < (a.smem_words >> 2); i += kThreads) s_bitmap4[i] = __ldcg(src4 + i);
         __syncthreads();
     }
-    for (int w0 = gw; w0 < a.nwords; w0 += U * nw) {
-        uint32_t cur[U];
-        bool cand[U], found[U];
-        int ib[U], ie[U], j[U];
+    for (int w0 = gw; w0 < a.nwords; w0 += kPullChunk * nw) {
+        // ---- pass 1: the first two in-neighbours of every candidate
+        uint32_t cur[kPullChunk];
+        unsigned cmask = 0;  // bit k: this lane's vertex of word k is a candidate
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int w = w0 + u * nw;
-            cur[u] = kFull;
-            cand[u] = false;
-            found[u] = false;
-            ib[u] = ie[u] = j[u] = 0;
+        for (int k = 0; k < kPullChunk; ++k) {
+            const int w = w0 + k * nw;
+            cur[k] = kFull;
             if (w < a.nwords) {
-                cur[u] = bm_word<kSmem>(vcur, w);
+                cur[k] = bm_word<kSmem>(vcur, w);
                 // candidates: not reached, and with at least one in-arc (excl
                 // also covers the padding bits past n).  excl is kept out of
                 // the visited set itself: a vertex without in-arcs may still
                 // have out-arcs, and it must not look reached to them.
-                const uint32_t skip = cur[u] | __ldg(a.excl + w);
-                cand[u] = !((skip >> lane) & 1u);
+                const uint32_t skip = cur[k] | __ldg(a.excl + w);
+                if (!((skip >> lane) & 1u)) cmask |= 1u << k;
             }
         }
-        // words without a candidate (all reached or without in-arcs) only
-        // carry their bitmap word over
-        bool anyc = false;
+        if (!__any_sync(kFull, cmask)) {  // nothing to test: carry the words over
 #pragma unroll
-        for (int u = 0; u < U; ++u) anyc |= cand[u];
-        if (!__any_sync(kFull, anyc)) {
-#pragma unroll
-            for (int u = 0; u < U; ++u)
-                if (lane == 0 && w0 + u * nw < a.nwords) vnext[w0 + u * nw] = cur[u];
+            for (int k = 0; k < kPullChunk; ++k)
+                if (lane == 0 && w0 + k * nw < a.nwords) vnext[w0 + k * nw] = cur[k];
             continue;
         }
-        // the first two in-neighbours (the likeliest to be reached: rows are in
-        // descending degree order) come from one coalesced load per word
-        int2 f2[U];
+        int2 f2[kPullChunk];
+        int db[kPullChunk], de[kPullChunk];  // out-row bounds: m_f of the vertices found
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-            f2[u] = make_int2(-1, -1);
-            if (cand[u]) {
-                const int v = ((w0 + u * nw) << 5) + lane;
-                ib[u] = __ldg(a.in_ptr + v);
-                ie[u] = __ldg(a.in_ptr + v + 1);
-                f2[u] = __ldg(a.first2 + v);
+        for (int k = 0; k < kPullChunk; ++k) {
+            f2[k] = make_int2(-1, -1);
+            db[k] = de[k] = 0;
+            if ((cmask >> k) & 1u) {
+                const int v = ((w0 + k * nw) << 5) + lane;
+                f2[k] = __ldg(a.first2 + v);
+                db[k] = __ldg(a.row_ptr + v);
+                de[k] = __ldg(a.row_ptr + v + 1);
             }
         }
+        unsigned fmask = 0;
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-            if (cand[u]) {
-                uint32_t h = 0;
-                if (f2[u].x >= 0) h |= (bm_word<kSmem>(vcur, f2[u].x >> 5) >> (f2[u].x & 31)) & 1u;
-                if (f2[u].y >= 0) h |= (bm_word<kSmem>(vcur, f2[u].y >> 5) >> (f2[u].y & 31)) & 1u;
-                found[u] = h != 0;
-                j[u] = min(ib[u] + 2, ie[u]);
-            }
+        for (int k = 0; k < kPullChunk; ++k) {
+            uint32_t h = 0;
+            if (f2[k].x >= 0) h |= (bm_word<kSmem>(vcur, f2[k].x >> 5) >> (f2[k].x & 31)) & 1u;
+            if (f2[k].y >= 0) h |= (bm_word<kSmem>(vcur, f2[k].y >> 5) >> (f2[k].y & 31)) & 1u;
+            if (h) fmask |= 1u << k;
         }
-        // own tests: the aligned group of 4 in-neighbours holding j, one
-        // 16-byte load per lane (scattered 4-byte loads cost a cache
-        // wavefront each), both words' loads in flight
-        bool more = false;
+        int nopen = 0;  // warp-uniform
 #pragma unroll
-        for (int u = 0; u < U; ++u) more |= cand[u] && !found[u] && j[u] < min(ie[u], ib[u] + a.pull_serial);
-        for (int r = 0; more; ++r) {
-            more = false;
-            int4 uu[U];
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const int jl = min(ie[u], ib[u] + a.pull_serial);
-                uu[u] = (cand[u] && !found[u] && j[u] < jl)
-                            ? __ldg(reinterpret_cast<const int4*>(a.pull_idx + (j[u] & ~3)))
-                            : make_int4(-1, -1, -1, -1);
-            }
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const int jl = min(ie[u], ib[u] + a.pull_serial);
-                if (cand[u] && !found[u] && j[u] < jl) {
-                    const int g0 = j[u] & ~3;
-                    const int xs[4] = {uu[u].x, uu[u].y, uu[u].z, uu[u].w};
-                    uint32_t h = 0;
-#pragma unroll
-                    for (int x = 0; x < 4; ++x)
-                        if (g0 + x >= j[u] && g0 + x < jl) h |= (bm_word<kSmem>(vcur, xs[x] >> 5) >> (xs[x] & 31)) & 1u;
-                    found[u] = h != 0;
-                    j[u] = min(g0 + 4, jl);
-                    more |= !found[u] && j[u] < jl;
-                }
-            }
-        }
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int w = w0 + u * nw;
+        for (int k = 0; k < kPullChunk; ++k) {
+            const int w = w0 + k * nw;
             if (w >= a.nwords) continue;  // warp-uniform
+            const int v = (w << 5) + lane;
+            const bool f = (fmask >> k) & 1u;
+            const uint32_t newbits = __ballot_sync(kFull, f);
+            if (f) {
+                a.dist[v] = step;
+                nf += 1;
+                mf += de[k] - db[k];
+            }
+            // pass 2 may set more bits of w (atomicOr, in program order after this store)
+            if (lane == 0) vnext[w] = cur[k] | newbits;
+            const bool op = ((cmask & ~fmask) >> k) & 1u;
+            const unsigned ob = __ballot_sync(kFull, op);
+            if (op) open[nopen + __popc(ob & below)] = v;
+            nopen += __popc(ob);
+        }
+        __syncwarp();
+        // ---- pass 2: the rest of the open candidates' rows
+        for (int b0 = 0; b0 < nopen; b0 += 32) {
+            const bool has = b0 + lane < nopen;
+            const int v = has ? open[b0 + lane] : 0;
+            int ib = 0, ie = 0;
+            if (has) {
+                ib = __ldg(a.in_ptr + v);
+                ie = __ldg(a.in_ptr + v + 1);
+            }
+            int j = min(ib + 2, ie);
+            bool found = false;
+            const int jl = min(ie, ib + a.pull_serial);
+            while (!found && j < jl) {
+                // the aligned group of 4 in-neighbours holding j, one 16-byte load
+                const int g0 = j & ~3;
+                const int4 q = __ldg(reinterpret_cast<const int4*>(a.pull_idx + g0));
+                const int xs[4] = {q.x, q.y, q.z, q.w};
+                uint32_t h = 0;
+#pragma unroll
+                for (int x = 0; x < 4; ++x)
+                    if (g0 + x >= j && g0 + x < jl) h |= (bm_word<kSmem>(vcur, xs[x] >> 5) >> (xs[x] & 31)) & 1u;
+                found = h != 0;
+                j = min(g0 + 4, jl);
+            }
             // rows with in-arcs left: each round packs the unresolved rows of
             // the warp end to end, tests their next 32 in-arcs (one per lane)
             // and resolves every owner from one ballot; found rows drop out
-            const bool left = __any_sync(kFull, cand[u] && !found[u] && j[u] < ie[u]);
+            const bool left = __any_sync(kFull, has && !found && j < ie);
             while (left) {
-                const int rem = (cand[u] && !found[u]) ? ie[u] - j[u] : 0;
+                const int rem = (has && !found) ? ie - j : 0;
                 const int incl = warp_inclusive_scan(rem, lane);
                 const int total = __shfl_sync(kFull, incl, 31);
                 if (total == 0) break;
@@ -557,7 +576,7 @@ __device__ void pull_level(const SsspArgs& a, int step, const uint32_t* vcur, ui
                     const int pv = __shfl_sync(kFull, ex, cidx);
                     if (pv <= lane) o = cidx;
                 }
-                const int oj = __shfl_sync(kFull, j[u], o);
+                const int oj = __shfl_sync(kFull, j, o);
                 const int oex = __shfl_sync(kFull, ex, o);
                 bool hh = false;
                 if (lane < total) {
@@ -568,20 +587,19 @@ __device__ void pull_level(const SsspArgs& a, int step, const uint32_t* vcur, ui
                 if (rem > 0 && ex < 32) {
                     const int hi = min(32, ex + rem);
                     const unsigned seg = (hi >= 32 ? kFull : ((1u << hi) - 1u)) & ~((1u << ex) - 1u);
-                    if (hits & seg) found[u] = true;
-                    j[u] += hi - ex;
+                    if (hits & seg) found = true;
+                    j += hi - ex;
                 }
             }
-            const uint32_t newbits = __ballot_sync(kFull, found[u]);
-            if (found[u]) {
-                const int v = (w << 5) + lane;
+            if (found) {
                 a.dist[v] = step;
+                atomicOr(vnext + (v >> 5), 1u << (v & 31));
                 nf += 1;
-                mf += symmetric ? (ie[u] - ib[u]) : (__ldg(a.row_ptr + v + 1) - __ldg(a.row_ptr + v));
+                mf += symmetric ? (ie - ib) : (__ldg(a.row_ptr + v + 1) - __ldg(a.row_ptr + v));
             }
-            if (lane == 0) vnext[w] = cur[u] | newbits;
-            if (keep) warp_keep(cand[u] && !found[u], (w << 5) + lane, lane, keep, s_cn);
+            if (keep) warp_keep(has && !found, v, lane, keep, s_cn);
         }
+        __syncwarp();  // the open list is refilled by the next chunk
     }
 }
 
