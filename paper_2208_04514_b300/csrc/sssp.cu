@@ -248,6 +248,12 @@ __device__ __forceinline__ void warp_keep(bool keep, int v, int lane, int32_t* l
     if (keep) list[base + __popc(b & ((1u << lane) - 1u))] = v;
 }
 
+// Vertices first reached by a level and the sum of their out-degrees (the
+// values the out-of-line level functions return in registers).
+struct LevelCount {
+    long long nf, mf;
+};
+
 // Load the 32 queue entries starting at slot b (one per lane).
 __device__ __forceinline__ void load_batch(const Queue& q, int qn, int b, int lane, int2& e, int& eoff) {
     const int i = b + lane;
@@ -607,12 +613,14 @@ __device__ void pull_level(const SsspArgs& a, int step, const uint32_t* vcur, ui
 // unreached), instead of the whole bitmap.  The step-start visited test reads
 // the distances: 0 <= dist[u] < step exactly when u was reached before this
 // level (vertices found now carry dist = step), so found vertices can be set
-// in the visited bitmap in place.  Found rows go straight to the push queue
-// (a push level may follow); candidates still unreached move to `keep`.
-__device__ __noinline__ void list_pull_level(const SsspArgs& a, int step, uint32_t* vis, const int32_t* cand, int ncand,
-                                int32_t* keep, int* s_cn, Queue qout, CtrSlot* out, long long& nf,
-                                long long& mf) {
+// in the visited bitmap in place.  Candidates still unreached move to `keep`.
+// No push queue is written (a list pull is mostly followed by another one);
+// a push after it expands the frontier straight from this level's list
+// (list_push_level).
+__device__ __noinline__ LevelCount list_pull_level(const SsspArgs& a, int step, uint32_t* vis, const int32_t* cand,
+                                                  int ncand, int32_t* keep, int* s_cn) {
     const int lane = threadIdx.x & 31;
+    long long nf = 0, mf = 0;
     const bool symmetric = a.in_ptr == a.row_ptr;
     // one candidate per thread and round; the loop bound is the same for the whole warp
     for (int base = threadIdx.x & ~31; base < ncand; base += kThreads) {
@@ -677,18 +685,71 @@ __device__ __noinline__ void list_pull_level(const SsspArgs& a, int step, uint32
                 j += hi - ex;
             }
         }
-        int rb = 0, re = 0;
         if (found) {
             a.dist[v] = step;
             atomicOr(vis + (v >> 5), 1u << (v & 31));
-            rb = symmetric ? ib : __ldg(a.row_ptr + v);
-            re = symmetric ? ie : __ldg(a.row_ptr + v + 1);
             nf += 1;
-            mf += re - rb;
+            mf += symmetric ? (ie - ib) : (__ldg(a.row_ptr + v + 1) - __ldg(a.row_ptr + v));
         }
-        warp_enqueue(found, rb, re, lane, qout, out);
         warp_keep(has && !found, v, lane, keep, s_cn);
     }
+    return {nf, mf};
+}
+
+// SOVM push right after a list pull (Eq. 7), without a queue: the frontier
+// is the entries of that pull's input list (this CTA's part) whose distance
+// is the level just finished (step - 1).  Each warp packs the rows of its
+// frontier vertices end to end and expands them 32 arcs per round; claims
+// and the next queue are as in push_level.
+__device__ __noinline__ LevelCount list_push_level(const SsspArgs& a, int step, uint32_t* vis, const int32_t* list,
+                                                  int nlist, CtrSlot* out) {
+    const int lane = threadIdx.x & 31;
+    long long nf = 0, mf = 0;
+    // the queue of the frontier this level finds: (step & 1) ? q1 : q0
+    const Queue qout = (step & 1) ? Queue{a.q1, a.q1off} : Queue{a.q0, a.q0off};
+    // one list entry per thread and round; the loop bound is the same for the whole warp
+    for (int base = threadIdx.x & ~31; base < nlist; base += kThreads) {
+        const int i = base + lane;
+        const int v = i < nlist ? __ldcg(list + i) : -1;
+        const bool fr = v >= 0 && __ldcg(a.dist + v) == step - 1;
+        int j = 0, je = 0;
+        if (fr) {
+            j = __ldg(a.row_ptr + v);
+            je = __ldg(a.row_ptr + v + 1);
+        }
+        while (__any_sync(kFull, j < je)) {
+            const int rem = je - j;
+            const int incl = warp_inclusive_scan(rem, lane);
+            const int total = __shfl_sync(kFull, incl, 31);
+            const int ex = incl - rem;
+            int o = 0;
+#pragma unroll
+            for (int bb = 16; bb > 0; bb >>= 1) {
+                const int cidx = o + bb;
+                const int pv = __shfl_sync(kFull, ex, cidx);
+                if (pv <= lane) o = cidx;
+            }
+            const int oj = __shfl_sync(kFull, j, o);
+            const int oex = __shfl_sync(kFull, ex, o);
+            bool claimed = false;
+            int c = 0, rb = 0, re = 0;
+            if (lane < total) {
+                c = __ldg(a.col_idx + oj + (lane - oex));
+                const uint32_t bit = 1u << (c & 31);
+                if (!(__ldcg(vis + (c >> 5)) & bit)) claimed = !(atomicOr(vis + (c >> 5), bit) & bit);
+            }
+            if (claimed) {
+                a.dist[c] = step;
+                rb = __ldg(a.row_ptr + c);
+                re = __ldg(a.row_ptr + c + 1);
+                nf += 1;
+                mf += re - rb;
+            }
+            warp_enqueue(claimed, rb, re, lane, qout, out);
+            if (rem > 0 && ex < 32) j += min(32, ex + rem) - ex;
+        }
+    }
+    return {nf, mf};
 }
 
 // After a pull level: queue the vertices it reached (bits of vnow not in vold).
@@ -761,7 +822,7 @@ __device__ __noinline__ void fused_init_level1(const SsspArgs& a, int srb, int s
 __global__ void __launch_bounds__(kThreads, DAWN_SSSP_MIN_CTAS) sssp_kernel(SsspArgs a) {
     Ctl* ctl = a.ctl;
     __shared__ unsigned long long s_snap[5];  // {qpack, nf, mf, nc, lr} of the level just finished
-    __shared__ int s_cn, s_cin;               // this CTA's candidates: being kept / to test
+    __shared__ int s_cn, s_cin, s_cprev;      // this CTA's candidates: being kept / to test / tested last
     __shared__ int s_status;
     // an earlier call that failed leaves the barrier state inconsistent: this
     // launch then stops before its first barrier (its outputs are undefined,
@@ -836,7 +897,7 @@ __global__ void __launch_bounds__(kThreads, DAWN_SSSP_MIN_CTAS) sssp_kernel(Sssp
     uint32_t* vcur = a.vis0;
     uint32_t* vnext = a.vis1;
     // level kinds: push (SOVM), pull over the bitmap, pull over the candidate lists
-    enum { kPush = 0, kBitmapPull = 1, kListPull = 2 };
+    enum { kPush = 0, kBitmapPull = 1, kListPull = 2 };  // a push after a list pull reads its list
     // the loop starts after level 0 (the source), or after level 1 when fused
     long long mu = a.m - (fused ? sdeg : 0);  // arcs out of vertices not yet reached
     long long prev_nf = fused ? 1 : 0;
@@ -850,7 +911,7 @@ __global__ void __launch_bounds__(kThreads, DAWN_SSSP_MIN_CTAS) sssp_kernel(Sssp
     const bool lists = a.cand0 != nullptr && region * gridDim.x <= a.cand_cap;
     int32_t* cl[2] = {a.cand0 + blockIdx.x * region, a.cand1 + blockIdx.x * region};
     int cpar = 0;  // the list the next list pull reads
-    if (threadIdx.x == 0) s_cn = s_cin = 0;
+    if (threadIdx.x == 0) s_cn = s_cin = s_cprev = 0;
     __syncthreads();
     while (true) {
         CtrSlot* cur = &ctr[step % 3];
@@ -898,9 +959,17 @@ __global__ void __launch_bounds__(kThreads, DAWN_SSSP_MIN_CTAS) sssp_kernel(Sssp
             else pull_level<false>(a, step + 1, vcur, vnext, nf, mf, keep, &s_cn);
             ++pulls;
         } else if (kind == kListPull) {
-            list_pull_level(a, step + 1, vcur, cl[cpar], s_cin, cl[cpar ^ 1], &s_cn, qnext, out, nf, mf);
+            const LevelCount lc = list_pull_level(a, step + 1, vcur, cl[cpar], s_cin, cl[cpar ^ 1], &s_cn);
+            nf = lc.nf;
+            mf = lc.mf;
             cpar ^= 1;
             ++pulls;
+        } else if (last == kListPull) {
+            // the frontier: entries of the last list pull's input list found by it
+            const LevelCount lc = list_push_level(a, step + 1, vcur, cl[cpar ^ 1], s_cprev, out);
+            nf = lc.nf;
+            mf = lc.mf;
+            ++pushes;
         } else {
             push_level(a, step + 1, vcur, qcur, qpack, qlong, qnext, out, nf, mf);
             ++pushes;
@@ -909,7 +978,8 @@ __global__ void __launch_bounds__(kThreads, DAWN_SSSP_MIN_CTAS) sssp_kernel(Sssp
         if (!grid_barrier(ctl, bar, bar_target, a.spin_limit, out, s_snap)) return;
         if (pull) {
             if (threadIdx.x == 0) {
-                s_cin = s_cn;  // the list just written is the one the next list pull reads
+                s_cprev = s_cin;  // the list just tested (read by a list push)
+                s_cin = s_cn;     // the list just written is the one the next list pull reads
                 s_cn = 0;
             }
             __syncthreads();
