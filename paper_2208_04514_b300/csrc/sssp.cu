@@ -309,8 +309,12 @@ __device__ __forceinline__ void warp_enqueue_group(unsigned has, const int* rb, 
 // atomicOr claims and the row_ptr loads of all windows are issued back to back,
 // so a warp waits for one chain of memory round trips per group, not per
 // window.
+//
+// pretest: read each target's bitmap word before claiming it, to spare the
+// atomics on targets already reached; off while few are reached (the read
+// would only lengthen the chain of round trips).
 __device__ void push_level(const SsspArgs& a, int step, uint32_t* vis, Queue qin, unsigned long long pack,
-                           bool qlong, Queue qout, CtrSlot* out, long long& nf, long long& mf) {
+                           bool qlong, bool pretest, Queue qout, CtrSlot* out, long long& nf, long long& mf) {
     const int lane = threadIdx.x & 31;
     const int qn = (int)(pack >> 32);
     const long long E = (long long)(pack & 0xffffffffull);
@@ -323,6 +327,7 @@ __device__ void push_level(const SsspArgs& a, int step, uint32_t* vis, Queue qin
     // without a read-only pre-test.  Heavy levels (hub rows): equal arc
     // ranges found by a 32-ary search.
     const bool light = E <= 8LL * qn && !qlong;
+    pretest = pretest && !light;
     long long a0, a1;
     int bstart;
     int2 e;
@@ -393,7 +398,7 @@ __device__ void push_level(const SsspArgs& a, int step, uint32_t* vis, Queue qin
         for (int q = 0; q < kPushGroup; ++q) c[q] = cidx[q] >= 0 ? __ldg(a.col_idx + cidx[q]) : -1;
         uint32_t wv[kPushGroup];
 #pragma unroll
-        for (int q = 0; q < kPushGroup; ++q) wv[q] = (c[q] >= 0 && !light) ? __ldcg(vis + (c[q] >> 5)) : (c[q] >= 0 ? 0u : kFull);
+        for (int q = 0; q < kPushGroup; ++q) wv[q] = (c[q] >= 0 && pretest) ? __ldcg(vis + (c[q] >> 5)) : (c[q] >= 0 ? 0u : kFull);
         // targets that look unreached: claim them and fetch their rows together
         int rb[kPushGroup], re[kPushGroup];
         unsigned cand = 0;
@@ -971,7 +976,7 @@ __global__ void __launch_bounds__(kThreads, DAWN_SSSP_MIN_CTAS) sssp_kernel(Sssp
             mf = lc.mf;
             ++pushes;
         } else {
-            push_level(a, step + 1, vcur, qcur, qpack, qlong, qnext, out, nf, mf);
+            push_level(a, step + 1, vcur, qcur, qpack, qlong, 16 * reached > a.n, qnext, out, nf, mf);
             ++pushes;
         }
         flush_counts(nf, mf, out, pull ? &s_cn : nullptr);
