@@ -16,6 +16,11 @@ What each function follows (the C file carries the same notes):
 * ``certificate``   -- O(n+m) exactness certificate for one distance vector.
 * ``wcc``           -- weakly connected component labels.
 * ``msbfs``         -- APSP-style batch: SOVM per source + ecc / sum / reached.
+* ``wsssp_minplus`` -- weighted extension (Sec. 5, (min, +) future work): the
+                       SOVM rounds of Alg. 3 over (min, +), non-negative int32
+                       weights, int64 distances.
+* ``dijkstra``      -- textbook Dijkstra (binary heap), pin for the above.
+* ``wcertificate``  -- O(n+m) exactness certificate for weighted distances.
 
 Every function is pinned by ``tests/test_oracle_pins.py`` to closed forms,
 brute force, a library routine (scipy) and invariants; none is "parity
@@ -69,6 +74,9 @@ def _load():
             "oracle_msbfs": [i32, vp, vp, vp, i32, vp, vp, vp, vp],
             "oracle_parents": [i32, vp, vp, vp, vp],
             "oracle_centrality": [i32, vp, vp, vp, i32, vp, vp, vp, vp, vp, vp],
+            "oracle_wsssp_minplus": [i32, vp, vp, vp, i32, vp, vp, vp],
+            "oracle_dijkstra": [i32, vp, vp, vp, i32, vp],
+            "oracle_wcertificate": [i32, vp, vp, vp, i32, vp, vp],
         }
         for name, args in sig.items():
             f = getattr(lib, name)
@@ -204,3 +212,47 @@ def msbfs(row_ptr, col_idx, sources, keep_dist: bool = True):
     if rc != 0:
         raise ValueError("oracle_msbfs: bad input")
     return block, ecc, dsum, reached
+
+
+def _w(weights, m):
+    w = np.ascontiguousarray(weights, dtype=np.int32)
+    if w.size != m:
+        raise ValueError(f"need {m} weights, got {w.size}")
+    return w if w.size else np.zeros(1, dtype=np.int32)
+
+
+def wsssp_minplus(row_ptr, col_idx, weights, src: int, with_stats: bool = False):
+    """(min, +) SOVM rounds.  Returns dist (int64[n], -1 = no path) [, rounds, arcs offered]."""
+    rp, ci = _csr(row_ptr, col_idx)
+    n = rp.size - 1
+    w = _w(weights, int(rp[-1]))
+    dist = np.empty(n, dtype=np.int64)
+    rounds = ctypes.c_int32(0)
+    relax = ctypes.c_int64(0)
+    rc = _load().oracle_wsssp_minplus(n, _p(rp), _p(ci), _p(w), int(src), _p(dist),
+                                      ctypes.addressof(rounds), ctypes.addressof(relax))
+    if rc != 0:
+        raise ValueError(f"oracle_wsssp_minplus failed ({rc})")
+    return (dist, rounds.value, relax.value) if with_stats else dist
+
+
+def dijkstra(row_ptr, col_idx, weights, src: int):
+    """Textbook Dijkstra.  Returns dist (int64[n], -1 = no path)."""
+    rp, ci = _csr(row_ptr, col_idx)
+    n = rp.size - 1
+    w = _w(weights, int(rp[-1]))
+    dist = np.empty(n, dtype=np.int64)
+    if _load().oracle_dijkstra(n, _p(rp), _p(ci), _p(w), int(src), _p(dist)) != 0:
+        raise ValueError("oracle_dijkstra failed")
+    return dist
+
+
+def wcertificate(row_ptr, col_idx, weights, src: int, dist) -> tuple[int, int]:
+    """(1, -1) when dist is the exact weighted distance vector from src, else (0, bad vertex)."""
+    rp, ci = _csr(row_ptr, col_idx)
+    n = rp.size - 1
+    w = _w(weights, int(rp[-1]))
+    d = np.ascontiguousarray(dist, dtype=np.int64)
+    bad = ctypes.c_int32(-1)
+    ok = _load().oracle_wcertificate(n, _p(rp), _p(ci), _p(w), int(src), _p(d), ctypes.addressof(bad))
+    return int(ok), int(bad.value)

@@ -40,7 +40,23 @@
  *   oracle_msbfs         APSP as SOVM from each listed source (Sec. 3.3,
  *                        "APSP repeats the SSSP per source"), plus per-source
  *                        eccentricity (largest finite distance, Table 1's
- *                        epsilon(i)), distance sum and reached count.
+ *                        epsilon(i)), distance sum and reached count. *
+ * The weighted extension (Sec. 5 names (min, +) operations on weighted graphs
+ * as future work; the readings are in the design notes): non-negative int32
+ * arc weights, int64 distances, -1 = no path.
+ *   oracle_wsssp_minplus  the SOVM iteration of Alg. 3 over the (min, +)
+ *                        semiring: each round every frontier vertex i (its
+ *                        distance changed in the previous round) offers
+ *                        d(i) + w(i, c) to every out-neighbour c, with d(i)
+ *                        as it was at the start of the round; the minimum
+ *                        is kept; the vertices whose distance fell form the
+ *                        next frontier; stop on a round that changes nothing.
+ *   oracle_dijkstra      textbook Dijkstra with a binary heap (a different
+ *                        algorithm for the same distances: a pin).
+ *   oracle_wcertificate  O(n + m) exactness check of a weighted distance
+ *                        vector: d(src) = 0; no arc from a reached vertex
+ *                        can lower its head; every reached vertex is reached
+ *                        from src along arcs with d(u) + w = d(v).
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -417,4 +433,185 @@ int oracle_centrality(int32_t n, const int32_t* row_ptr, const int32_t* col_idx,
     free(dist);
     free(count);
     return 0;
+}
+
+
+/* ------------------------------------------------------------------------
+ * Weighted extension: (min, +) in place of (OR, AND).
+ * ---------------------------------------------------------------------- */
+
+#define ORACLE_INF INT64_MAX
+
+/*
+ * The SOVM loop of Alg. 3 with (min, +): alpha = vertices whose distance
+ * changed in the previous round; each round every alpha[i] offers
+ * dprev[i] + w to each out-neighbour, dprev being the distances at the start
+ * of the round, and the smaller value is kept; beta collects the vertices
+ * whose distance fell.  A round that lowers nothing ends the loop.  With
+ * non-negative weights at most n - 1 rounds change something; a further one
+ * is reported as an error (-2).  rounds (nullable) receives the number of
+ * rounds that changed a distance; relax (nullable) the arcs offered.
+ */
+int oracle_wsssp_minplus(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, const int32_t* w,
+                         int32_t src, int64_t* dist, int32_t* rounds, int64_t* relax) {
+    if (n <= 0 || src < 0 || src >= n) return -1;
+    for (int32_t v = 0; v < n; ++v)
+        for (int32_t j = row_ptr[v]; j < row_ptr[v + 1]; ++j)
+            if (w[j] < 0) return -1;
+    int64_t* d = (int64_t*)malloc(sizeof(int64_t) * (size_t)n);
+    int64_t* dprev = (int64_t*)malloc(sizeof(int64_t) * (size_t)n);
+    uint8_t* alpha = (uint8_t*)calloc((size_t)n, 1);
+    uint8_t* beta = (uint8_t*)calloc((size_t)n, 1);
+    if (!d || !dprev || !alpha || !beta) {
+        free(d); free(dprev); free(alpha); free(beta);
+        return -1;
+    }
+    for (int32_t v = 0; v < n; ++v) d[v] = ORACLE_INF;
+    d[src] = 0;
+    alpha[src] = 1;
+    int32_t r = 0;
+    int64_t offered = 0;
+    int rc = 0;
+    while (1) {
+        memcpy(dprev, d, sizeof(int64_t) * (size_t)n);
+        int changed = 0;
+        for (int32_t i = 0; i < n; ++i) {
+            if (!alpha[i]) continue;
+            for (int32_t j = row_ptr[i]; j < row_ptr[i + 1]; ++j) {
+                const int32_t c = col_idx[j];
+                const int64_t nd = dprev[i] + (int64_t)w[j];
+                offered += 1;
+                if (nd < d[c]) {
+                    d[c] = nd;
+                    beta[c] = 1;
+                    changed = 1;
+                }
+            }
+        }
+        if (!changed) break;
+        r += 1;
+        if (r > n - 1) { rc = -2; break; }
+        uint8_t* t = alpha;
+        alpha = beta;
+        beta = t;
+        memset(beta, 0, (size_t)n);
+    }
+    for (int32_t v = 0; v < n; ++v) dist[v] = d[v] == ORACLE_INF ? -1 : d[v];
+    if (rounds) *rounds = r;
+    if (relax) *relax = offered;
+    free(d); free(dprev); free(alpha); free(beta);
+    return rc;
+}
+
+/* Textbook Dijkstra: binary min-heap of (distance, vertex) with lazy deletion. */
+typedef struct { int64_t key; int32_t v; } oracle_heap_item;
+
+static void heap_push(oracle_heap_item* h, int64_t* size, int64_t key, int32_t v) {
+    int64_t i = (*size)++;
+    h[i].key = key;
+    h[i].v = v;
+    while (i > 0) {
+        const int64_t p = (i - 1) / 2;
+        if (h[p].key <= h[i].key) break;
+        oracle_heap_item t = h[p]; h[p] = h[i]; h[i] = t;
+        i = p;
+    }
+}
+
+static oracle_heap_item heap_pop(oracle_heap_item* h, int64_t* size) {
+    oracle_heap_item top = h[0];
+    h[0] = h[--(*size)];
+    int64_t i = 0;
+    while (1) {
+        const int64_t l = 2 * i + 1, r = l + 1;
+        int64_t m = i;
+        if (l < *size && h[l].key < h[m].key) m = l;
+        if (r < *size && h[r].key < h[m].key) m = r;
+        if (m == i) break;
+        oracle_heap_item t = h[m]; h[m] = h[i]; h[i] = t;
+        i = m;
+    }
+    return top;
+}
+
+int oracle_dijkstra(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, const int32_t* w,
+                    int32_t src, int64_t* dist) {
+    if (n <= 0 || src < 0 || src >= n) return -1;
+    const int64_t m = row_ptr[n];
+    oracle_heap_item* h = (oracle_heap_item*)malloc(sizeof(oracle_heap_item) * (size_t)(m + 1));
+    uint8_t* done = (uint8_t*)calloc((size_t)n, 1);
+    if (!h || !done) { free(h); free(done); return -1; }
+    for (int32_t v = 0; v < n; ++v) dist[v] = ORACLE_INF;
+    dist[src] = 0;
+    int64_t size = 0;
+    heap_push(h, &size, 0, src);
+    while (size > 0) {
+        const oracle_heap_item it = heap_pop(h, &size);
+        if (done[it.v]) continue;
+        done[it.v] = 1;
+        for (int32_t j = row_ptr[it.v]; j < row_ptr[it.v + 1]; ++j) {
+            const int32_t c = col_idx[j];
+            const int64_t nd = it.key + (int64_t)w[j];
+            if (nd < dist[c]) {
+                dist[c] = nd;
+                heap_push(h, &size, nd, c);
+            }
+        }
+    }
+    for (int32_t v = 0; v < n; ++v)
+        if (dist[v] == ORACLE_INF) dist[v] = -1;
+    free(h);
+    free(done);
+    return 0;
+}
+
+/*
+ * Exactness certificate for non-negative weights.  Returns 1 when
+ *   (1) dist[src] = 0 and every entry is >= -1;
+ *   (2) for every arc u -> v with dist[u] >= 0: dist[v] >= 0 and
+ *       dist[v] <= dist[u] + w (no arc can lower v);
+ *   (3) every v with dist[v] >= 0 is reached from src along tight arcs
+ *       (dist[u] + w = dist[v]), found by a graph search over them.
+ * (3) gives a path of weight dist[v], so dist[v] >= the true distance; (2)
+ * along a shortest path gives dist[v] <= it, and closes the reached set
+ * under out-arcs.  Zero weights need the search in (3): vertices that only
+ * support each other through zero-weight arcs are not reached from src.
+ * Returns 0 otherwise, with *bad the first offending vertex.
+ */
+int oracle_wcertificate(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, const int32_t* w,
+                        int32_t src, const int64_t* dist, int32_t* bad) {
+    *bad = -1;
+    if (n <= 0 || src < 0 || src >= n) return 0;
+    if (dist[src] != 0) { *bad = src; return 0; }
+    for (int32_t v = 0; v < n; ++v)
+        if (dist[v] < -1) { *bad = v; return 0; }
+    for (int32_t u = 0; u < n; ++u) {
+        if (dist[u] < 0) continue;
+        for (int32_t j = row_ptr[u]; j < row_ptr[u + 1]; ++j) {
+            const int32_t v = col_idx[j];
+            if (dist[v] < 0 || dist[v] > dist[u] + (int64_t)w[j]) { *bad = v; return 0; }
+        }
+    }
+    uint8_t* seen = (uint8_t*)calloc((size_t)n, 1);
+    int32_t* stack = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
+    if (!seen || !stack) { free(seen); free(stack); return 0; }
+    int64_t top = 0;
+    stack[top++] = src;
+    seen[src] = 1;
+    while (top > 0) {
+        const int32_t u = stack[--top];
+        for (int32_t j = row_ptr[u]; j < row_ptr[u + 1]; ++j) {
+            const int32_t v = col_idx[j];
+            if (!seen[v] && dist[v] == dist[u] + (int64_t)w[j]) {
+                seen[v] = 1;
+                stack[top++] = v;
+            }
+        }
+    }
+    int ok = 1;
+    for (int32_t v = 0; v < n && ok; ++v)
+        if (dist[v] >= 0 && !seen[v]) { *bad = v; ok = 0; }
+    free(seen);
+    free(stack);
+    return ok;
 }

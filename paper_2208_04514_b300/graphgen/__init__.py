@@ -13,6 +13,8 @@ Workloads (seeds fixed so that every run sees the same graphs):
                       symmetrised, seed 2
 ``lattice(4096)``     4096 x 4096 4-neighbour lattice, bonds deleted with p = 0.1, seed 3
 ``rmat(16, seed=4)``  RMAT scale 16 for the batched all-sources workload
+``arc_weights``       integer arc weights for the weighted extension, uniform on
+                      [lo, hi] (default [1, 255], seed 7), symmetric per edge
 ====================  ===========================================================
 """
 from __future__ import annotations
@@ -55,6 +57,8 @@ def _load():
         lib.gg_splitmix64_first.argtypes = [u64]
         lib.gg_xoshiro_stream.restype = None
         lib.gg_xoshiro_stream.argtypes = [u64, i64, vp]
+        lib.gg_arc_weights.restype = None
+        lib.gg_arc_weights.argtypes = [vp, vp, i32, i32, i32, u64, ctypes.c_int, vp]
         _lib = lib
     return _lib
 
@@ -138,6 +142,18 @@ def xoshiro_stream(seed: int, count: int) -> np.ndarray:
     out = np.empty(count, dtype=np.uint64)
     _load().gg_xoshiro_stream(seed, count, out.ctypes.data)
     return out
+
+
+def arc_weights(g: Graph, lo: int = 1, hi: int = 255, seed: int = 7) -> np.ndarray:
+    """int32 weight per arc (aligned with ``col_idx``), uniform on [lo, hi] from a
+    hash of the arc's endpoints and ``seed``; both arcs of an undirected edge get
+    the same weight when ``g.symmetric``."""
+    if not (0 <= lo <= hi <= 2**31 - 1):
+        raise ValueError("need 0 <= lo <= hi <= 2^31 - 1")
+    out = np.empty(max(g.m, 1), dtype=np.int32)
+    _load().gg_arc_weights(g.row_ptr.ctypes.data, np.ascontiguousarray(g.col_idx, dtype=np.int32).ctypes.data
+                           if g.m else None, g.n, lo, hi, seed, 1 if g.symmetric else 0, out.ctypes.data)
+    return out[:g.m].copy()
 
 
 def from_arcs(n: int, src, dst, name: str = "arcs", symmetric: bool = False) -> Graph:

@@ -342,6 +342,25 @@ void gg_uniform_vertices(int32_t n, int32_t k, uint64_t seed, int32_t* out) {
     for (int32_t i = 0; i < k; ++i) out[i] = (int32_t)rng_below(&r, (uint32_t)n);
 }
 
+/*
+ * Arc weights for the weighted extension: w = lo + h mod (hi - lo + 1), h the
+ * splitmix64 output of seed mixed with the arc's endpoints.  With symmetric
+ * set the endpoints are taken as an unordered pair, so both arcs of an
+ * undirected edge carry the same weight; repeated arcs get the same weight.
+ */
+void gg_arc_weights(const int32_t* row_ptr, const int32_t* col_idx, int32_t n, int32_t lo, int32_t hi,
+                    uint64_t seed, int symmetric, int32_t* out) {
+    const uint64_t span = (uint64_t)((int64_t)hi - (int64_t)lo + 1);
+    for (int32_t u = 0; u < n; ++u) {
+        for (int32_t j = row_ptr[u]; j < row_ptr[u + 1]; ++j) {
+            uint32_t a = (uint32_t)u, b = (uint32_t)col_idx[j];
+            if (symmetric && b < a) { uint32_t t = a; a = b; b = t; }
+            uint64_t x = seed ^ (((uint64_t)a << 32) | (uint64_t)b);
+            out[j] = (int32_t)((int64_t)lo + (int64_t)(splitmix64_next(&x) % span));
+        }
+    }
+}
+
 int32_t gg_n(const gg_csr* g) { return g->n; }
 int64_t gg_m(const gg_csr* g) { return g->m; }
 

@@ -39,6 +39,14 @@ MUTANTS = {
     "radius_counts_isolated": ("if (r > 1 && (small < 0 || e < small)) small = e;", "if (small < 0 || e < small) small = e;"),
     "parents_largest_id": ("(parent[v] < 0 || u < parent[v])) parent[v] = u;", "(parent[v] < 0 || u > parent[v])) parent[v] = u;"),
     "parents_same_level_too": ("if (dist[v] == dist[u] + 1 && (parent[v] < 0", "if (dist[v] >= dist[u] && dist[v] > 0 && (parent[v] < 0"),
+    "minplus_ignores_weight": ("const int64_t nd = dprev[i] + (int64_t)w[j];", "const int64_t nd = dprev[i] + 1;"),
+    "minplus_current_values": ("const int64_t nd = dprev[i] + (int64_t)w[j];", "const int64_t nd = d[i] + (int64_t)w[j];"),
+    "minplus_nonstrict": ("if (nd < d[c]) {\n                    d[c] = nd;", "if (nd <= d[c]) {\n                    d[c] = nd;"),
+    "dijkstra_drops_key": ("const int64_t nd = it.key + (int64_t)w[j];", "const int64_t nd = (int64_t)w[j];"),
+    "wcert_no_tight_search": ("if (dist[v] >= 0 && !seen[v]) { *bad = v; ok = 0; }",
+                              "if (0 && dist[v] >= 0 && !seen[v]) { *bad = v; ok = 0; }"),
+    "wcert_loose_bound": ("if (dist[v] < 0 || dist[v] > dist[u] + (int64_t)w[j]) { *bad = v; return 0; }",
+                          "if (dist[v] < 0 || dist[v] > dist[u] + (int64_t)w[j] + 1) { *bad = v; return 0; }"),
 }
 
 

@@ -16,7 +16,7 @@ Run against a mutant (``DAWN_ORACLE_SO``) by ``test_oracle_mutants.py``.
 import numpy as np
 import pytest
 import scipy.sparse as sp
-from scipy.sparse.csgraph import connected_components, shortest_path
+from scipy.sparse.csgraph import connected_components, csgraph_from_dense, shortest_path
 
 import oracle
 from paper_2208_04514_b300 import graphgen as gg
@@ -480,3 +480,191 @@ def test_centrality_vs_scipy(seed):
     assert c["summary"]["radius"] == (ecc[reaching].min() if reaching.any() else -1)
     assert c["summary"]["pairs"] == fin.sum()
     assert c["summary"]["dist_total"] == int(d[fin].sum())
+
+
+# ---------------------------------------- weighted (min, +) extension pins --
+
+def weighted_from_arcs(n, arcs):
+    """CSR + aligned weights from (u, v, w) triples (self-loops and repeats kept)."""
+    arcs = sorted(arcs)
+    g = gg.from_arcs(n, [a for a, _, _ in arcs], [b for _, b, _ in arcs])
+    return g, np.array([c for _, _, c in arcs], dtype=np.int32)
+
+
+def random_weighted(seed, n=None, wmax=None):
+    g = random_digraph(seed, n=n)
+    rng = np.random.default_rng(10_000 + seed)
+    wmax = wmax if wmax is not None else int(rng.choice([0, 1, 3, 20, 1000]))
+    return g, rng.integers(0, wmax + 1, g.m).astype(np.int32)
+
+
+def scipy_wdist(g, w, src):
+    """scipy's Dijkstra (a library routine).  Repeated arcs keep their smallest
+    weight; the graph goes through a dense matrix with inf for 'no arc', so
+    that zero-weight arcs stay arcs (csgraph_from_dense with null_value=inf)."""
+    n = g.n
+    dense = np.full((n, n), np.inf)
+    src_of = np.repeat(np.arange(n), g.out_degree())
+    for u, v, c in zip(src_of, g.col_idx, w):
+        if c < dense[u, v]:
+            dense[u, v] = c
+    cg = csgraph_from_dense(dense, null_value=np.inf)
+    d = shortest_path(cg, method="D", directed=True, indices=[src])[0]
+    return np.where(np.isinf(d), -1, d).astype(np.int64)
+
+
+def floyd_weighted(g, w):
+    n = g.n
+    d = np.full((n, n), np.inf)
+    np.fill_diagonal(d, 0)
+    src_of = np.repeat(np.arange(n), g.out_degree())
+    for u, v, c in zip(src_of, g.col_idx, w):
+        d[u, v] = min(d[u, v], c) if u != v else 0
+    for k in range(n):
+        d = np.minimum(d, d[:, [k]] + d[[k], :])
+    return np.where(np.isinf(d), -1, d).astype(np.int64)
+
+
+@pytest.mark.parametrize("seed", RNG_SEEDS)
+def test_weighted_vs_scipy_and_floyd(seed):
+    g, w = random_weighted(2000 + seed)
+    fw = floyd_weighted(g, w)
+    for src in range(0, g.n, max(1, g.n // 5)):
+        want = scipy_wdist(g, w, src)
+        np.testing.assert_array_equal(fw[src], want)
+        np.testing.assert_array_equal(oracle.wsssp_minplus(g.row_ptr, g.col_idx, w, src), want)
+        np.testing.assert_array_equal(oracle.dijkstra(g.row_ptr, g.col_idx, w, src), want)
+
+
+def tight_hops(g, w, src, dist):
+    """Fewest arcs on a shortest path to each reached vertex: BFS over the arcs
+    u -> v with dist[u] + w = dist[v] (numpy / Python, independent of the oracle)."""
+    n = g.n
+    hops = np.full(n, -1)
+    hops[src] = 0
+    frontier = [src]
+    while frontier:
+        nxt = []
+        for u in frontier:
+            for j in range(g.row_ptr[u], g.row_ptr[u + 1]):
+                v = int(g.col_idx[j])
+                if hops[v] < 0 and dist[v] == dist[u] + int(w[j]):
+                    hops[v] = hops[u] + 1
+                    nxt.append(v)
+        frontier = nxt
+    return hops
+
+
+@pytest.mark.parametrize("seed", range(16))
+def test_weighted_rounds_are_shortest_path_hops(seed):
+    """Round k of the (min, +) iteration holds the least weight over walks of at
+    most k arcs, so the rounds that change something number the largest, over
+    reached vertices, of the fewest arcs on a shortest path."""
+    g, w = random_weighted(2100 + seed)
+    for src in range(0, g.n, max(1, g.n // 3)):
+        d, rounds, _ = oracle.wsssp_minplus(g.row_ptr, g.col_idx, w, src, with_stats=True)
+        assert rounds == int(tight_hops(g, w, src, d).max())
+
+
+def test_weighted_closed_forms():
+    # weighted directed path: prefix sums
+    n = 7
+    wts = [3, 0, 5, 1, 1, 9]
+    g, w = weighted_from_arcs(n, [(i, i + 1, wts[i]) for i in range(n - 1)])
+    want = np.concatenate([[0], np.cumsum(wts)])
+    np.testing.assert_array_equal(oracle.wsssp_minplus(g.row_ptr, g.col_idx, w, 0), want)
+    np.testing.assert_array_equal(oracle.wsssp_minplus(g.row_ptr, g.col_idx, w, 3),
+                                  [-1, -1, -1, 0, 1, 2, 11])
+    # directed cycle with unit weights: (v - s) mod n
+    c, wc = weighted_from_arcs(9, [(i, (i + 1) % 9, 1) for i in range(9)])
+    np.testing.assert_array_equal(oracle.wsssp_minplus(c.row_ptr, c.col_idx, wc, 4), (np.arange(9) - 4) % 9)
+    # a shortcut of weight 10 against a 4-arc path of weight 4: the path wins
+    s, ws = weighted_from_arcs(5, [(0, 4, 10), (0, 1, 1), (1, 2, 1), (2, 3, 1), (3, 4, 1)])
+    assert oracle.wsssp_minplus(s.row_ptr, s.col_idx, ws, 0)[4] == 4
+    # all-zero weights: 0 on every reached vertex
+    g2 = random_digraph(77, n=30, p=0.1)
+    z = np.zeros(g2.m, dtype=np.int32)
+    bfs = oracle.sssp_sovm(g2.row_ptr, g2.col_idx, 0)
+    np.testing.assert_array_equal(oracle.wsssp_minplus(g2.row_ptr, g2.col_idx, z, 0), np.where(bfs >= 0, 0, -1))
+    # n = 1, with and without a self-loop
+    one, w1 = weighted_from_arcs(1, [(0, 0, 5)])
+    np.testing.assert_array_equal(oracle.wsssp_minplus(one.row_ptr, one.col_idx, w1, 0), [0])
+    # the largest weights: distances past int32
+    big, wb = weighted_from_arcs(4, [(0, 1, 2**31 - 1), (1, 2, 2**31 - 1), (2, 3, 2**31 - 1)])
+    assert oracle.wsssp_minplus(big.row_ptr, big.col_idx, wb, 0)[3] == 3 * (2**31 - 1)
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_unit_weights_reduce_to_bfs(seed):
+    g = random_digraph(2200 + seed)
+    ones = np.ones(g.m, dtype=np.int32)
+    for src in range(0, g.n, max(1, g.n // 4)):
+        bfs = oracle.sssp_sovm(g.row_ptr, g.col_idx, src)
+        np.testing.assert_array_equal(oracle.wsssp_minplus(g.row_ptr, g.col_idx, ones, src), bfs)
+
+
+def test_weighted_golden_fixture():
+    from pathlib import Path
+    path = Path(__file__).parent / "golden" / "hand_weighted_6.txt"
+    n, arcs, cases = None, [], []
+    for line in path.read_text().splitlines():
+        line = line.split("#", 1)[0].strip()
+        if not line:
+            continue
+        key, _, rest = line.partition(":")
+        vals = [int(x) for x in rest.split()]
+        if key == "n":
+            n = vals[0]
+        elif key == "warc":
+            arcs.append(tuple(vals))
+        elif key.startswith("wdist"):
+            cases.append((int(key.split()[1]), np.array(vals)))
+    g, w = weighted_from_arcs(n, arcs)
+    assert cases
+    for src, want in cases:
+        np.testing.assert_array_equal(oracle.wsssp_minplus(g.row_ptr, g.col_idx, w, src), want)
+        np.testing.assert_array_equal(oracle.dijkstra(g.row_ptr, g.col_idx, w, src), want)
+        assert oracle.wcertificate(g.row_ptr, g.col_idx, w, src, want) == (1, -1)
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_wcertificate_accepts_exact_rejects_planted(seed):
+    g, w = random_weighted(2300 + seed, wmax=5)
+    src = 0
+    d = scipy_wdist(g, w, src)
+    assert oracle.wcertificate(g.row_ptr, g.col_idx, w, src, d) == (1, -1)
+    reached = np.nonzero(d > 0)[0]
+    for v in reached[:6]:
+        for delta in (-1, +1):
+            bad = d.copy()
+            bad[v] += delta
+            assert oracle.wcertificate(g.row_ptr, g.col_idx, w, src, bad)[0] == 0
+    unreached = np.nonzero(d < 0)[0]
+    if unreached.size:
+        bad = d.copy()
+        bad[unreached[0]] = 5
+        assert oracle.wcertificate(g.row_ptr, g.col_idx, w, src, bad)[0] == 0
+
+
+def test_wcertificate_rejects_zero_weight_mutual_support():
+    """Vertices 2 and 3 are unreachable from 0 but support each other through
+    zero-weight arcs; only the search over tight arcs from the source sees it."""
+    g, w = weighted_from_arcs(4, [(0, 1, 1), (2, 3, 0), (3, 2, 0)])
+    exact = np.array([0, 1, -1, -1])
+    assert oracle.wcertificate(g.row_ptr, g.col_idx, w, 0, exact) == (1, -1)
+    fake = np.array([0, 1, 5, 5])
+    assert oracle.wcertificate(g.row_ptr, g.col_idx, w, 0, fake)[0] == 0
+
+
+def test_weighted_rejects_negative_weights():
+    g, w = weighted_from_arcs(3, [(0, 1, 1), (1, 2, -1)])
+    with pytest.raises(ValueError):
+        oracle.wsssp_minplus(g.row_ptr, g.col_idx, w, 0)
+
+
+def test_wcertificate_rejects_tight_but_too_long():
+    """d(2) is 2 through 1, but a claim of 3 is tight through 3 (d(3) = 2, w = 1):
+    only the arc bound on 1 -> 2 rejects it."""
+    g, w = weighted_from_arcs(4, [(0, 1, 1), (1, 2, 1), (0, 3, 2), (3, 2, 1)])
+    assert oracle.wcertificate(g.row_ptr, g.col_idx, w, 0, np.array([0, 1, 2, 2])) == (1, -1)
+    assert oracle.wcertificate(g.row_ptr, g.col_idx, w, 0, np.array([0, 1, 3, 2]))[0] == 0
