@@ -219,6 +219,50 @@ DAWN_API int dawn_sssp_many(dawn_graph_t g, const int32_t* sources, int32_t k, i
  */
 DAWN_API int dawn_l2_read_gbs(int64_t bytes, int32_t passes, double* gbs, void* stream);
 
+/*
+ * Weighted extension.  Sec. 5 names (min, +) operations on weighted graphs as
+ * the way DAWN is to be extended; these calls run the SOVM rounds of Alg. 3
+ * with (min, +) in place of (OR, AND).
+ *
+ * Attach arc weights to g: weights[j] belongs to arc j of the col_idx array
+ * given to dawn_graph_upload (same order).
+ *   weights  host or device, int32[m], every entry >= 0; DAWN_E_INVALID with
+ *            the first negative index in dawn_last_error otherwise (g then
+ *            has no weights until a valid set is given).
+ * Replaces earlier weights.  The first call allocates the weighted path's
+ * buffers (4m + 28n bytes); dawn_graph_free releases them.  Synchronizes
+ * `stream`.
+ */
+DAWN_API int dawn_graph_set_weights(dawn_graph_t g, const int32_t* weights, void* stream);
+
+typedef struct {
+    int32_t rounds;        /* rounds that lowered some distance (at most n - 1) */
+    int32_t reserved;
+    int64_t reached;       /* vertices with dist >= 0 (src included) */
+    int64_t relaxations;   /* arcs offered a distance: the out-degrees of every frontier, summed */
+    int64_t improvements;  /* offers that lowered a distance */
+} dawn_wsssp_stats;
+
+/*
+ * Weighted single-source shortest paths: dist[v] = the least total weight of
+ * a directed path src -> v, -1 when there is none, 0 at src.  Round r offers
+ * d(u) + w(u, v) from every vertex u whose distance fell in round r - 1 to
+ * each out-neighbour v (an atomic minimum); the vertices whose distance fell
+ * form the next frontier; the loop stops on a round that lowers nothing.
+ * The result is unique; the rounds and counts can vary from run to run
+ * (values lowered during a round are offered at once).
+ *   src    0 <= src < n.
+ *   dist   host or device, int64[n], written in full.
+ *   stats  host or device, or NULL.
+ * DAWN_E_INVALID when g has no weights.  Synchronous.
+ */
+DAWN_API int dawn_wsssp(dawn_graph_t g, int32_t src, int64_t* dist, dawn_wsssp_stats* stats, void* stream);
+
+/* Stream-ordered dawn_wsssp: dist_dev device int64[n], stats_dev device or
+ * NULL; a device-side failure is reported by dawn_graph_sync. */
+DAWN_API int dawn_wsssp_async(dawn_graph_t g, int32_t src, int64_t* dist_dev, dawn_wsssp_stats* stats_dev,
+                              void* stream);
+
 /* Synchronize `stream` and return (then clear) the sticky device status of g:
  * DAWN_OK, DAWN_E_TIMEOUT or DAWN_E_OVERFLOW. */
 DAWN_API int dawn_graph_sync(dawn_graph_t g, void* stream);

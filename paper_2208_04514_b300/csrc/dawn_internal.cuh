@@ -124,6 +124,7 @@ struct dawn_graph {
     size_t ms_counts_cap = 0;
     int ms_blocks_per_sm = 0;
     unsigned ms_launches = 0;         // picks the barrier counter of the next batched launch
+    void* weighted = nullptr;         // weights and work buffers of the (min, +) path (weighted.cu)
 };
 
 namespace dawn {
@@ -135,6 +136,10 @@ int sssp_occupancy(dawn_graph* g);
 int graph_sync_status(dawn_graph* g, cudaStream_t stream);
 // many.cu: release the captured graph of dawn_sssp_many
 void many_release(dawn_graph* g);
+// weighted.cu: release the weighted path's buffers; zero its control block
+// after a failed launch (graph_sync_status)
+void weighted_release(dawn_graph* g);
+int weighted_reset(dawn_graph* g, cudaStream_t st);
 // cluster.cu: one source on a single thread-block cluster; DAWN_E_INVALID when unavailable
 int cluster_launch(dawn_graph* g, int32_t src, int32_t* dist_dev, const dawn_sssp_opts* opts,
                    dawn_sssp_stats* stats_dev, cudaStream_t st);

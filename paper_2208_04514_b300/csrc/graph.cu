@@ -275,6 +275,7 @@ void release(dawn_graph* g) {
     f(g->cl_ovf);
     f(g->cl_ovf_n);
     many_release(g);
+    weighted_release(g);
     f(g->ctl);
     f(g->stats_dev);
     f(g->ms_vis[0]);
@@ -446,6 +447,7 @@ int graph_sync_status(dawn_graph* g, cudaStream_t st) {
     if (s == DEV_OK) return DAWN_OK;
     // clear the sticky word and the barrier state a timed-out launch left behind
     DAWN_CUDA_TRY(cudaMemsetAsync(g->ctl, 0, sizeof(Ctl), st));
+    if (weighted_reset(g, st) != DAWN_OK) return DAWN_E_CUDA;
     DAWN_CUDA_TRY(cudaStreamSynchronize(st));
     if (s == DEV_TIMEOUT) return fail(DAWN_E_TIMEOUT, "a grid-barrier wait on the device ran out of its spin budget");
     if (s == DEV_OVERFLOW) return fail(DAWN_E_OVERFLOW, "a distance exceeded the int16 range (32767)");

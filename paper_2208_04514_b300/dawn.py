@@ -86,6 +86,14 @@ class dawn_msbfs_opts(ctypes.Structure):
                 ("trace", ctypes.c_void_p)]
 
 
+class dawn_wsssp_stats(ctypes.Structure):
+    _fields_ = [("rounds", ctypes.c_int32), ("reserved", ctypes.c_int32), ("reached", ctypes.c_int64),
+                ("relaxations", ctypes.c_int64), ("improvements", ctypes.c_int64)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+
+
 class dawn_apsp_summary(ctypes.Structure):
     _fields_ = [("diameter", ctypes.c_int32), ("radius", ctypes.c_int32), ("pairs", ctypes.c_int64),
                 ("dist_total", ctypes.c_int64)]
@@ -120,6 +128,9 @@ _SIGNATURES = {
     "dawn_serve_drain": [_vp, _i64],
     "dawn_serve_destroy": [_vp],
     "dawn_l2_read_gbs": [_i64, _i32, _vp, _vp],
+    "dawn_graph_set_weights": [_vp, _vp, _vp],
+    "dawn_wsssp": [_vp, _i32, _vp, _vp, _vp],
+    "dawn_wsssp_async": [_vp, _i32, _vp, _vp, _vp],
     "dawn_last_error": [],
     "dawn_version": [],
 }
@@ -238,6 +249,23 @@ def dawn_sssp_many(g: int, sources, k: int | None = None, dist=None, stats=None,
     o = _opts(opts, dawn_sssp_opts)
     _check(load().dawn_sssp_many(g, _ptr(sources), k, _ptr(dist), _ptr(stats), ctypes.byref(o) if o else None,
                                  _stream(stream)))
+
+
+def dawn_graph_set_weights(g: int, weights, stream=None) -> None:
+    """Attach non-negative int32 arc weights (aligned with the uploaded col_idx)."""
+    _check(load().dawn_graph_set_weights(g, _ptr(weights), _stream(stream)))
+
+
+def dawn_wsssp(g: int, src: int, dist, stream=None) -> dict:
+    """Weighted SSSP ((min, +) rounds) into int64 dist; returns the call's statistics."""
+    st = dawn_wsssp_stats()
+    _check(load().dawn_wsssp(g, int(src), _ptr(dist), ctypes.byref(st), _stream(stream)))
+    return st.as_dict()
+
+
+def dawn_wsssp_async(g: int, src: int, dist_dev, stats_dev=None, stream=None) -> None:
+    """Stream-ordered dawn_wsssp (device int64 dist, device stats or None)."""
+    _check(load().dawn_wsssp_async(g, int(src), _ptr(dist_dev), _ptr(stats_dev), _stream(stream)))
 
 
 def dawn_sssp_tree(g: int, src: int, dist, parent, stream=None) -> None:
