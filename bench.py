@@ -352,6 +352,68 @@ def bench_tree(dawn, torch, flush, g, srcs, peak):
             "tie_break": "smallest-id predecessor", "early_stop": "rows in ascending order"}
 
 
+def bench_weighted(dawn, torch, flush, g, srcs, peak, nsrc=16, cpu_sources=2):
+    """Weighted extension ((min, +) rounds of Alg. 3) on the headline graph with
+    seeded integer arc weights uniform on [1, 255] (symmetric per edge), the
+    first nsrc headline sources, L2 flushed between sources.  GTEPS counts the
+    arcs of the reached vertices (E_r), as the unweighted figure does; the
+    rounds offer more arcs than that (a vertex is offered again each time its
+    distance falls), so relaxations are reported beside it.  Algorithmic
+    bytes: 16 per offered arc (col_idx, weight, the head's 8-byte distance)
+    + 16 per lowering (the 8-byte write and the head's row bounds) + 8 n (the
+    distance vector); roofline fraction against the measured copy bandwidth.
+    CPU baseline: the oracle's textbook Dijkstra (single-threaded) on the
+    first cpu_sources sources."""
+    from paper_2208_04514_b300 import graphgen as gg
+    import oracle
+    stream = torch.cuda.current_stream()
+    w = gg.arc_weights(g, 1, 255, seed=7)
+    srcs = [int(s) for s in srcs[:nsrc]]
+    h = dawn.dawn_graph_upload(g.row_ptr, g.col_idx, flags=dawn.DAWN_SYMMETRIC, stream=stream)
+    dawn.dawn_graph_set_weights(h, w, stream)
+    dist = torch.empty((len(srcs), g.n), dtype=torch.int64, device="cuda")
+    stats = torch.zeros((len(srcs), dawn.WSTATS_WORDS), dtype=torch.int64, device="cuda")
+    for rep in range(2):  # the second pass is the measured one
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in srcs]
+        for i, s in enumerate(srcs):
+            _flush(flush, i)
+            ev[i][0].record(stream)
+            dawn.dawn_wsssp_async(h, s, dist[i], stats[i], stream)
+            ev[i][1].record(stream)
+        dawn.dawn_graph_sync(h, stream)
+    us = [a.elapsed_time(b) * 1e3 for a, b in ev]
+    st = [dawn.wstats_from_words(r) for r in stats.cpu().numpy()]
+    d_host = dist.cpu().numpy()
+    dawn.dawn_graph_free(h)
+    deg = g.out_degree()
+    e_r = [int(deg[d_host[i] >= 0].sum()) for i in range(len(srcs))]
+    gteps = [e / (t * 1e-6) / 1e9 for e, t in zip(e_r, us)]
+    balg = [16 * x["relaxations"] + 16 * x["improvements"] + 8 * g.n for x in st]
+    achieved = [b / (t * 1e-6) / 1e9 for b, t in zip(balg, us)]
+    t0 = time.perf_counter()
+    ok = True
+    for i, s in enumerate(srcs[:cpu_sources]):
+        ref = oracle.dijkstra(g.row_ptr, g.col_idx, w, s)
+        ok = ok and bool((ref == d_host[i]).all())
+    t_cpu = (time.perf_counter() - t0) / max(1, min(cpu_sources, len(srcs)))
+    return {"workload": f"rmat20_weighted_1to255_{len(srcs)}src",
+            "weights": "int32 uniform on [1, 255] from a hash of the endpoint pair (seed 7), same on both arcs of an edge",
+            "us_per_source_median": statistics.median(us), "us_per_source_mean": statistics.fmean(us),
+            "gteps_median": statistics.median(gteps),
+            "gteps_harmonic_mean": len(gteps) / sum(1.0 / x for x in gteps),
+            "rounds_median": statistics.median(x["rounds"] for x in st),
+            "relaxations_per_source_median": statistics.median(x["relaxations"] for x in st),
+            "relaxations_over_e_r": statistics.median(x["relaxations"] / e for x, e in zip(st, e_r)),
+            "roofline": {"bound": "hbm", "achieved_median": statistics.median(achieved), "peak": peak,
+                         "unit": "GB/s", "frac": statistics.median(achieved) / peak,
+                         "bytes_alg_per_source_median": statistics.median(balg),
+                         "kernel": "wsssp_kernel"},
+            "bit_exact_vs_oracle_dijkstra": ok,
+            "cpu_baseline": {"us_per_source": t_cpu * 1e6, "kind": "oracle", "cores": 1,
+                             "sample": f"first {min(cpu_sources, len(srcs))} sources, textbook Dijkstra single-threaded"},
+            "l2": "flushed between sources"}
+
+
 def bench_batched(dawn, torch, flush, plain_sample=4096, k=0, lanes_list=(64, 128, 256)):
     """RMAT scale 16 (seed 4), all 65,536 vertices as sources, int16 distance
     block of each pass kept on the device and reduced to eccentricity and
@@ -748,6 +810,7 @@ def run_gpu(args):
         line["secondary"] = {"lattice": bench_lattice(dawn, torch, flush),
                              "batched": bench_batched(dawn, torch, flush),
                              "tree": bench_tree(dawn, torch, flush, g, srcs, peak),
+                             "weighted": bench_weighted(dawn, torch, flush, g, srcs, peak),
                              "centrality": bench_centrality(dawn, torch, flush),
                              "modes": bench_modes(dawn, torch, flush, g, srcs),
                              "many_graph": bench_many_graph(dawn, torch, g, srcs)}
@@ -781,6 +844,9 @@ def run_one(args):
     elif args.workload == "tree":
         g, srcs = build_workload()
         out = bench_tree(dawn, torch, flush, g, srcs, measured_peaks()[0])
+    elif args.workload == "weighted":
+        g, srcs = build_workload()
+        out = bench_weighted(dawn, torch, flush, g, srcs, measured_peaks()[0])
     elif args.workload == "batched":
         out = bench_batched(dawn, torch, flush, k=args.batched_k, lanes_list=(args.batched_lanes,) if args.batched_lanes else (64, 128, 256))
     else:
@@ -803,7 +869,7 @@ def main():
                     help="use only the first N of the 64 sources (small profiling runs; not a bench value)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end host-buffer pass")
     ap.add_argument("--serve-requests", type=int, default=48, help="requests per arrival rate in the serving mix")
-    ap.add_argument("--workload", choices=["all", "lattice", "batched", "serving", "tree", "centrality", "modes", "many"], default="all",
+    ap.add_argument("--workload", choices=["all", "lattice", "batched", "serving", "tree", "centrality", "modes", "many", "weighted"], default="all",
                     help="run one secondary workload alone and print its figures (profiling runs; not a bench line)")
     ap.add_argument("--batched-k", type=int, default=0, help="with --workload batched: sources (0 = all)")
     ap.add_argument("--lattice-side", type=int, default=4096, help="with --workload lattice: side of the lattice")

@@ -295,6 +295,13 @@ def dawn_sssp_noalloc(row_ptr_dev, col_idx_dev, src: int, dist_dev, n: int | Non
 
 
 STATS_WORDS = ctypes.sizeof(dawn_sssp_stats) // 8  # int64 words per stats record
+WSTATS_WORDS = ctypes.sizeof(dawn_wsssp_stats) // 8  # int64 words per weighted stats record
+
+
+def wstats_from_words(words) -> dict:
+    """dawn_wsssp_stats from WSTATS_WORDS int64 words (a device stats row copied back)."""
+    raw = np.ascontiguousarray(words, dtype=np.int64).tobytes()
+    return dawn_wsssp_stats.from_buffer_copy(raw).as_dict()
 
 
 def stats_from_words(words) -> dict:
