@@ -143,27 +143,6 @@ __device__ __forceinline__ int w_scan(int x, int lane) {
     return x;
 }
 
-// Queue vertex v (lanes with `q`) for the next round: one record per vertex
-// with a non-empty row, one 64-bit reservation per warp (records in the high
-// word, arcs in the low word, so offsets grow with the slot).  Full warp.
-__device__ __forceinline__ void w_enqueue(bool q, int v, int rb, int re, int lane, int32_t* qv, int2* qe,
-                                          int32_t* qo, WSlot* out) {
-    const int deg = q ? re - rb : 0;
-    const unsigned rows = __ballot_sync(kWFull, deg > 0);
-    if (!rows) return;
-    const int dincl = w_scan(deg, lane);
-    const int dtot = __shfl_sync(kWFull, dincl, 31);
-    unsigned long long base = 0;
-    if (lane == 0) base = atomicAdd(&out->qpack, ((unsigned long long)__popc(rows) << 32) | (unsigned)dtot);
-    base = __shfl_sync(kWFull, base, 0);
-    if (deg > 0) {
-        const int pos = (int)(base >> 32) + __popc(rows & ((1u << lane) - 1u));
-        qv[pos] = v;
-        qe[pos] = make_int2(rb, deg);
-        qo[pos] = (int)(base & 0xffffffffu) + dincl - deg;
-    }
-}
-
 // Sum the per-thread counts over the CTA and add them to the round's slot.
 __device__ __forceinline__ void w_flush(long long lowered, long long reached, WSlot* out) {
     __shared__ long long s_a[kWWarps], s_b[kWWarps];
@@ -189,7 +168,52 @@ __device__ __forceinline__ void w_flush(long long lowered, long long reached, WS
     }
 }
 
-// One (min, +) round over the frontier of round r (qn records, E arcs).
+// Queue up to kWGroup vertices per lane (lanes' `q` bits) for the next round:
+// one record per vertex with a non-empty row, one 64-bit reservation per
+// warp (records in the high word, arcs in the low word, so offsets grow with
+// the slot).  Full warp.
+constexpr int kWGroup = 4;
+
+__device__ __forceinline__ void w_enqueue_group(unsigned q, const int* v, const int* rb, const int* re, int lane,
+                                                int32_t* qv, int2* qe, int32_t* qo, WSlot* out) {
+    int cnt = 0, deg = 0;
+#pragma unroll
+    for (int i = 0; i < kWGroup; ++i) {
+        if ((q >> i) & 1u) {
+            const int d = re[i] - rb[i];
+            cnt += d > 0;
+            deg += d;
+        }
+    }
+    const int cincl = w_scan(cnt, lane);
+    const int ctot = __shfl_sync(kWFull, cincl, 31);
+    if (ctot == 0) return;
+    const int dincl = w_scan(deg, lane);
+    const int dtot = __shfl_sync(kWFull, dincl, 31);
+    unsigned long long base = 0;
+    if (lane == 31) base = atomicAdd(&out->qpack, ((unsigned long long)ctot << 32) | (unsigned)dtot);
+    base = __shfl_sync(kWFull, base, 31);
+    int pos = (int)(base >> 32) + cincl - cnt;
+    int aoff = (int)(base & 0xffffffffu) + dincl - deg;
+#pragma unroll
+    for (int i = 0; i < kWGroup; ++i) {
+        if (!((q >> i) & 1u)) continue;
+        const int d = re[i] - rb[i];
+        if (d <= 0) continue;
+        qv[pos] = v[i];
+        qe[pos] = make_int2(rb[i], d);
+        qo[pos] = aoff;
+        ++pos;
+        aoff += d;
+    }
+}
+
+// One (min, +) round over the frontier of round r (qn records, E arcs).  A
+// warp walks its arc range in groups of kWGroup windows of 32 consecutive
+// arcs; within a group the loads of every step (arcs and weights, the heads'
+// distances, the atomic minimums, the marks, the heads' rows) are issued for
+// all windows together, so the warp waits for one chain of round trips per
+// group, not per window.
 __device__ void relax_round(const WArgs& a, int r, int qn, long long E, WSlot* out, long long& lowered,
                             long long& reached) {
     const int lane = threadIdx.x & 31;
@@ -236,52 +260,81 @@ __device__ void relax_round(const WArgs& a, int r, int qn, long long E, WSlot* o
     int32_t* nqv = a.qv[(r + 1) & 1];
     int2* nqe = a.qe[(r + 1) & 1];
     int32_t* nqo = a.qo[(r + 1) & 1];
-    for (long long wb = a0; wb < a1; wb += 32) {
-        // keep the batch covering the window [wb, min(wb + 31, a1 - 1)]: if
-        // its last arc lies past the batch's last record, restart the batch
-        // at the record holding wb
-        const long long last = min(wb + 31, a1 - 1);
-        const int off31 = __shfl_sync(kWFull, off, 31);
-        const int len31 = __shfl_sync(kWFull, e.y, 31);
-        if (bstart + 32 < qn && last >= (long long)off31 + len31) {
-            int k;
-            if (wb >= (long long)off31 + len31) k = 32;
-            else k = 31 - __clz(__ballot_sync(kWFull, (long long)off <= wb));
-            bstart += k;
-            load(bstart);
-        }
-        const long long t = wb + lane;
-        int o = 0;
+    for (long long gb = a0; gb < a1; gb += 32 * kWGroup) {
+        int j[kWGroup];
+        unsigned long long odu[kWGroup];
 #pragma unroll
-        for (int b = 16; b > 0; b >>= 1) {
-            const int pv = __shfl_sync(kWFull, off, o + b);
-            if ((long long)pv <= t) o += b;
+        for (int q = 0; q < kWGroup; ++q) {
+            const long long wb = gb + 32 * q;
+            j[q] = -1;
+            odu[q] = 0;
+            if (wb >= a1) continue;  // warp-uniform
+            // keep the batch covering the window [wb, min(wb + 31, a1 - 1)]:
+            // if its last arc lies past the batch's last record, restart the
+            // batch at the record holding wb
+            const long long last = min(wb + 31, a1 - 1);
+            const int off31 = __shfl_sync(kWFull, off, 31);
+            const int len31 = __shfl_sync(kWFull, e.y, 31);
+            if (bstart + 32 < qn && last >= (long long)off31 + len31) {
+                int k;
+                if (wb >= (long long)off31 + len31) k = 32;
+                else k = 31 - __clz(__ballot_sync(kWFull, (long long)off <= wb));
+                bstart += k;
+                load(bstart);
+            }
+            const long long t = wb + lane;
+            int o = 0;
+#pragma unroll
+            for (int b = 16; b > 0; b >>= 1) {
+                const int pv = __shfl_sync(kWFull, off, o + b);
+                if ((long long)pv <= t) o += b;
+            }
+            const int ost = __shfl_sync(kWFull, e.x, o);
+            const int ooff = __shfl_sync(kWFull, off, o);
+            odu[q] = __shfl_sync(kWFull, du, o);
+            if (t < a1) j[q] = ost + (int)(t - ooff);
         }
-        const int ost = __shfl_sync(kWFull, e.x, o);
-        const int ooff = __shfl_sync(kWFull, off, o);
-        const unsigned long long odu = __shfl_sync(kWFull, du, o);
-        bool q = false;
-        int c = 0, rb = 0, re = 0;
-        if (t < a1) {
-            const int j = ost + (int)(t - ooff);
-            c = __ldg(a.col_idx + j);
-            const unsigned long long nd = odu + (unsigned long long)(unsigned)__ldg(a.w + j);
-            if (nd < __ldcg(a.dist + c)) {
-                const unsigned long long old = atomicMin(a.dist + c, nd);
-                if (nd < old) {
+        int c[kWGroup];
+        unsigned long long nd[kWGroup];
+#pragma unroll
+        for (int q = 0; q < kWGroup; ++q) {
+            c[q] = j[q] >= 0 ? __ldg(a.col_idx + j[q]) : 0;
+            nd[q] = j[q] >= 0 ? odu[q] + (unsigned long long)(unsigned)__ldg(a.w + j[q]) : kNoPath;
+        }
+        unsigned long long cur[kWGroup];
+#pragma unroll
+        for (int q = 0; q < kWGroup; ++q) cur[q] = j[q] >= 0 ? __ldcg(a.dist + c[q]) : 0ull;
+        unsigned fell = 0;
+#pragma unroll
+        for (int q = 0; q < kWGroup; ++q) {
+            if (j[q] >= 0 && nd[q] < cur[q]) {
+                const unsigned long long old = atomicMin(a.dist + c[q], nd[q]);
+                if (nd[q] < old) {
+                    fell |= 1u << q;
                     lowered += 1;
                     reached += old == kNoPath;
-                    // queued once per round: the first lowering this round sets the mark
-                    const uint32_t bit = 1u << (c & 31);
-                    q = !(atomicOr(mark + (c >> 5), bit) & bit);
                 }
             }
         }
-        if (q) {
-            rb = __ldg(a.row_ptr + c);
-            re = __ldg(a.row_ptr + c + 1);
+        // queued once per round: the first lowering this round sets the mark
+        unsigned qd = 0;
+#pragma unroll
+        for (int q = 0; q < kWGroup; ++q) {
+            if ((fell >> q) & 1u) {
+                const uint32_t bit = 1u << (c[q] & 31);
+                if (!(atomicOr(mark + (c[q] >> 5), bit) & bit)) qd |= 1u << q;
+            }
         }
-        w_enqueue(q, c, rb, re, lane, nqv, nqe, nqo, out);
+        int rb[kWGroup], re[kWGroup];
+#pragma unroll
+        for (int q = 0; q < kWGroup; ++q) {
+            rb[q] = re[q] = 0;
+            if ((qd >> q) & 1u) {
+                rb[q] = __ldg(a.row_ptr + c[q]);
+                re[q] = __ldg(a.row_ptr + c[q] + 1);
+            }
+        }
+        w_enqueue_group(qd, c, rb, re, lane, nqv, nqe, nqo, out);
     }
 }
 
