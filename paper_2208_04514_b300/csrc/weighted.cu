@@ -304,41 +304,45 @@ __device__ void relax_round(const WArgs& a, int r, int qn, long long E, WSlot* o
         unsigned long long cur[kWGroup];
 #pragma unroll
         for (int q = 0; q < kWGroup; ++q) cur[q] = j[q] >= 0 ? __ldcg(a.dist + c[q]) : 0ull;
-        unsigned fell = 0;
+        // an offer below the head's current distance: the head's distance
+        // falls this round (to this offer or to a smaller one), so the head
+        // belongs to the next frontier whatever the atomic minimum returns;
+        // the minimum, the mark and the head's row are issued together
+        unsigned offer = 0;
 #pragma unroll
-        for (int q = 0; q < kWGroup; ++q) {
-            if (j[q] >= 0 && nd[q] < cur[q]) {
-                const unsigned long long old = atomicMin(a.dist + c[q], nd[q]);
-                if (nd[q] < old) {
-                    fell |= 1u << q;
-                    lowered += 1;
-                    reached += old == kNoPath;
-                }
-            }
-        }
-        // queued once per round: the first lowering this round sets the mark
-        unsigned qd = 0;
-#pragma unroll
-        for (int q = 0; q < kWGroup; ++q) {
-            if ((fell >> q) & 1u) {
-                const uint32_t bit = 1u << (c[q] & 31);
-                if (!(atomicOr(mark + (c[q] >> 5), bit) & bit)) qd |= 1u << q;
-            }
-        }
+        for (int q = 0; q < kWGroup; ++q)
+            if (j[q] >= 0 && nd[q] < cur[q]) offer |= 1u << q;
+        unsigned long long old[kWGroup];
+        uint32_t mw[kWGroup];
         int rb[kWGroup], re[kWGroup];
 #pragma unroll
         for (int q = 0; q < kWGroup; ++q) {
+            old[q] = kNoPath;
+            mw[q] = ~0u;
             rb[q] = re[q] = 0;
-            if ((qd >> q) & 1u) {
+            if ((offer >> q) & 1u) {
+                old[q] = atomicMin(a.dist + c[q], nd[q]);
+                mw[q] = atomicOr(mark + (c[q] >> 5), 1u << (c[q] & 31));
                 rb[q] = __ldg(a.row_ptr + c[q]);
                 re[q] = __ldg(a.row_ptr + c[q] + 1);
             }
+        }
+        // queued once per round: the offer that set the mark queues the head
+        unsigned qd = 0;
+#pragma unroll
+        for (int q = 0; q < kWGroup; ++q) {
+            if (!((offer >> q) & 1u)) continue;
+            if (nd[q] < old[q]) {
+                lowered += 1;
+                reached += old[q] == kNoPath;
+            }
+            if (!((mw[q] >> (c[q] & 31)) & 1u)) qd |= 1u << q;
         }
         w_enqueue_group(qd, c, rb, re, lane, nqv, nqe, nqo, out);
     }
 }
 
-__global__ void __launch_bounds__(kWThreads) wsssp_kernel(WArgs a) {
+__global__ void __launch_bounds__(kWThreads, 2) wsssp_kernel(WArgs a) {
     __shared__ unsigned long long s_snap[3];
     __shared__ int s_status;
     if (threadIdx.x == 0) s_status = w_ld_relaxed_s32(a.status);
