@@ -83,6 +83,7 @@ struct dawn_graph {
     int32_t nwords = 0;               // ceil(n / 32), bitmap words
     int32_t* row_ptr = nullptr;       // CSR, device
     std::vector<int32_t> row_ptr_host;  // copy of row_ptr: the source row bounds travel as launch arguments
+    std::vector<int32_t> csize_host;    // symmetric graphs: size of each vertex's connected component
     int32_t* col_idx = nullptr;
     int32_t* in_ptr = nullptr;        // CSC (== CSR when symmetric), device
     int32_t* in_idx = nullptr;

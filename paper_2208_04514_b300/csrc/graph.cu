@@ -202,6 +202,60 @@ __global__ void pull_order_cta_kernel(const int32_t* __restrict__ in_ptr, const 
     }
 }
 
+// Connected components of a symmetric graph (lock-free union-find): every
+// vertex starts as its own root; each arc u -> v with v < u links the two
+// roots, the larger under the smaller, by compare-and-swap (so no cycle can
+// form), finds halving paths as they go; a final pass points every vertex
+// at its root.  The level loop uses the component sizes: on a symmetric
+// graph the vertices reachable from s are exactly s's component.
+__device__ int cc_find(int* p, int v) {
+    while (true) {
+        const int q = p[v];
+        if (q == v) return v;
+        const int r = p[q];
+        if (r != q) p[v] = r;  // path halving (a stale write only lengthens a later walk)
+        v = q;
+    }
+}
+
+__global__ void cc_init_kernel(int* p, int32_t n) {
+    for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (long long)gridDim.x * blockDim.x)
+        p[v] = (int)v;
+}
+
+// one warp per vertex, lanes over its row
+__global__ void cc_hook_kernel(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci, int32_t n, int* p) {
+    const int lane = threadIdx.x & 31;
+    const long long nw = (long long)gridDim.x * (blockDim.x >> 5);
+    for (long long u = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < n; u += nw) {
+        for (int j = rp[u] + lane; j < rp[u + 1]; j += 32) {
+            int a = (int)u, b = ci[j];
+            if (b >= a) continue;
+            while (true) {
+                int ra = cc_find(p, a), rb = cc_find(p, b);
+                if (ra == rb) break;
+                if (ra < rb) { const int t = ra; ra = rb; rb = t; }
+                const int old = atomicCAS(p + ra, ra, rb);
+                if (old == ra) break;
+                a = ra;  // ra gained a parent meanwhile: retry from there
+                b = rb;
+            }
+        }
+    }
+}
+
+__global__ void cc_count_kernel(int* p, int32_t n, int32_t* size) {
+    for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (long long)gridDim.x * blockDim.x) {
+        const int r = cc_find(p, (int)v);
+        atomicAdd(size + r, 1);
+    }
+}
+
+__global__ void cc_size_kernel(int* p, int32_t n, const int32_t* size, int32_t* csize) {
+    for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (long long)gridDim.x * blockDim.x)
+        csize[v] = size[cc_find(p, (int)v)];
+}
+
 // first2[v] = the first two in-neighbours of v in pull order (-1 past the row's
 // end): a pull tests them from one coalesced load per warp, before any
 // scattered read of the row itself.
@@ -432,6 +486,32 @@ int upload(const int32_t* row_ptr, const int32_t* col_idx, int32_t n, int64_t m,
     g->row_ptr_host.resize((size_t)n + 1);
     e = cudaMemcpy(g->row_ptr_host.data(), g->row_ptr, sizeof(int32_t) * ((size_t)n + 1), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) { release(g); return cuda_fail(e, "graph setup (row_ptr copy)", __FILE__, __LINE__); }
+    if (flags & DAWN_SYMMETRIC) {
+        // component size per vertex (host copy: it travels as a launch argument)
+        int* p = nullptr;
+        int32_t* size = nullptr;
+        int32_t* csize = nullptr;
+        const int grid = grid_for(n, g->sms);
+        e = cudaMallocAsync((void**)&p, sizeof(int) * (size_t)n, st);
+        if (e == cudaSuccess) e = cudaMallocAsync((void**)&size, sizeof(int32_t) * (size_t)n, st);
+        if (e == cudaSuccess) e = cudaMallocAsync((void**)&csize, sizeof(int32_t) * (size_t)n, st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(size, 0, sizeof(int32_t) * (size_t)n, st);
+        if (e == cudaSuccess) {
+            cc_init_kernel<<<grid, kThreads, 0, st>>>(p, n);
+            cc_hook_kernel<<<grid_for((int64_t)n * 32, g->sms), kThreads, 0, st>>>(g->row_ptr, g->col_idx, n, p);
+            cc_count_kernel<<<grid, kThreads, 0, st>>>(p, n, size);
+            cc_size_kernel<<<grid, kThreads, 0, st>>>(p, n, size, csize);
+            e = cudaGetLastError();
+        }
+        g->csize_host.resize((size_t)n);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(g->csize_host.data(), csize, sizeof(int32_t) * (size_t)n, cudaMemcpyDeviceToHost, st);
+        if (p) cudaFreeAsync(p, st);
+        if (size) cudaFreeAsync(size, st);
+        if (csize) cudaFreeAsync(csize, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) { release(g); return cuda_fail(e, "graph setup (components)", __FILE__, __LINE__); }
+    }
     int rc = sssp_occupancy(g);
     if (rc != DAWN_OK) { release(g); return rc; }
     *out = g;

@@ -75,6 +75,8 @@ struct SsspArgs {
     int32_t nwords;
     int32_t src;
     int32_t srb, sre;        // the source row [srb, sre) of col_idx; srb < 0: read from row_ptr
+    long long reach_target;  // vertices reachable from src when known (symmetric graph: src's
+                             // connected component), else past n: the loop stops on reaching them
     int32_t mode;
     int32_t alpha;
     int32_t beta;
@@ -931,6 +933,12 @@ __global__ void __launch_bounds__(kThreads, DAWN_SSSP_MIN_CTAS) sssp_kernel(Sssp
         reached += nf_cur;
         edges += mf_cur;
         mu -= mf_cur;
+        // every vertex src can reach has its distance: no level can find more
+        // (the empty level that would show it is skipped)
+        if (reached >= a.reach_target) {
+            ++step;
+            break;
+        }
         const long long nc_cur = (long long)s_snap[3];  // unreached candidates, after a pull
         int kind;
         if (a.mode == DAWN_MODE_PUSH) kind = kPush;
@@ -1061,6 +1069,7 @@ int sssp_launch(dawn_graph* g, int32_t src, int32_t* dist_dev, const dawn_sssp_o
     a.src = src;
     a.srb = g->row_ptr_host[src];
     a.sre = g->row_ptr_host[src + 1];
+    a.reach_target = g->csize_host.empty() ? LLONG_MAX : (long long)g->csize_host[src];
     a.mode = opts ? opts->mode : DAWN_MODE_AUTO;
     a.alpha = (opts && opts->alpha > 0) ? opts->alpha : (g->tuning.alpha > 0 ? g->tuning.alpha : 15);
     a.beta = (opts && opts->beta > 0) ? opts->beta : (g->tuning.beta > 0 ? g->tuning.beta : 18);
@@ -1217,6 +1226,7 @@ int sssp_noalloc(const int32_t* row_ptr, const int32_t* col_idx, int32_t n, int6
     a.nwords = (int32_t)(((int64_t)n + 31) / 32);
     a.src = src;
     a.srb = a.sre = -1;  // the caller's CSR: read on the device
+    a.reach_target = LLONG_MAX;
     a.mode = DAWN_MODE_PUSH;
     a.bar_parity = 0;  // the whole control block was just zeroed
     a.smem_words = 0;
