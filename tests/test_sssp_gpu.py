@@ -353,3 +353,31 @@ def test_many_device_rows_graph_replay(dawn):
                 np.testing.assert_array_equal(one.cpu().numpy(), want[0])
     finally:
         dawn.dawn_graph_free(h)
+
+
+def test_symmetric_components_stop_when_reached(dawn):
+    """On a symmetric graph the loop stops as soon as the source's connected
+    component (found at upload) is reached: distances and statistics are as
+    before, and the levels run are exactly those that reached a vertex."""
+    src, dst = [], []
+    def edge(a, b):
+        src.extend([a, b])
+        dst.extend([b, a])
+    for i in range(49):          # path 0..49
+        edge(i, i + 1)
+    for i in range(51, 70):      # star: centre 50, leaves 51..69
+        edge(50, i)
+    for i in range(30):          # cycle 70..99
+        edge(70 + i, 70 + (i + 1) % 30)
+    edge(0, 0)                   # a self-loop; 100..104 isolated
+    g = gg.from_arcs(105, src, dst, symmetric=True)
+    h = upload(dawn, g)
+    try:
+        for s in [0, 25, 49, 50, 57, 70, 85, 102]:
+            d, st = gpu_sssp(dawn, h, g.n, s, {"engine": 1})  # the grid engine (AUTO picks the cluster here)
+            np.testing.assert_array_equal(d, oracle.sssp_sovm(g.row_ptr, g.col_idx, s))
+            check_stats(g, d, st)
+            if st["levels"] > 0:
+                assert st["push_steps"] + st["pull_steps"] == st["levels"]
+    finally:
+        dawn.dawn_graph_free(h)
