@@ -147,8 +147,16 @@ __device__ __forceinline__ void red_release_add(unsigned* p, unsigned v) {
 // thread 0 also reads that counter slot after the acquire and leaves
 // {qpack, nf, mf, nc, lr} in s_snap for the whole CTA: one L2 request per CTA
 // instead of one per warp on a single hot line.
+struct NoStep {
+    __device__ void operator()() const {}
+};
+
+// after: run by thread 0 once the snapshot is taken, before the CTA is
+// released (the level loop's bookkeeping, published through shared memory).
+template <typename After = NoStep>
 __device__ bool grid_barrier(Ctl* ctl, unsigned* count, unsigned& target, long long spin_limit,
-                             const CtrSlot* snap = nullptr, unsigned long long* s_snap = nullptr) {
+                             const CtrSlot* snap = nullptr, unsigned long long* s_snap = nullptr,
+                             After after = After()) {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -171,6 +179,7 @@ __device__ bool grid_barrier(Ctl* ctl, unsigned* count, unsigned& target, long l
             s_snap[2] = ld_relaxed_u64(&snap->mf);
             s_snap[3] = ld_relaxed_u64(&snap->nc);
             s_snap[4] = ld_relaxed_u64(&snap->lr);
+            after();
         }
         s_ok = ok;
     }
@@ -826,10 +835,80 @@ __device__ __noinline__ void fused_init_level1(const SsspArgs& a, int srb, int s
     flush_counts(claimed ? 1 : 0, claimed ? re - rb : 0, out);
 }
 
+// level kinds: push (SOVM), pull over the bitmap, pull over the candidate lists
+enum LevelKind { kPush = 0, kBitmapPull = 1, kListPull = 2, kStop = 3 };
+// how a push gets its frontier: the queue, a conversion of the bitmap
+// difference a bitmap pull left (then a barrier), or a list pull's list
+enum PushFrom { kFromQueue = 0, kFromBitmap = 1, kFromList = 2 };
+
+// The level loop's bookkeeping, kept by thread 0 of each CTA in shared memory
+// and advanced inside the grid barrier that ends a level, so the other threads
+// hold only the level's kind in registers.
+struct LoopState {
+    long long mu;       // arcs out of vertices not yet reached
+    long long prev_nf;  // vertices found by the level before the last one
+    long long reached, edges;
+    int pushes, pulls;
+    int last;           // kind of the last level run
+    int kind, from;     // the next level (kStop: the loop is over)
+    int levels;         // when stopped: the last level that reached a vertex
+};
+
+// The parameters of the direction rule (copied out of the launch arguments, so
+// that the barrier's callback captures a few scalars, not the whole struct).
+struct RuleArgs {
+    long long reach_target;
+    int32_t n, mode, alpha, beta;
+    bool lists;
+};
+
+// Thread 0, once the level `step` is over and its counters are in snap: add
+// them up and choose the next level (Beamer's rule, list pulls while the
+// candidates are few), or stop.
+__device__ __forceinline__ void next_level(const RuleArgs& a, LoopState& L, const unsigned long long* snap, int step) {
+    const bool lists = a.lists;
+    const long long nf_cur = (long long)snap[1];
+    const long long mf_cur = (long long)snap[2];
+    const long long nc_cur = (long long)snap[3];  // unreached candidates, after a pull
+    if (nf_cur == 0 || step >= a.n) {
+        L.kind = kStop;
+        L.levels = step > 0 ? step - 1 : 0;
+        return;
+    }
+    L.reached += nf_cur;
+    L.edges += mf_cur;
+    L.mu -= mf_cur;
+    // every vertex src can reach has its distance: no level can find more
+    // (the empty level that would show it is skipped)
+    if (L.reached >= a.reach_target) {
+        L.kind = kStop;
+        L.levels = step;
+        return;
+    }
+    int kind;
+    if (a.mode == DAWN_MODE_PUSH) kind = kPush;
+    else if (a.mode == DAWN_MODE_PULL)
+        kind = (L.last != kPush && lists && nc_cur <= 4 * mf_cur && 4 * nc_cur <= a.n) ? kListPull : kBitmapPull;
+    else if (L.last == kPush) kind = mf_cur * a.alpha > L.mu ? kBitmapPull : kPush;
+    // after a pull: test only the candidates left while they are few (next to
+    // the frontier's arcs, and at most a quarter of the vertices: a larger
+    // list is cheaper as a bitmap pull with its tests in shared memory);
+    // otherwise the push / pull rule
+    else if (lists && nc_cur <= 4 * mf_cur && 4 * nc_cur <= a.n) kind = kListPull;
+    else kind = (nf_cur * a.beta < a.n && nf_cur < L.prev_nf) ? kPush : kBitmapPull;
+    L.from = kind != kPush ? kFromQueue : (L.last == kBitmapPull ? kFromBitmap : (L.last == kListPull ? kFromList : kFromQueue));
+    L.prev_nf = nf_cur;
+    L.kind = kind;
+    L.last = kind;
+    if (kind == kPush) ++L.pushes;
+    else ++L.pulls;
+}
+
 __global__ void __launch_bounds__(kThreads, DAWN_SSSP_MIN_CTAS) sssp_kernel(SsspArgs a) {
     Ctl* ctl = a.ctl;
     __shared__ unsigned long long s_snap[5];  // {qpack, nf, mf, nc, lr} of the level just finished
     __shared__ int s_cn, s_cin, s_cprev;      // this CTA's candidates: being kept / to test / tested last
+    __shared__ LoopState L;
     __shared__ int s_status;
     // an earlier call that failed leaves the barrier state inconsistent: this
     // launch then stops before its first barrier (its outputs are undefined,
@@ -845,6 +924,10 @@ __global__ void __launch_bounds__(kThreads, DAWN_SSSP_MIN_CTAS) sssp_kernel(Sssp
     const long long gtid = (long long)blockIdx.x * kThreads + threadIdx.x;
     const long long gthreads = (long long)gridDim.x * kThreads;
 
+    // candidate lists: this CTA's region is the vertices of the bitmap words its warps scan
+    const int nwarps = gridDim.x * kWarps;
+    const long long region = (long long)kWarps * ((a.nwords + nwarps - 1) / nwarps) * 32;
+    const bool lists = a.cand0 != nullptr && region * gridDim.x <= a.cand_cap;
     // this launch's counter slots (zero on entry); zero the next launch's
     CtrSlot* ctr = ctl->ctr[a.bar_parity];
     if (blockIdx.x == gridDim.x - 1 && threadIdx.x < 3 * (int)(sizeof(CtrSlot) / 8))
@@ -862,11 +945,30 @@ __global__ void __launch_bounds__(kThreads, DAWN_SSSP_MIN_CTAS) sssp_kernel(Sssp
     // and the first grid barrier already ends level 1.
     const bool fused = a.mode != DAWN_MODE_PULL && sdeg <= kThreads &&
                        (a.mode == DAWN_MODE_PUSH || (long long)sdeg * a.alpha <= a.m - sdeg);
+    // the loop starts after level 0 (the source), or after level 1 when fused
+    int step = fused ? 1 : 0;
+    if (threadIdx.x == 0) {
+        L.mu = a.m - (fused ? sdeg : 0);
+        L.prev_nf = fused ? 1 : 0;
+        L.reached = fused ? 1 : 0;
+        L.edges = fused ? sdeg : 0;
+        L.pushes = fused ? 1 : 0;
+        L.pulls = 0;
+        L.last = kPush;
+        L.kind = kStop;
+        L.from = kFromQueue;
+        L.levels = 0;
+        s_cn = s_cin = s_cprev = 0;
+    }
+    const RuleArgs ra = {a.reach_target, a.n, a.mode, a.alpha, a.beta, lists};
+    unsigned long long* const snap = s_snap;
+    LoopState* const lp = &L;
+    auto advance = [ra, snap, lp](int done_step) { next_level(ra, *lp, snap, done_step); };
     const bool d16 = (((uintptr_t)a.dist) & 15u) == 0;
     if (fused) {
         fused_init_level1(a, srb, sdeg, &ctr[1]);  // ends with __syncthreads
         if (s_status != DEV_OK) return;
-        if (!grid_barrier(ctl, bar, bar_target, a.spin_limit, &ctr[1], s_snap)) return;
+        if (!grid_barrier(ctl, bar, bar_target, a.spin_limit, &ctr[1], s_snap, [advance]() { advance(1); })) return;
         if (gtid == 0) ctl->bar[a.bar_parity ^ 1].count = 0;  // the next launch's counter
         if (tracer) {
             trace_rec(a, tslot, 1, 0, 1);
@@ -893,7 +995,7 @@ __global__ void __launch_bounds__(kThreads, DAWN_SSSP_MIN_CTAS) sssp_kernel(Sssp
         __syncthreads();
         if (s_status != DEV_OK) return;
         // dist[src] = 0 after the fill; the barrier orders it after every -1 store
-        if (!grid_barrier(ctl, bar, bar_target, a.spin_limit, &ctr[0], s_snap)) return;
+        if (!grid_barrier(ctl, bar, bar_target, a.spin_limit, &ctr[0], s_snap, [advance]() { advance(0); })) return;
         if (gtid == 0) {
             a.dist[src] = 0;
             ctl->bar[a.bar_parity ^ 1].count = 0;  // the next launch's counter
@@ -903,60 +1005,23 @@ __global__ void __launch_bounds__(kThreads, DAWN_SSSP_MIN_CTAS) sssp_kernel(Sssp
 
     uint32_t* vcur = a.vis0;
     uint32_t* vnext = a.vis1;
-    // level kinds: push (SOVM), pull over the bitmap, pull over the candidate lists
-    enum { kPush = 0, kBitmapPull = 1, kListPull = 2 };  // a push after a list pull reads its list
-    // the loop starts after level 0 (the source), or after level 1 when fused
-    long long mu = a.m - (fused ? sdeg : 0);  // arcs out of vertices not yet reached
-    long long prev_nf = fused ? 1 : 0;
-    long long reached = fused ? 1 : 0, edges = fused ? sdeg : 0;
-    int pushes = fused ? 1 : 0, pulls = 0;
-    int last = kPush;
-    int step = fused ? 1 : 0;
-    // this CTA's region of the candidate lists: the bitmap words its warps scan
-    const int nwarps = gridDim.x * kWarps;
-    const long long region = (long long)kWarps * ((a.nwords + nwarps - 1) / nwarps) * 32;
-    const bool lists = a.cand0 != nullptr && region * gridDim.x <= a.cand_cap;
     int32_t* cl[2] = {a.cand0 + blockIdx.x * region, a.cand1 + blockIdx.x * region};
     int cpar = 0;  // the list the next list pull reads
-    if (threadIdx.x == 0) s_cn = s_cin = s_cprev = 0;
-    __syncthreads();
     while (true) {
+        const int kind = L.kind;  // chosen by thread 0 inside the last barrier
+        if (kind == kStop) break;
+        const int from = L.from;
         CtrSlot* cur = &ctr[step % 3];
         // the frontier found at step s lives in queue (s & 1)
         const Queue qcur = (step & 1) ? Queue{a.q1, a.q1off} : Queue{a.q0, a.q0off};
         const Queue qnext = (step & 1) ? Queue{a.q0, a.q0off} : Queue{a.q1, a.q1off};
         unsigned long long qpack = s_snap[0];
         bool qlong = s_snap[4] != 0;  // the queue holds a row of more than kEntryArcs arcs
-        const long long nf_cur = (long long)s_snap[1];
-        const long long mf_cur = (long long)s_snap[2];
-        if (nf_cur == 0 || step >= a.n) break;
-        reached += nf_cur;
-        edges += mf_cur;
-        mu -= mf_cur;
-        // every vertex src can reach has its distance: no level can find more
-        // (the empty level that would show it is skipped)
-        if (reached >= a.reach_target) {
-            ++step;
-            break;
-        }
-        const long long nc_cur = (long long)s_snap[3];  // unreached candidates, after a pull
-        int kind;
-        if (a.mode == DAWN_MODE_PUSH) kind = kPush;
-        else if (a.mode == DAWN_MODE_PULL)
-            kind = (last != kPush && lists && nc_cur <= 4 * mf_cur && 4 * nc_cur <= a.n) ? kListPull : kBitmapPull;
-        else if (last == kPush) kind = mf_cur * a.alpha > mu ? kBitmapPull : kPush;
-        // after a pull: test only the candidates left while they are few
-        // (next to the frontier's arcs, and at most a quarter of the
-        // vertices: a larger list is cheaper as a bitmap pull with its
-        // tests in shared memory); otherwise the push / pull rule
-        else if (lists && nc_cur <= 4 * mf_cur && 4 * nc_cur <= a.n) kind = kListPull;
-        else kind = (nf_cur * a.beta < a.n && nf_cur < prev_nf) ? kPush : kBitmapPull;
         const bool pull = kind != kPush;
-        prev_nf = nf_cur;
         if (blockIdx.x == 0 && threadIdx.x < (int)(sizeof(CtrSlot) / 8))
             reinterpret_cast<unsigned long long*>(&ctr[(step + 2) % 3])[threadIdx.x] = 0;
 
-        if (kind == kPush && last == kBitmapPull) {
+        if (from == kFromBitmap) {
             // the frontier exists only as a bitmap difference: turn it into a queue
             bitmap_to_queue(a, vcur, vnext, qcur, cur);
             if (!grid_barrier(ctl, bar, bar_target, a.spin_limit, cur, s_snap)) return;
@@ -970,50 +1035,46 @@ __global__ void __launch_bounds__(kThreads, DAWN_SSSP_MIN_CTAS) sssp_kernel(Sssp
             int32_t* keep = lists ? cl[cpar] : nullptr;
             if (a.smem_words > 0) pull_level<true>(a, step + 1, vcur, vnext, nf, mf, keep, &s_cn);
             else pull_level<false>(a, step + 1, vcur, vnext, nf, mf, keep, &s_cn);
-            ++pulls;
         } else if (kind == kListPull) {
             const LevelCount lc = list_pull_level(a, step + 1, vcur, cl[cpar], s_cin, cl[cpar ^ 1], &s_cn);
             nf = lc.nf;
             mf = lc.mf;
             cpar ^= 1;
-            ++pulls;
-        } else if (last == kListPull) {
+        } else if (from == kFromList) {
             // the frontier: entries of the last list pull's input list found by it
             const LevelCount lc = list_push_level(a, step + 1, vcur, cl[cpar ^ 1], s_cprev, out);
             nf = lc.nf;
             mf = lc.mf;
-            ++pushes;
         } else {
-            push_level(a, step + 1, vcur, qcur, qpack, qlong, 16 * reached > a.n, qnext, out, nf, mf);
-            ++pushes;
+            push_level(a, step + 1, vcur, qcur, qpack, qlong, 16 * L.reached > a.n, qnext, out, nf, mf);
         }
         flush_counts(nf, mf, out, pull ? &s_cn : nullptr);
-        if (!grid_barrier(ctl, bar, bar_target, a.spin_limit, out, s_snap)) return;
-        if (pull) {
-            if (threadIdx.x == 0) {
-                s_cprev = s_cin;  // the list just tested (read by a list push)
-                s_cin = s_cn;     // the list just written is the one the next list pull reads
-                s_cn = 0;
-            }
-            __syncthreads();
-        }
+        const int done = step + 1;
+        if (!grid_barrier(ctl, bar, bar_target, a.spin_limit, out, s_snap, [advance, pull, done]() {
+                if (pull) {
+                    s_cprev = s_cin;  // the list just tested (read by a list push)
+                    s_cin = s_cn;     // the list just written is the one the next list pull reads
+                    s_cn = 0;
+                }
+                advance(done);
+            }))
+            return;
         if (tracer) trace_rec(a, tslot, kind == kPush ? 2 : (kind == kBitmapPull ? 3 : 5), step + 1, (long long)s_snap[1]);
         if (kind == kBitmapPull) {
             uint32_t* t = vcur;
             vcur = vnext;
             vnext = t;
         }
-        last = kind;
         ++step;
     }
     if (gtid == 0 && a.stats) {
         dawn_sssp_stats s;
-        s.levels = step > 0 ? step - 1 : 0;
-        s.push_steps = pushes;
-        s.pull_steps = pulls;
+        s.levels = L.levels;
+        s.push_steps = L.pushes;
+        s.pull_steps = L.pulls;
         s.reserved = 0;
-        s.reached = reached;
-        s.edges = edges;
+        s.reached = L.reached;
+        s.edges = L.edges;
         *a.stats = s;
     }
 }
