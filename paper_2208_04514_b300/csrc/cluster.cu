@@ -160,27 +160,34 @@ __global__ void __launch_bounds__(kClThreads, 1) cluster_sssp_kernel(ClArgs a) {
                         won[q] = (*(volatile uint32_t*)word & bit) == 0u && (atomicOr(word, bit) & bit) == 0u;
                     }
                 }
+                // local appends of all four arcs: one shared reservation per warp
+                unsigned lb[4];
+                int ltot = 0;
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
                     if (won[q]) a.dist[x[q]] = level;
                     my_claims += won[q];
-                    // local appends: one shared reservation per warp
-                    const bool loc = won[q] && owner[q] == rank;
-                    const unsigned b = __ballot_sync(kFull, loc);
-                    if (b) {
-                        const int leader = __ffs(b) - 1;
-                        int slot0 = 0;
-                        if (lane == leader) slot0 = atomicAdd(&sh.qn[pn], __popc(b));
-                        slot0 = __shfl_sync(kFull, slot0, leader);
-                        if (loc) {
-                            const int slot = slot0 + __popc(b & ((1u << lane) - 1u));
+                    lb[q] = __ballot_sync(kFull, won[q] && owner[q] == rank);
+                    ltot += __popc(lb[q]);
+                }
+                if (ltot) {
+                    int slot0 = 0;
+                    if (lane == 0) slot0 = atomicAdd(&sh.qn[pn], ltot);
+                    slot0 = __shfl_sync(kFull, slot0, 0);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        if ((lb[q] >> lane) & 1u) {
+                            const int slot = slot0 + __popc(lb[q] & ((1u << lane) - 1u));
                             if (slot < a.qcap) s_list[pn][slot] = x[q];
                             else ovf_next[atomicAdd(ovf_next_n, 1u)] = x[q];
                         }
+                        slot0 += __popc(lb[q]);
                     }
+                }
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
                     if (won[q] && owner[q] != rank)
                         cl_append(cluster, owner[q], rank, x[q], s_list[pn], &sh.qn[pn], ovf_next, ovf_next_n, a.qcap);
-                }
             }
             unsigned wl = __ballot_sync(kFull, has && wide);
             while (wl) {  // long rows: the whole warp, one arc per thread
