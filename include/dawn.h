@@ -105,10 +105,15 @@ typedef struct dawn_server* dawn_server_t;
  *   n >= 1, 0 <= m < 2^31, flags = DAWN_DIRECTED or DAWN_SYMMETRIC.
  * The library validates the CSR on the device (DAWN_E_INVALID with the first
  * offending index in dawn_last_error), builds the in-adjacency for directed
- * graphs, and allocates the per-graph work buffers (about 4m + 40n bytes
- * beyond the CSR for a directed graph, 24n for a symmetric one).  The caller
- * keeps ownership of its arrays; *out owns the device copy until
- * dawn_graph_free.  Synchronizes `stream`.
+ * graphs, a copy of the in-adjacency with each row ordered by the neighbours'
+ * out-degree (largest first) and the first two entries of each such row, and
+ * allocates the per-graph work buffers: about 4m + 45n bytes beyond the CSR
+ * for a symmetric graph, 8m + 49n for a directed one.  For a symmetric graph
+ * it also finds the connected components, so that a search stops as soon as
+ * the source's component is reached.  Host memory: 8n bytes (copies of
+ * row_ptr and of the component sizes).  The caller keeps ownership of its
+ * arrays; *out owns the device copy until dawn_graph_free.  Synchronizes
+ * `stream`.
  */
 DAWN_API int dawn_graph_upload(const int32_t* row_ptr, const int32_t* col_idx, int32_t n, int64_t m,
                                uint32_t flags, void* stream, dawn_graph_t* out);
@@ -124,8 +129,10 @@ DAWN_API int dawn_graph_info(dawn_graph_t g, int32_t* n, int64_t* m, uint32_t* f
  * Single-source shortest paths (Alg. 3 SOVM and Alg. 1 BOVM, Sec. 3.2-3.3).
  *   src   0 <= src < n, else DAWN_E_INVALID.
  *   dist  host or device, int32[n], written in full.
- * Runs the level loop from src until a step reaches no vertex, in one
- * persistent cooperative kernel on `stream`, then synchronizes `stream`.
+ * Runs the level loop from src until a step reaches no vertex (on a
+ * symmetric graph: until every vertex of src's connected component has its
+ * distance, which skips that empty step), in one persistent cooperative
+ * kernel on `stream`, then synchronizes `stream`.
  * DAWN_MODE_AUTO is used; see dawn_sssp_ex for the other modes.
  */
 DAWN_API int dawn_sssp(dawn_graph_t g, int32_t src, int32_t* dist, void* stream);
