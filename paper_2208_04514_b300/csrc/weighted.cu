@@ -168,44 +168,65 @@ __device__ __forceinline__ void w_flush(long long lowered, long long reached, WS
     }
 }
 
-// Queue up to kWGroup vertices per lane (lanes' `q` bits) for the next round:
-// one record per vertex with a non-empty row, one 64-bit reservation per
-// warp (records in the high word, arcs in the low word, so offsets grow with
-// the slot).  Full warp.
+// Windows of 32 arcs a warp takes per group (see relax_round).
 constexpr int kWGroup = 4;
 
-__device__ __forceinline__ void w_enqueue_group(unsigned q, const int* v, const int* rb, const int* re, int lane,
-                                                int32_t* qv, int2* qe, int32_t* qo, WSlot* out) {
-    int cnt = 0, deg = 0;
+// Queue records gathered per warp in shared memory and reserved in the next
+// round's queue in batches: one 64-bit atomic on the round's counter per
+// batch (>= kWFlush records) rather than one per group of windows, since the
+// reservations of every warp meet on that one counter.
+constexpr int kWBuf = 192;                     // records a warp's buffer holds
+constexpr int kWFlush = kWBuf - 32 * kWGroup;  // flush at this fill: a group adds at most 32 * kWGroup
+__shared__ int s_wbuf_v[kWWarps][kWBuf];       // vertex
+__shared__ int2 s_wbuf_e[kWWarps][kWBuf];      // {first arc, arc count}
+
+// Append the lanes' queued vertices with a non-empty row to the warp's buffer
+// (nbuf records, warp-uniform).  Full warp.
+__device__ __forceinline__ void w_buffer_group(unsigned q, const int* v, const int* rb, const int* re, int lane,
+                                               int* bv, int2* be, int& nbuf) {
+    int cnt = 0;
+#pragma unroll
+    for (int i = 0; i < kWGroup; ++i) cnt += ((q >> i) & 1u) && re[i] > rb[i];
+    const int incl = w_scan(cnt, lane);
+    int pos = nbuf + incl - cnt;
 #pragma unroll
     for (int i = 0; i < kWGroup; ++i) {
-        if ((q >> i) & 1u) {
-            const int d = re[i] - rb[i];
-            cnt += d > 0;
-            deg += d;
+        if (((q >> i) & 1u) && re[i] > rb[i]) {
+            bv[pos] = v[i];
+            be[pos] = make_int2(rb[i], re[i] - rb[i]);
+            ++pos;
         }
     }
-    const int cincl = w_scan(cnt, lane);
-    const int ctot = __shfl_sync(kWFull, cincl, 31);
-    if (ctot == 0) return;
-    const int dincl = w_scan(deg, lane);
-    const int dtot = __shfl_sync(kWFull, dincl, 31);
-    unsigned long long base = 0;
-    if (lane == 31) base = atomicAdd(&out->qpack, ((unsigned long long)ctot << 32) | (unsigned)dtot);
-    base = __shfl_sync(kWFull, base, 31);
-    int pos = (int)(base >> 32) + cincl - cnt;
-    int aoff = (int)(base & 0xffffffffu) + dincl - deg;
+    nbuf += __shfl_sync(kWFull, incl, 31);
+    __syncwarp();
+}
+
+// Reserve the warp's nbuf buffered records in the next round's queue (one
+// atomic: records in the high word, arcs in the low word) and copy them
+// there with each record's arc offset.  Full warp.
+__device__ __forceinline__ void w_flush_buffer(const int* bv, const int2* be, int nbuf, int lane, int32_t* qv,
+                                               int2* qe, int32_t* qo, WSlot* out) {
+    int arcs = 0;
+    for (int i = lane; i < nbuf; i += 32) arcs += be[i].y;
 #pragma unroll
-    for (int i = 0; i < kWGroup; ++i) {
-        if (!((q >> i) & 1u)) continue;
-        const int d = re[i] - rb[i];
-        if (d <= 0) continue;
-        qv[pos] = v[i];
-        qe[pos] = make_int2(rb[i], d);
-        qo[pos] = aoff;
-        ++pos;
-        aoff += d;
+    for (int o = 16; o > 0; o >>= 1) arcs += __shfl_xor_sync(kWFull, arcs, o);
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(&out->qpack, ((unsigned long long)nbuf << 32) | (unsigned)arcs);
+    base = __shfl_sync(kWFull, base, 0);
+    const int slot0 = (int)(base >> 32);
+    int carry = (int)(base & 0xffffffffu);
+    for (int i0 = 0; i0 < nbuf; i0 += 32) {
+        const int i = i0 + lane;
+        const int2 e = i < nbuf ? be[i] : make_int2(0, 0);
+        const int incl = w_scan(e.y, lane);
+        if (i < nbuf) {
+            qv[slot0 + i] = bv[i];
+            qe[slot0 + i] = e;
+            qo[slot0 + i] = carry + incl - e.y;
+        }
+        carry += __shfl_sync(kWFull, incl, 31);
     }
+    __syncwarp();
 }
 
 // One (min, +) round over the frontier of round r (qn records, E arcs).  A
@@ -260,6 +281,9 @@ __device__ void relax_round(const WArgs& a, int r, int qn, long long E, WSlot* o
     int32_t* nqv = a.qv[(r + 1) & 1];
     int2* nqe = a.qe[(r + 1) & 1];
     int32_t* nqo = a.qo[(r + 1) & 1];
+    int* bv = s_wbuf_v[threadIdx.x >> 5];
+    int2* be = s_wbuf_e[threadIdx.x >> 5];
+    int nbuf = 0;  // warp-uniform
     for (long long gb = a0; gb < a1; gb += 32 * kWGroup) {
         int j[kWGroup];
         unsigned long long odu[kWGroup];
@@ -338,8 +362,13 @@ __device__ void relax_round(const WArgs& a, int r, int qn, long long E, WSlot* o
             }
             if (!((mw[q] >> (c[q] & 31)) & 1u)) qd |= 1u << q;
         }
-        w_enqueue_group(qd, c, rb, re, lane, nqv, nqe, nqo, out);
+        w_buffer_group(qd, c, rb, re, lane, bv, be, nbuf);
+        if (nbuf >= kWFlush) {
+            w_flush_buffer(bv, be, nbuf, lane, nqv, nqe, nqo, out);
+            nbuf = 0;
+        }
     }
+    if (nbuf > 0) w_flush_buffer(bv, be, nbuf, lane, nqv, nqe, nqo, out);
 }
 
 __global__ void __launch_bounds__(kWThreads, 2) wsssp_kernel(WArgs a) {
