@@ -272,43 +272,70 @@ __device__ __forceinline__ void load_batch(const Queue& q, int qn, int b, int la
     eoff = i < qn ? __ldcg(q.off + i) : INT_MAX;
 }
 
-// Append up to kPushGroup claimed rows per lane with one reservation per warp
-// (same record layout as warp_enqueue; a lane's rows keep their order).
+// Windows of 32 arcs a push takes per group (see push_level).
 constexpr int kPushGroup = 4;
 
-__device__ __forceinline__ void warp_enqueue_group(unsigned has, const int* rb, const int* re, int lane, Queue q,
-                                                   CtrSlot* out) {
-    int cnt = 0, deg = 0, dmax = 0;
+// The rows a push level claims gather in a per-warp buffer in the kernel's
+// dynamic shared memory (the pull levels' bitmap copy, idle during a push)
+// and are reserved in the queue in batches: one atomic on the level's
+// counter per batch of >= kPushFlush rows instead of one per group of
+// windows, since every warp's reservations meet on that one counter.
+extern __shared__ uint4 s_bitmap4[];  // the kernel's dynamic shared memory
+constexpr int kPushBuf = 192;                          // rows a warp's buffer holds
+constexpr int kPushFlush = kPushBuf - 32 * kPushGroup;  // a group adds at most 32 * kPushGroup
+constexpr int kPushBufBytes = kWarps * kPushBuf * (int)sizeof(int2);
+
+// Append the lanes' claimed non-empty rows {first arc, arc count} to the
+// warp's buffer (nbuf rows, warp-uniform).  Full warp.
+__device__ __forceinline__ void warp_buffer_group(unsigned has, const int* rb, const int* re, int lane, int2* buf,
+                                                  int& nbuf) {
+    int cnt = 0;
+#pragma unroll
+    for (int i = 0; i < kPushGroup; ++i) cnt += ((has >> i) & 1u) && re[i] > rb[i];
+    const int incl = warp_inclusive_scan(cnt, lane);
+    int pos = nbuf + incl - cnt;
 #pragma unroll
     for (int i = 0; i < kPushGroup; ++i) {
-        if ((has >> i) & 1u) {
-            const int d = re[i] - rb[i];
-            cnt += d > 0;
-            deg += d;
-            dmax = max(dmax, d);
+        if (((has >> i) & 1u) && re[i] > rb[i]) {
+            buf[pos] = make_int2(rb[i], re[i] - rb[i]);
+            ++pos;
         }
     }
-    const int cincl = warp_inclusive_scan(cnt, lane);
-    const int ctot = __shfl_sync(kFull, cincl, 31);
-    if (ctot == 0) return;
-    const int dincl = warp_inclusive_scan(deg, lane);
-    const int dtot = __shfl_sync(kFull, dincl, 31);
-    unsigned long long base = 0;
-    if (lane == 31) base = atomicAdd(&out->qpack, ((unsigned long long)ctot << 32) | (unsigned)dtot);
-    base = __shfl_sync(kFull, base, 31);
-    if (__any_sync(kFull, dmax > kEntryArcs) && lane == 31) atomicOr(&out->lr, 1ull);
-    int pos = (int)(base >> 32) + cincl - cnt;
-    int aoff = (int)(base & 0xffffffffu) + dincl - deg;
-#pragma unroll
-    for (int i = 0; i < kPushGroup; ++i) {
-        if (!((has >> i) & 1u)) continue;
-        const int d = re[i] - rb[i];
-        if (d <= 0) continue;
-        q.ent[pos] = make_int2(rb[i], d);
-        q.off[pos] = aoff;
-        ++pos;
-        aoff += d;
+    nbuf += __shfl_sync(kFull, incl, 31);
+    __syncwarp();
+}
+
+// Reserve the warp's nbuf buffered rows in the queue (one atomic: records in
+// the high word, arcs in the low word) and copy them with their arc offsets;
+// a row of more than kEntryArcs arcs raises the level's long-row flag.
+// Full warp.
+__device__ __forceinline__ void warp_flush_rows(const int2* buf, int nbuf, int lane, Queue q, CtrSlot* out) {
+    int arcs = 0;
+    bool lng = false;
+    for (int i = lane; i < nbuf; i += 32) {
+        const int d = buf[i].y;
+        arcs += d;
+        lng |= d > kEntryArcs;
     }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) arcs += __shfl_xor_sync(kFull, arcs, o);
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(&out->qpack, ((unsigned long long)nbuf << 32) | (unsigned)arcs);
+    base = __shfl_sync(kFull, base, 0);
+    if (__any_sync(kFull, lng) && lane == 0) atomicOr(&out->lr, 1ull);
+    const int slot0 = (int)(base >> 32);
+    int carry = (int)(base & 0xffffffffu);
+    for (int i0 = 0; i0 < nbuf; i0 += 32) {
+        const int i = i0 + lane;
+        const int2 e = i < nbuf ? buf[i] : make_int2(0, 0);
+        const int incl = warp_inclusive_scan(e.y, lane);
+        if (i < nbuf) {
+            q.ent[slot0 + i] = e;
+            q.off[slot0 + i] = carry + incl - e.y;
+        }
+        carry += __shfl_sync(kFull, incl, 31);
+    }
+    __syncwarp();
 }
 
 // SOVM push: expand the frontier's rows (Eq. 7: the new vector is the union
@@ -331,6 +358,8 @@ __device__ void push_level(const SsspArgs& a, int step, uint32_t* vis, Queue qin
     const long long E = (long long)(pack & 0xffffffffull);
     const long long nw = (long long)gridDim.x * kWarps;
     const long long gw = (long long)blockIdx.x * kWarps + (threadIdx.x >> 5);
+    int2* buf = reinterpret_cast<int2*>(s_bitmap4) + (threadIdx.x >> 5) * kPushBuf;  // claimed rows
+    int nbuf = 0;  // warp-uniform
     if (E == 0) return;
     // Light levels (rows of at most 8 arcs on average and none longer than
     // kEntryArcs, e.g. a lattice frontier): each warp takes whole records by
@@ -439,8 +468,13 @@ __device__ void push_level(const SsspArgs& a, int step, uint32_t* vis, Queue qin
                 mf += re[q] - rb[q];
             }
         }
-        warp_enqueue_group(claimed, rb, re, lane, qout, out);
+        warp_buffer_group(claimed, rb, re, lane, buf, nbuf);
+        if (nbuf >= kPushFlush) {
+            warp_flush_rows(buf, nbuf, lane, qout, out);
+            nbuf = 0;
+        }
     }
+    if (nbuf > 0) warp_flush_rows(buf, nbuf, lane, qout, out);
 }
 
 // BOVM pull: every unreached vertex tests its in-neighbours against the
@@ -452,8 +486,8 @@ __device__ void push_level(const SsspArgs& a, int step, uint32_t* vis, Queue qin
 
 // kSmem: the CTA first copies the whole step-start bitmap into shared memory
 // (it is read-only for the level), so every in-neighbour test is a shared
-// memory load instead of an L2 round trip.
-extern __shared__ uint4 s_bitmap4[];
+// memory load instead of an L2 round trip (s_bitmap4, the kernel's dynamic
+// shared memory).
 
 template <bool kSmem>
 __device__ __forceinline__ uint32_t bm_word(const uint32_t* vcur, int w) {
@@ -1084,12 +1118,17 @@ __global__ void __launch_bounds__(kThreads, DAWN_SSSP_MIN_CTAS) sssp_kernel(Sssp
 // Largest bitmap the pull levels copy into shared memory (n up to 1,638,400).
 constexpr int kSmemBitmapMax = DAWN_SSSP_SMEM_BITMAP_MAX;
 
+// Dynamic shared memory of a launch: the pull levels' bitmap copy (0 when it
+// does not fit) or the push levels' row buffers, whichever is larger.
+int sssp_dynamic_smem(int bitmap_bytes) { return bitmap_bytes > kPushBufBytes ? bitmap_bytes : kPushBufBytes; }
+
 int sssp_occupancy(dawn_graph* g) {
     int nb = 0;
     DAWN_CUDA_TRY(cudaFuncSetAttribute(sssp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBitmapMax));
     const size_t words4 = (size_t)(g->nwords + 3) / 4 * 4;
     g->sssp_smem_bytes = words4 * 4 <= (size_t)kSmemBitmapMax ? (int)(words4 * 4) : 0;
-    DAWN_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sssp_kernel, kThreads, g->sssp_smem_bytes));
+    DAWN_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sssp_kernel, kThreads,
+                                                                sssp_dynamic_smem(g->sssp_smem_bytes)));
     if (nb < 1) return fail(DAWN_E_CUDA, "persistent SSSP kernel cannot be resident on an SM");
     g->sssp_blocks_per_sm = nb;
     return DAWN_OK;
@@ -1155,7 +1194,7 @@ int sssp_launch(dawn_graph* g, int32_t src, int32_t* dist_dev, const dawn_sssp_o
     dim3 grid(g->sms * bps), block(kThreads);
     void* args[] = {&a};
     DAWN_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)sssp_kernel, grid, block, args,
-                                              (size_t)g->sssp_smem_bytes, st));
+                                              (size_t)sssp_dynamic_smem(g->sssp_smem_bytes), st));
     g->sssp_launches += 1;  // only a launch that was accepted zeroes the other counter
     return DAWN_OK;
 }
@@ -1222,7 +1261,9 @@ int noalloc_setup(NoAllocDevice** out) {
         void* p = nullptr;
         DAWN_CUDA_TRY(cudaGetSymbolAddress(&p, g_noalloc_scratch));
         DAWN_CUDA_TRY(cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev));
-        DAWN_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d.blocks_per_sm, sssp_kernel, kThreads, 0));
+        DAWN_CUDA_TRY(cudaFuncSetAttribute(sssp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBitmapMax));
+        DAWN_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d.blocks_per_sm, sssp_kernel, kThreads,
+                                                                    kPushBufBytes));
         if (d.blocks_per_sm < 1) return fail(DAWN_E_CUDA, "persistent SSSP kernel cannot be resident on an SM");
         d.scratch = static_cast<unsigned char*>(p);
     }
@@ -1302,7 +1343,7 @@ int sssp_noalloc(const int32_t* row_ptr, const int32_t* col_idx, int32_t n, int6
     a.spin_limit = kDefaultSpin;
     dim3 grid(d->sms * d->blocks_per_sm), block(kThreads);
     void* args[] = {&a};
-    DAWN_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)sssp_kernel, grid, block, args, 0, st));
+    DAWN_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)sssp_kernel, grid, block, args, kPushBufBytes, st));
     int status = 0;
     DAWN_CUDA_TRY(cudaMemcpyAsync(&status, &ctl->status, sizeof(int), cudaMemcpyDeviceToHost, st));
     DAWN_CUDA_TRY(cudaStreamSynchronize(st));
