@@ -515,25 +515,36 @@ template <bool kSmem>
 __device__ void pull_level(const SsspArgs& a, int step, const uint32_t* vcur, uint32_t* vnext,
                            long long& nf, long long& mf, int32_t* keep, int* s_cn) {
     const int lane = threadIdx.x & 31;
-    const int gw = blockIdx.x * kWarps + (threadIdx.x >> 5);
-    const int nw = gridDim.x * kWarps;
     const bool symmetric = a.in_ptr == a.row_ptr;
     const unsigned below = (1u << lane) - 1u;
     int* open = s_pull_open[threadIdx.x >> 5];
+    // this CTA's words are a contiguous range; its warps take chunks of
+    // kPullChunk words from a shared counter, so a warp whose chunks hold many
+    // open candidates does not keep the others waiting for it
+    __shared__ int s_chunk;
+    const int R = (a.nwords + gridDim.x - 1) / gridDim.x;
+    const int wbase = (int)min((long long)a.nwords, (long long)blockIdx.x * R);
+    const int wend = min(a.nwords, wbase + R);
+    if (threadIdx.x == 0) s_chunk = 0;
     if (kSmem) {
         const uint4* src4 = reinterpret_cast<const uint4*>(vcur);
         for (int i = threadIdx.x; i < (a.smem_words >> 2); i += kThreads) s_bitmap4[i] = __ldcg(src4 + i);
-        __syncthreads();
     }
-    for (int w0 = gw; w0 < a.nwords; w0 += kPullChunk * nw) {
+    __syncthreads();
+    while (true) {
+        int c = 0;
+        if (lane == 0) c = atomicAdd(&s_chunk, 1);
+        c = __shfl_sync(kFull, c, 0);
+        const int w0 = wbase + c * kPullChunk;
+        if (w0 >= wend) break;  // warp-uniform
         // ---- pass 1: the first two in-neighbours of every candidate
         uint32_t cur[kPullChunk];
         unsigned cmask = 0;  // bit k: this lane's vertex of word k is a candidate
 #pragma unroll
         for (int k = 0; k < kPullChunk; ++k) {
-            const int w = w0 + k * nw;
+            const int w = w0 + k;
             cur[k] = kFull;
-            if (w < a.nwords) {
+            if (w < wend) {
                 cur[k] = bm_word<kSmem>(vcur, w);
                 // candidates: not reached, and with at least one in-arc (excl
                 // also covers the padding bits past n).  excl is kept out of
@@ -546,7 +557,7 @@ __device__ void pull_level(const SsspArgs& a, int step, const uint32_t* vcur, ui
         if (!__any_sync(kFull, cmask)) {  // nothing to test: carry the words over
 #pragma unroll
             for (int k = 0; k < kPullChunk; ++k)
-                if (lane == 0 && w0 + k * nw < a.nwords) vnext[w0 + k * nw] = cur[k];
+                if (lane == 0 && w0 + k < wend) vnext[w0 + k] = cur[k];
             continue;
         }
         int2 f2[kPullChunk];
@@ -556,7 +567,7 @@ __device__ void pull_level(const SsspArgs& a, int step, const uint32_t* vcur, ui
             f2[k] = make_int2(-1, -1);
             db[k] = de[k] = 0;
             if ((cmask >> k) & 1u) {
-                const int v = ((w0 + k * nw) << 5) + lane;
+                const int v = ((w0 + k) << 5) + lane;
                 f2[k] = __ldg(a.first2 + v);
                 db[k] = __ldg(a.row_ptr + v);
                 de[k] = __ldg(a.row_ptr + v + 1);
@@ -573,8 +584,8 @@ __device__ void pull_level(const SsspArgs& a, int step, const uint32_t* vcur, ui
         int nopen = 0;  // warp-uniform
 #pragma unroll
         for (int k = 0; k < kPullChunk; ++k) {
-            const int w = w0 + k * nw;
-            if (w >= a.nwords) continue;  // warp-uniform
+            const int w = w0 + k;
+            if (w >= wend) continue;  // warp-uniform
             const int v = (w << 5) + lane;
             const bool f = (fmask >> k) & 1u;
             const uint32_t newbits = __ballot_sync(kFull, f);
