@@ -525,6 +525,9 @@ __device__ void pull_level(const SsspArgs& a, int step, const uint32_t* vcur, ui
     const int R = (a.nwords + gridDim.x - 1) / gridDim.x;
     const int wbase = (int)min((long long)a.nwords, (long long)blockIdx.x * R);
     const int wend = min(a.nwords, wbase + R);
+    // chunks of up to kPullChunk words, fewer when the range is short, so
+    // that every warp of the CTA gets work
+    const int kc = max(1, min(kPullChunk, R / kWarps));
     if (threadIdx.x == 0) s_chunk = 0;
     if (kSmem) {
         const uint4* src4 = reinterpret_cast<const uint4*>(vcur);
@@ -535,8 +538,9 @@ __device__ void pull_level(const SsspArgs& a, int step, const uint32_t* vcur, ui
         int c = 0;
         if (lane == 0) c = atomicAdd(&s_chunk, 1);
         c = __shfl_sync(kFull, c, 0);
-        const int w0 = wbase + c * kPullChunk;
+        const int w0 = wbase + c * kc;
         if (w0 >= wend) break;  // warp-uniform
+        const int wlim = min(wend, w0 + kc);  // this chunk's words: [w0, wlim)
         // ---- pass 1: the first two in-neighbours of every candidate
         uint32_t cur[kPullChunk];
         unsigned cmask = 0;  // bit k: this lane's vertex of word k is a candidate
@@ -544,7 +548,7 @@ __device__ void pull_level(const SsspArgs& a, int step, const uint32_t* vcur, ui
         for (int k = 0; k < kPullChunk; ++k) {
             const int w = w0 + k;
             cur[k] = kFull;
-            if (w < wend) {
+            if (w < wlim) {
                 cur[k] = bm_word<kSmem>(vcur, w);
                 // candidates: not reached, and with at least one in-arc (excl
                 // also covers the padding bits past n).  excl is kept out of
@@ -557,7 +561,7 @@ __device__ void pull_level(const SsspArgs& a, int step, const uint32_t* vcur, ui
         if (!__any_sync(kFull, cmask)) {  // nothing to test: carry the words over
 #pragma unroll
             for (int k = 0; k < kPullChunk; ++k)
-                if (lane == 0 && w0 + k < wend) vnext[w0 + k] = cur[k];
+                if (lane == 0 && w0 + k < wlim) vnext[w0 + k] = cur[k];
             continue;
         }
         int2 f2[kPullChunk];
@@ -585,7 +589,7 @@ __device__ void pull_level(const SsspArgs& a, int step, const uint32_t* vcur, ui
 #pragma unroll
         for (int k = 0; k < kPullChunk; ++k) {
             const int w = w0 + k;
-            if (w >= wend) continue;  // warp-uniform
+            if (w >= wlim) continue;  // warp-uniform
             const int v = (w << 5) + lane;
             const bool f = (fmask >> k) & 1u;
             const uint32_t newbits = __ballot_sync(kFull, f);
