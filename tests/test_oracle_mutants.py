@@ -19,7 +19,8 @@ SRC = ROOT / "oracle" / "dawn_oracle.c"
 MUTANTS = {
     "sovm_wrong_stamp": ("beta[c] = 1;\n                    dist[c] = step;",
                          "beta[c] = 1;\n                    dist[c] = step + 1;"),
-    "sovm_no_swap": ("        alpha = beta;\n        beta = t;\n", "        (void)t;\n"),
+    "sovm_no_swap": ("(\"reset the vector by swap\") */\n        uint8_t* t = alpha;\n        alpha = beta;\n        beta = t;\n",
+                     "(\"reset the vector by swap\") */\n        uint8_t* t = alpha;\n        (void)t;\n"),
     "sovm_restamps_source": ("if (dist[c] == -1) {\n                    beta[c] = 1;",
                              "if (dist[c] <= 0) {\n                    beta[c] = 1;"),
     "bovm_merge_inside_loop": ("beta[i] = 1;\n                    dist[i] = step;",
