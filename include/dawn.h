@@ -237,8 +237,10 @@ DAWN_API int dawn_l2_read_gbs(int64_t bytes, int32_t passes, double* gbs, void* 
  *            the first negative index in dawn_last_error otherwise (g then
  *            has no weights until a valid set is given).
  * Replaces earlier weights.  The first call allocates the weighted path's
- * buffers (4m + 28n bytes); dawn_graph_free releases them.  Synchronizes
- * `stream`.
+ * buffers (about 12m + 33n bytes: the weights, a copy of the arcs with their
+ * weights interleaved, {head, weight} per arc, which the rounds read with one
+ * 8-byte load, and the round queues); dawn_graph_free releases them.
+ * Synchronizes `stream`.
  */
 DAWN_API int dawn_graph_set_weights(dawn_graph_t g, const int32_t* weights, void* stream);
 

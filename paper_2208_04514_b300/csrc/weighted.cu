@@ -56,6 +56,7 @@ struct alignas(128) WCtl {
 
 struct WeightedState {
     int32_t* w = nullptr;               // arc weights, aligned with col_idx
+    int2* cw = nullptr;                 // {col_idx, weight} per arc: one 8-byte load per offered arc
     int32_t* qv[2] = {nullptr, nullptr};  // frontier records: vertex
     int2* qe[2] = {nullptr, nullptr};     // {first arc, arc count}
     int32_t* qo[2] = {nullptr, nullptr};  // arc offset within the round
@@ -71,6 +72,7 @@ struct WArgs {
     const int32_t* __restrict__ row_ptr;
     const int32_t* __restrict__ col_idx;
     const int32_t* __restrict__ w;
+    const int2* __restrict__ cw;
     unsigned long long* dist;
     int32_t* qv[2];
     int2* qe[2];
@@ -322,8 +324,9 @@ __device__ void relax_round(const WArgs& a, int r, int qn, long long E, WSlot* o
         unsigned long long nd[kWGroup];
 #pragma unroll
         for (int q = 0; q < kWGroup; ++q) {
-            c[q] = j[q] >= 0 ? __ldg(a.col_idx + j[q]) : 0;
-            nd[q] = j[q] >= 0 ? odu[q] + (unsigned long long)(unsigned)__ldg(a.w + j[q]) : kNoPath;
+            const int2 t = j[q] >= 0 ? __ldg(a.cw + j[q]) : make_int2(0, 0);
+            c[q] = t.x;
+            nd[q] = j[q] >= 0 ? odu[q] + (unsigned long long)(unsigned)t.y : kNoPath;
         }
         unsigned long long cur[kWGroup];
 #pragma unroll
@@ -443,6 +446,12 @@ __global__ void __launch_bounds__(kWThreads, 2) wsssp_kernel(WArgs a) {
 }
 
 // First index j with w[j] < 0 (atomicMin over a 64-bit slot preset to ~0).
+__global__ void interleave_kernel(const int32_t* __restrict__ ci, const int32_t* __restrict__ w, long long m,
+                                  int2* __restrict__ cw) {
+    for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < m; j += (long long)gridDim.x * blockDim.x)
+        cw[j] = make_int2(ci[j], w[j]);
+}
+
 __global__ void negative_weight_kernel(const int32_t* __restrict__ w, long long m, unsigned long long* first) {
     for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < m; j += (long long)gridDim.x * blockDim.x)
         if (w[j] < 0) atomicMin(first, (unsigned long long)j);
@@ -466,6 +475,7 @@ int wsssp_launch(dawn_graph* g, int32_t src, int64_t* dist_dev, dawn_wsssp_stats
     a.row_ptr = g->row_ptr;
     a.col_idx = g->col_idx;
     a.w = s->w;
+    a.cw = s->cw;
     a.dist = reinterpret_cast<unsigned long long*>(dist_dev);
     for (int p = 0; p < 2; ++p) {
         a.qv[p] = s->qv[p];
@@ -495,6 +505,7 @@ void weighted_release(dawn_graph* g) {
     if (!s) return;
     auto f = [](void* p) { if (p) cudaFree(p); };
     f(s->w);
+    f(s->cw);
     for (int p = 0; p < 2; ++p) {
         f(s->qv[p]);
         f(s->qe[p]);
@@ -577,6 +588,9 @@ DAWN_API int dawn_graph_set_weights(dawn_graph_t g, const int32_t* weights, void
         s->w = nullptr;
         return fail(DAWN_E_INVALID, "weights[%llu] is negative", first_h);
     }
+    if (!s->cw) DAWN_CUDA_TRY(cudaMalloc((void**)&s->cw, sizeof(int2) * (size_t)g->m));
+    interleave_kernel<<<w_grid(g->m, g->sms), 256, 0, st>>>(g->col_idx, s->w, (long long)g->m, s->cw);
+    DAWN_CUDA_TRY(cudaGetLastError());
     return DAWN_OK;
 }
 
