@@ -381,3 +381,25 @@ def test_symmetric_components_stop_when_reached(dawn):
                 assert st["push_steps"] + st["pull_steps"] == st["levels"]
     finally:
         dawn.dawn_graph_free(h)
+
+
+@pytest.mark.parametrize("symmetric", [True, False])
+def test_pulls_against_a_bitmap_in_global_memory(dawn, symmetric):
+    """n = 2^21: the visited bitmap (256 KB) is larger than a CTA copies into
+    shared memory, so the pull levels test in-neighbours against the bitmap
+    in global memory, the other pull path.  RMAT scale 21, edge factor 4,
+    symmetric and directed, AUTO and pull only, against the oracle."""
+    g = gg.rmat(21, edge_factor=4, seed=12, symmetrise=symmetric)
+    assert (g.n + 31) // 32 * 4 > 200 * 1024
+    h = upload(dawn, g)
+    try:
+        for src in gg.sample_sources(g, 3, seed=21):
+            want = oracle.sssp_sovm(g.row_ptr, g.col_idx, int(src))
+            for opts in ({"mode": 0, "engine": 1}, {"mode": 2, "engine": 1}):
+                d, st = gpu_sssp(dawn, h, g.n, int(src), opts)
+                np.testing.assert_array_equal(d, want, err_msg=f"src={src} opts={opts}")
+                check_stats(g, d, st)
+                if opts["mode"] == 2:
+                    assert st["pull_steps"] >= 1 and st["push_steps"] == 0
+    finally:
+        dawn.dawn_graph_free(h)
