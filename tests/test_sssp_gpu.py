@@ -4,8 +4,9 @@ oracle, element by element.  Distances are integers: the bar is bit-exact.
 Sizes: tiny hand-derived and random digraphs (all three traversal modes),
 the 1024-vertex directed ER graph with sources 0-3, RMAT graphs of growing
 scale with isolated and hub sources, ragged n (not a multiple of 32),
-and at full size the RMAT scale-20 graph (sampled sources against Alg. 3,
-all 64 against the certificate) and the 4096^2 lattice (against Alg. 2).
+at full size the RMAT scale-20 graph (sampled sources against Alg. 3, all
+64 against the certificate) and the 4096^2 lattice (against Alg. 2), and
+RMAT scale 21, whose pulls test against the bitmap in global memory.
 """
 import numpy as np
 import pytest
