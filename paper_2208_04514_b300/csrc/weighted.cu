@@ -286,6 +286,13 @@ __device__ void relax_round(const WArgs& a, int r, int qn, long long E, WSlot* o
     int* bv = s_wbuf_v[threadIdx.x >> 5];
     int2* be = s_wbuf_e[threadIdx.x >> 5];
     int nbuf = 0;  // warp-uniform
+    // the record holding the last arc of the window before (warp-uniform):
+    // its arcs [c_lo, c_hi) of the round's list start at col_idx[c_ost], and
+    // its vertex's distance is c_du.  A window inside it (a long row) needs
+    // no search.
+    int c_lo = 1, c_hi = 0;  // arc offsets within a round stay below 2^31
+    int c_ost = 0;
+    unsigned long long c_du = 0;
     for (long long gb = a0; gb < a1; gb += 32 * kWGroup) {
         int j[kWGroup];
         unsigned long long odu[kWGroup];
@@ -295,10 +302,16 @@ __device__ void relax_round(const WArgs& a, int r, int qn, long long E, WSlot* o
             j[q] = -1;
             odu[q] = 0;
             if (wb >= a1) continue;  // warp-uniform
-            // keep the batch covering the window [wb, min(wb + 31, a1 - 1)]:
-            // if its last arc lies past the batch's last record, restart the
-            // batch at the record holding wb
             const long long last = min(wb + 31, a1 - 1);
+            const long long t = wb + lane;
+            if (wb >= (long long)c_lo && last < (long long)c_hi) {  // warp-uniform
+                odu[q] = c_du;
+                if (t < a1) j[q] = c_ost + (int)(t - c_lo);
+                continue;
+            }
+            // keep the batch covering the window [wb, last]: if its last arc
+            // lies past the batch's last record, restart the batch at the
+            // record holding wb
             const int off31 = __shfl_sync(kWFull, off, 31);
             const int len31 = __shfl_sync(kWFull, e.y, 31);
             if (bstart + 32 < qn && last >= (long long)off31 + len31) {
@@ -308,7 +321,6 @@ __device__ void relax_round(const WArgs& a, int r, int qn, long long E, WSlot* o
                 bstart += k;
                 load(bstart);
             }
-            const long long t = wb + lane;
             int o = 0;
 #pragma unroll
             for (int b = 16; b > 0; b >>= 1) {
@@ -319,6 +331,12 @@ __device__ void relax_round(const WArgs& a, int r, int qn, long long E, WSlot* o
             const int ooff = __shfl_sync(kWFull, off, o);
             odu[q] = __shfl_sync(kWFull, du, o);
             if (t < a1) j[q] = ost + (int)(t - ooff);
+            // remember the record of the window's last arc
+            const int ol = __shfl_sync(kWFull, o, (int)(last - wb));
+            c_ost = __shfl_sync(kWFull, e.x, ol);
+            c_lo = __shfl_sync(kWFull, off, ol);
+            c_hi = c_lo + __shfl_sync(kWFull, e.y, ol);
+            c_du = __shfl_sync(kWFull, du, ol);
         }
         int c[kWGroup];
         unsigned long long nd[kWGroup];
