@@ -11,6 +11,13 @@
 // in-adjacency (the CSR itself for symmetric graphs).  When its rows are in
 // ascending order (checked at upload) a row scan stops at the first
 // qualifying arc; otherwise every in-arc of every reached vertex is read.
+//
+// Level 2 goes the other way.  Its predecessors are the source's
+// out-neighbours, usually few, while on skewed graphs its vertices include
+// hubs.  A hub would scan thousands of in-arcs to meet the smallest of those
+// few, so the out-rows of the level-1 vertices are pushed instead: every arc
+// (u, v) with d(u) = 1 and d(v) = 2 takes an atomic minimum on parent[v].  It
+// is the same minimum, reached from the other end of the arcs.
 #include <algorithm>
 
 #include "dawn_internal.cuh"
@@ -23,6 +30,7 @@ constexpr int kTreeSerial = 8;      // arcs a thread tests by itself
 constexpr int kTreeWarpMax = 512;   // rows with more arcs left are scanned by the whole CTA
 constexpr int kTreeHeavyMax = 64;   // such rows per CTA and round
 constexpr unsigned kNone = 0xffffffffu;
+constexpr int kTreePushMax = 2048;  // source rows up to this long push level 2
 
 // One thread per vertex.  A vertex at level 1 hangs on the source (the only
 // vertex at level 0).  Otherwise the thread tests the first kTreeSerial arcs
@@ -31,10 +39,83 @@ constexpr unsigned kNone = 0xffffffffu;
 // when more than kTreeWarpMax are left.  With rows in ascending order the
 // first qualifying arc is the smallest, so a scan stops at the first step
 // that finds one; otherwise the whole row is read.
+// Level 2 by push: the out-arcs of the source row's vertices (k of them, the
+// arcs [srb, srb + k) of col_idx) split evenly over the grid.  Every CTA
+// builds the offsets of those rows in shared memory; vertices other than
+// level 1 (the source itself on a self-loop) contribute no arcs.  parent is
+// -1 (all bits set) on entry, so the atomic minimum over unsigned values
+// keeps the smallest predecessor.
+__global__ void __launch_bounds__(kTreeThreads, 1) push_level2_kernel(const int32_t* __restrict__ row_ptr,
+                                                                      const int32_t* __restrict__ col_idx,
+                                                                      const int32_t* __restrict__ dist,
+                                                                      int32_t* parent, int srb, int k) {
+    __shared__ long long s_off[kTreePushMax + 1];
+    __shared__ int s_u[kTreePushMax], s_rb[kTreePushMax];
+    __shared__ long long s_part[kTreeThreads / 32];
+    const unsigned kFull = 0xffffffffu;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    constexpr int kPer = kTreePushMax / kTreeThreads;  // rows per thread, consecutive
+    long long mine[kPer];
+    long long sum = 0;
+#pragma unroll
+    for (int q = 0; q < kPer; ++q) {
+        const int i = threadIdx.x * kPer + q;
+        mine[q] = 0;
+        if (i < k) {
+            const int u = col_idx[srb + i];
+            const int rb = row_ptr[u];
+            s_u[i] = u;
+            s_rb[i] = rb;
+            if (dist[u] == 1) mine[q] = row_ptr[u + 1] - rb;
+        }
+        sum += mine[q];
+    }
+    // exclusive offsets over the CTA: warp scans, then the warps' totals
+    long long incl = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const long long y = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) s_part[w] = incl;
+    __syncthreads();
+    if (w == 0) {
+        long long x = s_part[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const long long y = __shfl_up_sync(kFull, x, o);
+            if (lane >= o) x += y;
+        }
+        s_part[lane] = x;  // inclusive totals of warps 0..lane
+    }
+    __syncthreads();
+    long long off = (w > 0 ? s_part[w - 1] : 0) + incl - sum;
+#pragma unroll
+    for (int q = 0; q < kPer; ++q) {
+        const int i = threadIdx.x * kPer + q;
+        if (i < k) s_off[i] = off;
+        off += mine[q];
+    }
+    if (threadIdx.x == kTreeThreads - 1) s_off[k] = off;
+    __syncthreads();
+    const long long T = s_off[k];
+    for (long long t = (long long)blockIdx.x * kTreeThreads + threadIdx.x; t < T;
+         t += (long long)gridDim.x * kTreeThreads) {
+        int lo = 0, hi = k;  // the last row i with s_off[i] <= t
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (s_off[mid] <= t) lo = mid;
+            else hi = mid;
+        }
+        const int v = col_idx[s_rb[lo] + (int)(t - s_off[lo])];
+        if (dist[v] == 2) atomicMin(reinterpret_cast<unsigned*>(parent) + v, (unsigned)s_u[lo]);
+    }
+}
+
 __global__ void __launch_bounds__(kTreeThreads, 2) parent_kernel(const int32_t* __restrict__ in_ptr,
                                                                  const int32_t* __restrict__ in_idx,
                                                                  const int32_t* __restrict__ dist, int32_t* parent,
-                                                                 int32_t n, int32_t src, int sorted) {
+                                                                 int32_t n, int32_t src, int sorted, int level2_done) {
     const unsigned kFull = 0xffffffffu;
     __shared__ int s_hcount;
     __shared__ int s_hv[kTreeHeavyMax], s_hj[kTreeHeavyMax], s_hie[kTreeHeavyMax], s_hd[kTreeHeavyMax];
@@ -51,9 +132,10 @@ __global__ void __launch_bounds__(kTreeThreads, 2) parent_kernel(const int32_t* 
         unsigned best = kNone;  // smallest qualifying predecessor found so far
         bool done = true;
         int j = 0, ie = 0;
+        const bool pushed = level2_done && d == 2;  // set by push_level2_kernel
         if (d == 1) {
             best = (unsigned)src;
-        } else if (d > 1) {
+        } else if (d > 1 && !pushed) {
             const int ib = in_ptr[v];
             ie = in_ptr[v + 1];
             const int jl = min(ie, ib + kTreeSerial);
@@ -117,7 +199,7 @@ __global__ void __launch_bounds__(kTreeThreads, 2) parent_kernel(const int32_t* 
                 if (stop) break;
             }
         }
-        if (valid && !heavy) parent[v] = best == kNone ? -1 : (int)best;
+        if (valid && !heavy && !pushed) parent[v] = best == kNone ? -1 : (int)best;
         if (threadIdx.x < nh) parent[s_hv[threadIdx.x]] = s_hbest[threadIdx.x] == kNone ? -1 : (int)s_hbest[threadIdx.x];
         __syncthreads();
         if (threadIdx.x == 0) s_hcount = 0;
@@ -131,8 +213,16 @@ int tree_pass(dawn_graph* g, int32_t src, const int32_t* dist_dev, int32_t* pare
     if (g->n == 0) return DAWN_OK;
     const long long want = ((long long)g->n + kTreeThreads - 1) / kTreeThreads;
     const int blocks = (int)std::min<long long>(want, 2LL * g->sms);
+    const int srb = g->row_ptr_host[src];
+    const int k = g->row_ptr_host[src + 1] - srb;
+    const int push = k > 0 && k <= kTreePushMax;
+    if (push) {
+        DAWN_CUDA_TRY(cudaMemsetAsync(parent_dev, 0xff, sizeof(int32_t) * (size_t)g->n, st));
+        push_level2_kernel<<<g->sms, kTreeThreads, 0, st>>>(g->row_ptr, g->col_idx, dist_dev, parent_dev, srb, k);
+        DAWN_CUDA_TRY(cudaGetLastError());
+    }
     parent_kernel<<<blocks, kTreeThreads, 0, st>>>(g->in_ptr, g->in_idx, dist_dev, parent_dev, g->n, src,
-                                                   g->in_sorted);
+                                                   g->in_sorted, push);
     DAWN_CUDA_TRY(cudaGetLastError());
     return DAWN_OK;
 }
