@@ -42,9 +42,9 @@ constexpr int kTreePushMax = 2048;  // source rows up to this long push level 2
 // Level 2 by push: the out-arcs of the source row's vertices (k of them, the
 // arcs [srb, srb + k) of col_idx) split evenly over the grid.  Every CTA
 // builds the offsets of those rows in shared memory; vertices other than
-// level 1 (the source itself on a self-loop) contribute no arcs.  parent is
-// -1 (all bits set) on entry, so the atomic minimum over unsigned values
-// keeps the smallest predecessor.
+// level 1 (the source itself on a self-loop) contribute no arcs.  It runs
+// after parent_kernel, which leaves -1 (all bits set) at level 2, so the
+// atomic minimum over unsigned values keeps the smallest predecessor.
 __global__ void __launch_bounds__(kTreeThreads, 1) push_level2_kernel(const int32_t* __restrict__ row_ptr,
                                                                       const int32_t* __restrict__ col_idx,
                                                                       const int32_t* __restrict__ dist,
@@ -132,7 +132,7 @@ __global__ void __launch_bounds__(kTreeThreads, 2) parent_kernel(const int32_t* 
         unsigned best = kNone;  // smallest qualifying predecessor found so far
         bool done = true;
         int j = 0, ie = 0;
-        const bool pushed = level2_done && d == 2;  // set by push_level2_kernel
+        const bool pushed = level2_done && d == 2;  // -1 here, then push_level2_kernel
         if (d == 1) {
             best = (unsigned)src;
         } else if (d > 1 && !pushed) {
@@ -199,7 +199,7 @@ __global__ void __launch_bounds__(kTreeThreads, 2) parent_kernel(const int32_t* 
                 if (stop) break;
             }
         }
-        if (valid && !heavy && !pushed) parent[v] = best == kNone ? -1 : (int)best;
+        if (valid && !heavy) parent[v] = best == kNone || pushed ? -1 : (int)best;
         if (threadIdx.x < nh) parent[s_hv[threadIdx.x]] = s_hbest[threadIdx.x] == kNone ? -1 : (int)s_hbest[threadIdx.x];
         __syncthreads();
         if (threadIdx.x == 0) s_hcount = 0;
@@ -216,13 +216,12 @@ int tree_pass(dawn_graph* g, int32_t src, const int32_t* dist_dev, int32_t* pare
     const int srb = g->row_ptr_host[src];
     const int k = g->row_ptr_host[src + 1] - srb;
     const int push = k > 0 && k <= kTreePushMax;
-    if (push) {
-        DAWN_CUDA_TRY(cudaMemsetAsync(parent_dev, 0xff, sizeof(int32_t) * (size_t)g->n, st));
-        push_level2_kernel<<<g->sms, kTreeThreads, 0, st>>>(g->row_ptr, g->col_idx, dist_dev, parent_dev, srb, k);
-        DAWN_CUDA_TRY(cudaGetLastError());
-    }
     parent_kernel<<<blocks, kTreeThreads, 0, st>>>(g->in_ptr, g->in_idx, dist_dev, parent_dev, g->n, src,
                                                    g->in_sorted, push);
+    if (push) {
+        DAWN_CUDA_TRY(cudaGetLastError());
+        push_level2_kernel<<<g->sms, kTreeThreads, 0, st>>>(g->row_ptr, g->col_idx, dist_dev, parent_dev, srb, k);
+    }
     DAWN_CUDA_TRY(cudaGetLastError());
     return DAWN_OK;
 }
