@@ -146,7 +146,8 @@ __device__ __forceinline__ void red_release_add(unsigned* p, unsigned v) {
 // another CTA reported a failure.  `target` lives in thread 0.  With `snap`,
 // thread 0 also reads that counter slot after the acquire and leaves
 // {qpack, nf, mf, nc, lr} in s_snap for the whole CTA: one L2 request per CTA
-// instead of one per warp on a single hot line.
+// instead of one per warp on a single hot line (and likewise snap2 into
+// s_snap2, read with it).
 struct NoStep {
     __device__ void operator()() const {}
 };
@@ -156,7 +157,8 @@ struct NoStep {
 template <typename After = NoStep>
 __device__ bool grid_barrier(Ctl* ctl, unsigned* count, unsigned& target, long long spin_limit,
                              const CtrSlot* snap = nullptr, unsigned long long* s_snap = nullptr,
-                             After after = After()) {
+                             After after = After(), const CtrSlot* snap2 = nullptr,
+                             unsigned long long* s_snap2 = nullptr) {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -179,6 +181,13 @@ __device__ bool grid_barrier(Ctl* ctl, unsigned* count, unsigned& target, long l
             s_snap[2] = ld_relaxed_u64(&snap->mf);
             s_snap[3] = ld_relaxed_u64(&snap->nc);
             s_snap[4] = ld_relaxed_u64(&snap->lr);
+            if (snap2) {  // a second level's slot (the fused levels 1 and 2)
+                s_snap2[0] = ld_relaxed_u64(&snap2->qpack);
+                s_snap2[1] = ld_relaxed_u64(&snap2->nf);
+                s_snap2[2] = ld_relaxed_u64(&snap2->mf);
+                s_snap2[3] = ld_relaxed_u64(&snap2->nc);
+                s_snap2[4] = ld_relaxed_u64(&snap2->lr);
+            }
             after();
         }
         s_ok = ok;
@@ -244,6 +253,31 @@ __device__ __forceinline__ void flush_counts(long long nf, long long mf, CtrSlot
             if (a) atomicAdd(&out->nf, (unsigned long long)a);
             if (b) atomicAdd(&out->mf, (unsigned long long)b);
             if (s_cn && *s_cn) atomicAdd(&out->nc, (unsigned long long)*s_cn);
+        }
+    }
+}
+
+// flush_counts for two levels at once (the fused levels 1 and 2).
+__device__ __forceinline__ void flush_counts_two(long long nf1, long long mf1, CtrSlot* out1, long long nf2,
+                                                 long long mf2, CtrSlot* out2) {
+    __shared__ long long s_c[4][kWarps];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    long long v[4] = {nf1, mf1, nf2, mf2};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(kFull, v[k], o);
+        if (lane == 0) s_c[k][w] = v[k];
+    }
+    __syncthreads();
+    if (w == 0) {
+        unsigned long long* dst[4] = {&out1->nf, &out1->mf, &out2->nf, &out2->mf};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            long long x = s_c[k][lane];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(kFull, x, o);
+            if (lane == 0 && x) atomicAdd(dst[k], (unsigned long long)x);
         }
     }
 }
@@ -843,11 +877,41 @@ __device__ void bitmap_to_queue(const SsspArgs& a, const uint32_t* vnow, const u
     }
 }
 
-// Init and level 1 together (see the kernel): clear this CTA's vertex range,
-// then claim the source's out-neighbours inside it and queue their rows.
-// Must be reached by the whole CTA.
-__device__ __noinline__ void fused_init_level1(const SsspArgs& a, int srb, int sdeg, CtrSlot* out) {
-    const int lane = threadIdx.x & 31;
+// Largest arc total T of the source's out-neighbours' rows for which every
+// CTA runs level 2 itself (fused_init_levels); 0 turns the fused level 2 off.
+#ifndef DAWN_FUSE2_MAX_ARCS
+#define DAWN_FUSE2_MAX_ARCS 16384
+#endif
+// Largest CTA vertex range (bitmap words) the fused level 2 keeps in shared memory.
+constexpr int kFuse2Words = kWarps * kPullChunk * 32 - 2 * kThreads;
+// Arcs of the level-1 rows a thread reads per round of the fused level 2.
+#ifndef DAWN_FUSE2_UNROLL
+#define DAWN_FUSE2_UNROLL 8
+#endif
+constexpr int kFuse2Unroll = DAWN_FUSE2_UNROLL;
+
+// Init and the first levels together (see the kernel).  Every CTA clears a
+// contiguous vertex range of its own, and meanwhile reads the whole source
+// row (the level-1 vertices, one per thread) with each one's row bounds; the
+// level-1 rows hold T arcs in all (a CTA-wide scan, the same in every CTA).
+//
+// T small (at most DAWN_FUSE2_MAX_ARCS, and the direction rule pushes level
+// 2 anyway): every CTA runs level 2 for its own range as well.  A level-2
+// vertex is a target of a level-1 row that is neither the source nor a
+// level-1 vertex, which a CTA can decide for the vertices of its own range
+// from the source row alone, so no grid barrier separates levels 1 and 2:
+// the CTA claims its level-1 vertices in a shared-memory copy of its bitmap
+// words, then reads all T arcs of the level-1 rows (the same lines in every
+// CTA, from L2 after the first reader) and claims the targets in its range
+// there too; the claim that sets a bit first reaches the vertex (dist = 2)
+// and queues its row for level 3.  Returns 2.
+//
+// Otherwise: level 1 alone (the claims in the CTA's range, their rows queued
+// for the level-2 push).  Returns 1.  Must be reached by the whole CTA.
+__device__ __noinline__ int fused_init_levels(const SsspArgs& a, int srb, int sdeg, CtrSlot* out1, CtrSlot* out2) {
+    __shared__ int s_wsum[kWarps];
+    __shared__ int s_T;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int32_t src = a.src;
     const bool d16 = (((uintptr_t)a.dist) & 15u) == 0;
     // ranges of a multiple of 128 vertices: whole int4 groups and bitmap words
@@ -869,19 +933,126 @@ __device__ __noinline__ void fused_init_level1(const SsspArgs& a, int srb, int s
         for (long long w = (v0 >> 5) + threadIdx.x; w < w1; w += kThreads)
             a.vis0[w] = (w == (src >> 5)) ? (1u << (src & 31)) : 0u;
     }
-    __syncthreads();
-    if (threadIdx.x == 0 && src >= v0 && src < v1) a.dist[src] = 0;
-    bool claimed = false;
+    // the level-1 vertex's row bounds (the loads wait for c, not for the clearing)
     int rb = 0, re = 0;
-    if (c >= v0 && c < v1) {
+    if (c >= 0) {
         rb = __ldg(a.row_ptr + c);
         re = __ldg(a.row_ptr + c + 1);
-        const uint32_t bit = 1u << (c & 31);
-        claimed = !(atomicOr(&a.vis0[c >> 5], bit) & bit);
-        if (claimed) a.dist[c] = 1;
     }
-    warp_enqueue(claimed, rb, re, lane, Queue{a.q1, a.q1off}, out);
-    flush_counts(claimed ? 1 : 0, claimed ? re - rb : 0, out);
+    // exclusive scan of the level-1 row lengths over the CTA: arc offsets and T
+    const int deg = re - rb;
+    const int incl = warp_inclusive_scan(deg, lane);
+    if (lane == 31) s_wsum[warp] = incl;
+    __syncthreads();  // also orders the clearing before the claims below
+    if (warp == 0) {
+        const int x = s_wsum[lane];
+        const int xi = warp_inclusive_scan(x, lane);
+        s_wsum[lane] = xi - x;
+        if (lane == 31) s_T = xi;
+    }
+    __syncthreads();
+    const int off = s_wsum[warp] + incl - deg;
+    const int T = s_T;
+    if (threadIdx.x == 0 && src >= v0 && src < v1) a.dist[src] = 0;
+    // the direction rule pushes level 2 (T bounds the arcs of the level-1 rows)
+    const bool push2 = a.mode == DAWN_MODE_PUSH || (long long)T * a.alpha <= a.m - sdeg - T;
+    // (a CTA claims at most min(T, its range) vertices: the claim list's bound)
+    const bool fuse2 = DAWN_FUSE2_MAX_ARCS > 0 && T >= 1 && T <= DAWN_FUSE2_MAX_ARCS && push2 &&
+                       per <= 32LL * kFuse2Words && min((long long)T, per) <= kPushBufBytes / 4;
+    if (!fuse2) {
+        bool claimed = false;
+        if (c >= v0 && c < v1 && c != src) {
+            const uint32_t bit = 1u << (c & 31);
+            claimed = !(atomicOr(&a.vis0[c >> 5], bit) & bit);
+            if (claimed) a.dist[c] = 1;
+        }
+        warp_enqueue(claimed, rb, re, lane, Queue{a.q1, a.q1off}, out1);
+        flush_counts(claimed ? 1 : 0, claimed ? re - rb : 0, out1);
+        return 1;
+    }
+    // ---- levels 1 and 2 in this CTA's range.  Shared memory: the level-1
+    // rows' arc offsets and first arcs, and the CTA's bitmap words (the
+    // pull's per-warp lists, idle until the first pull); the push's per-warp
+    // row buffers (the dynamic shared memory, idle until the first push).
+    int* s_off = &s_pull_open[0][0];
+    int* s_rb = s_off + kThreads;
+    uint32_t* s_vis = reinterpret_cast<uint32_t*>(s_rb + kThreads);
+    const long long wr0 = v0 >> 5;
+    const int nwr = (int)((v1 - v0 + 31) >> 5);  // v0 is a multiple of 128
+    for (int i = threadIdx.x; i < nwr; i += kThreads)
+        s_vis[i] = (wr0 + i == (src >> 5)) ? (1u << (src & 31)) : 0u;
+    s_off[threadIdx.x] = off;
+    s_rb[threadIdx.x] = rb;
+    __syncthreads();
+    long long nf1 = 0, mf1 = 0;
+    if (c >= v0 && c < v1) {
+        const uint32_t bit = 1u << (c & 31);
+        if (!(atomicOr(&s_vis[(c - v0) >> 5], bit) & bit)) {
+            a.dist[c] = 1;
+            nf1 = 1;
+            mf1 = deg;
+        }
+    }
+    __syncthreads();  // every level-1 vertex of the range is marked before level 2 tests it
+    // level 2, first pass: every arc of the level-1 rows, kFuse2Unroll per
+    // thread with their col_idx loads in flight together; the targets claimed
+    // in this CTA's range go to a list (in the push's row buffers, idle until
+    // the first push: at most T entries)
+    __shared__ int s_nclaim;
+    int* claims = reinterpret_cast<int*>(s_bitmap4);
+    if (threadIdx.x == 0) s_nclaim = 0;
+    for (int base = 0; base < T; base += kThreads * kFuse2Unroll) {  // CTA-uniform
+        int t[kFuse2Unroll];
+#pragma unroll
+        for (int q = 0; q < kFuse2Unroll; ++q) {
+            const int e = base + q * kThreads + threadIdx.x;
+            t[q] = -1;
+            if (e < T) {
+                // the level-1 row holding arc e: the last entry whose offset is <= e
+                int lo = 0, hi = sdeg;
+                while (hi - lo > 1) {
+                    const int mid = (lo + hi) >> 1;
+                    if (s_off[mid] <= e) lo = mid;
+                    else hi = mid;
+                }
+                t[q] = s_rb[lo] + (e - s_off[lo]);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < kFuse2Unroll; ++q) t[q] = t[q] >= 0 ? __ldg(a.col_idx + t[q]) : -1;
+#pragma unroll
+        for (int q = 0; q < kFuse2Unroll; ++q) {
+            if (t[q] >= v0 && t[q] < v1) {
+                const uint32_t bit = 1u << (t[q] & 31);
+                if (!(atomicOr(&s_vis[(t[q] - v0) >> 5], bit) & bit)) {
+                    a.dist[t[q]] = 2;
+                    claims[atomicAdd(&s_nclaim, 1)] = t[q];
+                }
+            }
+        }
+    }
+    __syncthreads();
+    // second pass: the claimed vertices' rows, queued for level 3
+    long long nf2 = 0, mf2 = 0;
+    const int ncl = s_nclaim;
+    const Queue q2{a.q0, a.q0off};  // the frontier found at level 2 lives in queue 0
+    for (int b = threadIdx.x & ~31; b < ncl; b += kThreads) {  // bound uniform over the warp
+        const int i = b + lane;
+        int rb2 = 0, re2 = 0;
+        if (i < ncl) {
+            const int t = claims[i];
+            rb2 = __ldg(a.row_ptr + t);
+            re2 = __ldg(a.row_ptr + t + 1);
+            nf2 += 1;
+            mf2 += re2 - rb2;
+        }
+        warp_enqueue(i < ncl, rb2, re2, lane, q2, out2);
+    }
+    __syncthreads();
+    // the CTA's bitmap words with both levels' claims (the clearing above wrote zeros)
+    for (int i = threadIdx.x; i < nwr; i += kThreads) a.vis0[wr0 + i] = s_vis[i];
+    flush_counts_two(nf1, mf1, out1, nf2, mf2, out2);
+    return 2;
 }
 
 // level kinds: push (SOVM), pull over the bitmap, pull over the candidate lists
@@ -991,10 +1162,12 @@ __global__ void __launch_bounds__(kThreads, DAWN_SSSP_MIN_CTAS) sssp_kernel(Sssp
     // push and the row fits one pass of the CTA: each CTA clears a contiguous
     // vertex range of its own and then claims the source's out-neighbours in
     // that range, so only __syncthreads orders the clearing before the claims
-    // and the first grid barrier already ends level 1.
+    // and the first grid barrier already ends level 1.  When the level-1 rows
+    // are short, level 2 joins it too (fused_init_levels): the first grid
+    // barrier then ends level 2.
     const bool fused = a.mode != DAWN_MODE_PULL && sdeg <= kThreads &&
                        (a.mode == DAWN_MODE_PUSH || (long long)sdeg * a.alpha <= a.m - sdeg);
-    // the loop starts after level 0 (the source), or after level 1 when fused
+    // the loop starts after level 0 (the source), or after level 1 (or 2) when fused
     int step = fused ? 1 : 0;
     if (threadIdx.x == 0) {
         L.mu = a.m - (fused ? sdeg : 0);
@@ -1015,14 +1188,31 @@ __global__ void __launch_bounds__(kThreads, DAWN_SSSP_MIN_CTAS) sssp_kernel(Sssp
     auto advance = [ra, snap, lp](int done_step) { next_level(ra, *lp, snap, done_step); };
     const bool d16 = (((uintptr_t)a.dist) & 15u) == 0;
     if (fused) {
-        fused_init_level1(a, srb, sdeg, &ctr[1]);  // ends with __syncthreads
+        const int levels = fused_init_levels(a, srb, sdeg, &ctr[1], &ctr[2]);  // ends with __syncthreads
         if (s_status != DEV_OK) return;
-        if (!grid_barrier(ctl, bar, bar_target, a.spin_limit, &ctr[1], s_snap, [advance]() { advance(1); })) return;
-        if (gtid == 0) ctl->bar[a.bar_parity ^ 1].count = 0;  // the next launch's counter
-        if (tracer) {
-            trace_rec(a, tslot, 1, 0, 1);
-            trace_rec(a, tslot, 2, 1, (long long)s_snap[1]);
+        if (levels == 2) {
+            // level 1's counts come with level 2's: the rule runs for both
+            __shared__ unsigned long long s_snap1[5];
+            unsigned long long* const snap1 = s_snap1;
+            if (!grid_barrier(ctl, bar, bar_target, a.spin_limit, &ctr[2], s_snap, [ra, snap, snap1, lp]() {
+                    next_level(ra, *lp, snap1, 1);
+                    if (lp->kind != kStop) next_level(ra, *lp, snap, 2);
+                }, &ctr[1], s_snap1))
+                return;
+            step = 2;
+            if (tracer) {
+                trace_rec(a, tslot, 1, 0, 1);
+                trace_rec(a, tslot, 2, 1, (long long)s_snap1[1]);
+                trace_rec(a, tslot, 2, 2, (long long)s_snap[1]);
+            }
+        } else {
+            if (!grid_barrier(ctl, bar, bar_target, a.spin_limit, &ctr[1], s_snap, [advance]() { advance(1); })) return;
+            if (tracer) {
+                trace_rec(a, tslot, 1, 0, 1);
+                trace_rec(a, tslot, 2, 1, (long long)s_snap[1]);
+            }
         }
+        if (gtid == 0) ctl->bar[a.bar_parity ^ 1].count = 0;  // the next launch's counter
     } else {
         if (d16) {
             int4* d4 = reinterpret_cast<int4*>(a.dist);
