@@ -64,7 +64,8 @@ extern "C" {
 
 /* ------------------------------------------------------------- graph flags */
 #define DAWN_DIRECTED    0u /* general digraph: the in-adjacency (CSC) is built on the device */
-#define DAWN_SYMMETRIC   1u /* caller asserts that every arc has its reverse: the CSR is its own CSC */
+#define DAWN_SYMMETRIC   1u /* every arc has its reverse (the arc multiset equals its reverse): the CSR is
+                               its own CSC; checked at upload, DAWN_E_INVALID naming a witness otherwise */
 
 /* --------------------------------------------------------- traversal modes */
 #define DAWN_MODE_AUTO   0 /* per level: SOVM push or BOVM pull, chosen from frontier counters */
@@ -104,7 +105,13 @@ typedef struct dawn_server* dawn_server_t;
  *   row_ptr  host or device, int32[n+1]; col_idx host or device, int32[m].
  *   n >= 1, 0 <= m < 2^31, flags = DAWN_DIRECTED or DAWN_SYMMETRIC.
  * The library validates the CSR on the device (DAWN_E_INVALID with the first
- * offending index in dawn_last_error), builds the in-adjacency for directed
+ * offending index in dawn_last_error).  With DAWN_SYMMETRIC it checks, in one
+ * O(n + m) device pass over two 64-bit hash sums, that the arc multiset equals
+ * its reverse (every arc (u, v) appears as often as (v, u); self-loops are
+ * their own reverse), and returns DAWN_E_INVALID naming an arc without a
+ * matching reverse (or, on rows of more than 4,096 arcs, the vertex) when it
+ * does not: such a graph must be uploaded as DAWN_DIRECTED.  It builds the
+ * in-adjacency for directed
  * graphs, a copy of the in-adjacency with each row ordered by the neighbours'
  * out-degree (largest first) and the first two entries of each such row, and
  * allocates the per-graph work buffers: about 4m + 45n bytes beyond the CSR

@@ -7,6 +7,8 @@
 #include <climits>
 #include <cstring>
 
+#include <algorithm>
+
 #include "dawn_internal.cuh"
 
 namespace dawn {
@@ -37,6 +39,107 @@ __global__ void validate_csr_kernel(const int32_t* __restrict__ rp, const int32_
     for (long long j = t0; j < m; j += stride) {
         int c = ci[j];
         if (c < 0 || c >= n) atomicMin(&bad[1], (unsigned long long)j);
+    }
+}
+
+// ---- symmetry of a graph uploaded as DAWN_SYMMETRIC.  The arc multiset must
+// equal its reverse (every arc (u, v) appears as often as (v, u)), since the
+// CSR then serves as its own in-adjacency.  One pass adds, over every arc,
+// h(u, v) - h(v, u) for two independent 64-bit hashes of the ordered pair
+// (mod 2^64): both sums are zero when the multisets are equal, and a graph
+// whose multisets differ leaves them both zero with probability about 2^-128.
+__device__ __forceinline__ unsigned long long pair_hash(unsigned long long x, unsigned long long seed) {
+    // the splitmix64 output function (a published 64-bit mixer) of the pair's key
+    x += seed;
+    x = (x ^ (x >> 30)) * 0xbf58476d1ce4e5b9ull;
+    x = (x ^ (x >> 27)) * 0x94d049bb133111ebull;
+    return x ^ (x >> 31);
+}
+constexpr unsigned long long kSymSeed1 = 0x9e3779b97f4a7c15ull, kSymSeed2 = 0x6a09e667f3bcc909ull;
+
+// One warp per row (lanes over its arcs); sums[0], sums[1] the two sums.
+__global__ void symmetry_sum_kernel(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci, int32_t n,
+                                    unsigned long long* sums) {
+    const int lane = threadIdx.x & 31;
+    const long long nw = (long long)gridDim.x * (blockDim.x >> 5);
+    unsigned long long s1 = 0, s2 = 0;
+    for (long long u = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < n; u += nw) {
+        for (int j = rp[u] + lane; j < rp[u + 1]; j += 32) {
+            const unsigned long long v = (unsigned)ci[j];
+            const unsigned long long fwd = ((unsigned long long)u << 32) | v, rev = (v << 32) | (unsigned long long)u;
+            s1 += pair_hash(fwd, kSymSeed1) - pair_hash(rev, kSymSeed1);
+            s2 += pair_hash(fwd, kSymSeed2) - pair_hash(rev, kSymSeed2);
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        s1 += __shfl_down_sync(0xffffffffu, s1, o);
+        s2 += __shfl_down_sync(0xffffffffu, s2, o);
+    }
+    if (lane == 0 && (s1 | s2)) {
+        atomicAdd(&sums[0], s1);
+        atomicAdd(&sums[1], s2);
+    }
+}
+
+// When the sums differ, find a witness: per vertex v, the hash sums of its
+// out-neighbours and of its in-neighbours (scattered from every arc) differ
+// for some v.  out_h[v] / in_h[v] start at zero.
+__global__ void symmetry_vertex_kernel(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci, int32_t n,
+                                       unsigned long long* out_h, unsigned long long* in_h) {
+    const int lane = threadIdx.x & 31;
+    const long long nw = (long long)gridDim.x * (blockDim.x >> 5);
+    for (long long u = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < n; u += nw) {
+        unsigned long long s = 0;
+        for (int j = rp[u] + lane; j < rp[u + 1]; j += 32) {
+            const int v = ci[j];
+            s += pair_hash((unsigned)v, kSymSeed1);
+            atomicAdd(&in_h[v], pair_hash((unsigned long long)u, kSymSeed1));
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        if (lane == 0) out_h[u] = s;
+    }
+}
+
+// The smallest vertex whose two sums differ (bad[0]); then, in a second
+// launch with that vertex, the smallest arc index j of its row whose head x
+// has fewer arcs back to it than the row has to x (bad[1]; a linear scan of
+// both rows, an error path only).
+__global__ void symmetry_witness_kernel(const unsigned long long* out_h, const unsigned long long* in_h, int32_t n,
+                                        unsigned long long* bad) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride)
+        if (out_h[v] != in_h[v]) atomicMin(&bad[0], (unsigned long long)v);
+}
+
+__global__ void symmetry_arc_kernel(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci, int v,
+                                    unsigned long long* bad) {
+    const int b = rp[v], e = rp[v + 1];
+    for (int j = b + (int)(blockIdx.x * blockDim.x + threadIdx.x); j < e; j += gridDim.x * blockDim.x) {
+        const int x = ci[j];
+        int fwd = 0, back = 0;
+        for (int k = b; k < e; ++k) fwd += ci[k] == x;
+        for (int k = rp[x]; k < rp[x + 1]; ++k) back += ci[k] == v;
+        if (back < fwd) atomicMin(&bad[1], (unsigned long long)j);
+    }
+}
+
+// No out-arc of v lacks its reverse: then an arc (y, v) into v does.  Every
+// row y is scanned for arcs into v (one warp per row); an arc j = (y, v) with
+// more copies in row y than arcs back from v to y is a witness (bad[1]).
+__global__ void symmetry_in_arc_kernel(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci, int32_t n,
+                                       int v, unsigned long long* bad) {
+    const int lane = threadIdx.x & 31;
+    const long long nw = (long long)gridDim.x * (blockDim.x >> 5);
+    for (long long y = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; y < n; y += nw) {
+        for (int j = rp[y] + lane; j < rp[y + 1]; j += 32) {
+            if (ci[j] != v) continue;
+            int fwd = 0, back = 0;
+            for (int k = rp[y]; k < rp[y + 1]; ++k) fwd += ci[k] == v;
+            for (int k = rp[v]; k < rp[v + 1]; ++k) back += ci[k] == (int)y;
+            if (back < fwd) atomicMin(&bad[1], (unsigned long long)j);
+        }
     }
 }
 
@@ -342,6 +445,79 @@ void release(dawn_graph* g) {
     delete g;
 }
 
+// DAWN_E_INVALID, naming a witness, when the graph's arc multiset differs
+// from its reverse (see symmetry_sum_kernel).
+int check_symmetric(dawn_graph* g, cudaStream_t st) {
+    unsigned long long* buf = nullptr;
+    unsigned long long h[2] = {0, 0};
+    cudaError_t e = cudaMallocAsync((void**)&buf, 2 * sizeof(unsigned long long), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(buf, 0, 2 * sizeof(unsigned long long), st);
+    if (e == cudaSuccess) {
+        symmetry_sum_kernel<<<grid_for((int64_t)g->n * 32, g->sms), kThreads, 0, st>>>(g->row_ptr, g->col_idx, g->n, buf);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h, buf, sizeof(h), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (buf) cudaFreeAsync(buf, st);
+    if (e != cudaSuccess) return cuda_fail(e, "symmetry check", __FILE__, __LINE__);
+    if (h[0] == 0 && h[1] == 0) return DAWN_OK;
+    // locate a witness (error path)
+    unsigned long long* vh = nullptr;
+    unsigned long long bad[2] = {ULLONG_MAX, ULLONG_MAX};
+    const size_t nb = sizeof(unsigned long long) * (size_t)g->n;
+    e = cudaMallocAsync((void**)&vh, 2 * nb + 2 * sizeof(unsigned long long), st);
+    unsigned long long* badd = vh ? vh + 2 * (size_t)g->n : nullptr;
+    if (e == cudaSuccess) e = cudaMemsetAsync(vh, 0, 2 * nb, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(badd, 0xff, 2 * sizeof(unsigned long long), st);
+    if (e == cudaSuccess) {
+        symmetry_vertex_kernel<<<grid_for((int64_t)g->n * 32, g->sms), kThreads, 0, st>>>(g->row_ptr, g->col_idx, g->n,
+                                                                                         vh, vh + g->n);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) {
+        symmetry_witness_kernel<<<grid_for(g->n, g->sms), kThreads, 0, st>>>(vh, vh + g->n, g->n, badd);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(bad, badd, sizeof(bad), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    int32_t vb[2] = {0, 0};
+    if (e == cudaSuccess && bad[0] != ULLONG_MAX)
+        e = cudaMemcpy(vb, g->row_ptr + bad[0], 2 * sizeof(int32_t), cudaMemcpyDeviceToHost);
+    // the arc search scans the row once per arc: only on rows of modest length
+    if (e == cudaSuccess && bad[0] != ULLONG_MAX && vb[1] - vb[0] <= 4096) {
+        symmetry_arc_kernel<<<8, kThreads, 0, st>>>(g->row_ptr, g->col_idx, (int)bad[0], badd);
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaMemcpyAsync(bad, badd, sizeof(bad), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    }
+    if (e == cudaSuccess && bad[0] != ULLONG_MAX && bad[1] == ULLONG_MAX && vb[1] - vb[0] <= 4096) {
+        symmetry_in_arc_kernel<<<grid_for((int64_t)g->n * 32, g->sms), kThreads, 0, st>>>(g->row_ptr, g->col_idx, g->n,
+                                                                                         (int)bad[0], badd);
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaMemcpyAsync(bad, badd, sizeof(bad), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    }
+    if (vh) cudaFreeAsync(vh, st);
+    if (e != cudaSuccess) return cuda_fail(e, "symmetry witness", __FILE__, __LINE__);
+    if (bad[1] != ULLONG_MAX) {
+        // the arc's tail: the row holding col_idx[bad[1]]
+        std::vector<int32_t> rp((size_t)g->n + 1);
+        int32_t x = -1;
+        long long y = -1;
+        if (cudaMemcpy(rp.data(), g->row_ptr, sizeof(int32_t) * rp.size(), cudaMemcpyDeviceToHost) == cudaSuccess &&
+            cudaMemcpy(&x, g->col_idx + bad[1], sizeof(int32_t), cudaMemcpyDeviceToHost) == cudaSuccess)
+            y = (long long)(std::upper_bound(rp.begin(), rp.end(), (int32_t)bad[1]) - rp.begin()) - 1;
+        return fail(DAWN_E_INVALID,
+                    "DAWN_SYMMETRIC: arc (%lld, %d) (col_idx[%llu]) has no matching reverse arc; upload it as DAWN_DIRECTED",
+                    y, x, bad[1]);
+    }
+    if (bad[0] != ULLONG_MAX)
+        return fail(DAWN_E_INVALID,
+                    "DAWN_SYMMETRIC: the arcs into vertex %llu differ from the arcs out of it; upload it as DAWN_DIRECTED",
+                    bad[0]);
+    return fail(DAWN_E_INVALID, "DAWN_SYMMETRIC: the arc multiset differs from its reverse; upload it as DAWN_DIRECTED");
+}
+
 int upload(const int32_t* row_ptr, const int32_t* col_idx, int32_t n, int64_t m, uint32_t flags,
            cudaStream_t st, dawn_graph** out) {
     dawn_graph* g = new dawn_graph();
@@ -387,6 +563,15 @@ int upload(const int32_t* row_ptr, const int32_t* col_idx, int32_t n, int64_t m,
     if (bad_h[1] != ULLONG_MAX) {
         release(g);
         return fail(DAWN_E_INVALID, "col_idx[%llu] is outside [0, n)", bad_h[1]);
+    }
+
+    // ---- a symmetric upload must be symmetric: the CSR stands in for the CSC
+    if ((flags & DAWN_SYMMETRIC) && m > 0) {
+        const int rc = check_symmetric(g, st);
+        if (rc != DAWN_OK) {
+            release(g);
+            return rc;
+        }
     }
 
     // ---- in-adjacency
