@@ -14,6 +14,12 @@
 // the vertices of its own slice.  Levels are separated by the hardware cluster
 // barrier.  A vertex is claimed once, at the first level an arc reaches it,
 // which is its distance (Thm 1).
+//
+// Many sources (dawn_sssp_many): a grid of several clusters, each taking the
+// next source from a device counter and running its level loop alone (its
+// own overflow lists), so independent searches fill the SMs one cluster
+// cannot; no cluster ever waits for another (Sec. 3.3: APSP as one SSSP per
+// source).
 #include <algorithm>
 #include <cooperative_groups.h>
 
@@ -30,9 +36,13 @@ constexpr int kClWarpRow = 32;  // longer rows are expanded by the whole warp
 struct ClArgs {
     const int32_t* __restrict__ row_ptr;
     const int32_t* __restrict__ col_idx;
-    int32_t* dist;
-    int32_t* ovf;          // 3 overflow lists of n entries (frontier of level L: list L % 3)
-    unsigned* ovf_n;       // their counts
+    int32_t* dist;         // many sources: row i of source srcs[i] at dist + i * dist_stride
+    int32_t* ovf;          // per cluster: 3 overflow lists of n entries (frontier of level L: list L % 3)
+    unsigned* ovf_n;       // per cluster: their counts (4 per cluster)
+    const int32_t* srcs;   // device, many sources (null: the single source src)
+    unsigned* next;        // many sources: the next index into srcs to take (zero at launch)
+    long long dist_stride;
+    int32_t k;
     const int* status;     // sticky status of the graph's control block
     dawn_sssp_stats* stats;
     int32_t n;
@@ -47,6 +57,7 @@ struct ClShared {
     int claims[2];         // vertices this CTA claimed at levels of each parity
     int cnt[2][16];        // every CTA's claims of the level, posted by the CTAs themselves
     int quit;
+    int task;              // many sources: the index of the source the cluster runs now
     long long edges[kClThreads / 32];
 };
 
@@ -75,31 +86,55 @@ __global__ void __launch_bounds__(kClThreads, 1) cluster_sssp_kernel(ClArgs a) {
     const int S = a.S;
     uint32_t* s_bm = cl_dyn;                                   // S words
     int* s_list[2] = {reinterpret_cast<int*>(cl_dyn + S), reinterpret_cast<int*>(cl_dyn + S) + a.qcap};
+    // this cluster's overflow lists and counts
+    const unsigned cid = blockIdx.x / C;
+    int32_t* const ovf = a.ovf + (long long)cid * 3 * a.n;
+    unsigned* const ovf_n = a.ovf_n + 4 * cid;
 
-    // an earlier failure on this graph leaves every later call idle (same in every CTA)
-    if (threadIdx.x == 0) sh.quit = *(volatile const int*)a.status != DEV_OK;
-    __syncthreads();
+  for (;;) {  // one source per pass: the single source, or the next of srcs
+    int32_t src = a.src;
+    int32_t* dist = a.dist;
+    dawn_sssp_stats* stats = a.stats;
+    // CTA 0 of the cluster takes the next source and reads the sticky status
+    // (an earlier failure on this graph leaves every later call idle), and
+    // posts both into every CTA of the cluster, so all decide alike
+    if (rank == 0 && threadIdx.x == 0) {
+        const int t = a.srcs ? (int)atomicAdd(a.next, 1u) : 0;
+        const int q = *(volatile const int*)a.status != DEV_OK;
+        for (unsigned r = 0; r < C; ++r) {
+            *cluster.map_shared_rank(&sh.task, r) = t;
+            *cluster.map_shared_rank(&sh.quit, r) = q;
+        }
+    }
+    cluster.sync();
     if (sh.quit) return;
+    if (a.srcs) {
+        const int t = sh.task;
+        if (t >= a.k) break;
+        src = __ldg(a.srcs + t);
+        dist = a.dist + (long long)t * a.dist_stride;
+        stats = a.stats ? a.stats + t : nullptr;
+    }
 
     // ---- init: bitmap slice 0, distances -1 (each CTA its share), source
     for (int i = threadIdx.x; i < S; i += kClThreads) s_bm[i] = 0u;
     const long long chunk = ((long long)a.n + C - 1) / C;
     const long long lo = (long long)rank * chunk, hi = min((long long)a.n, lo + chunk);
-    for (long long v = lo + threadIdx.x; v < hi; v += kClThreads) a.dist[v] = -1;
+    for (long long v = lo + threadIdx.x; v < hi; v += kClThreads) dist[v] = -1;
     if (threadIdx.x == 0) {
         sh.qn[0] = sh.qn[1] = 0;
         sh.claims[0] = sh.claims[1] = 0;
-        if (rank == 0) a.ovf_n[0] = a.ovf_n[1] = a.ovf_n[2] = 0u;
+        if (rank == 0) ovf_n[0] = ovf_n[1] = ovf_n[2] = 0u;
     }
     __syncthreads();
-    const int sw = a.src >> 5;
+    const int sw = src >> 5;
     const unsigned sowner = (unsigned)(sw / S);
     if (threadIdx.x == 0 && rank == sowner) {
-        s_bm[sw - (int)sowner * S] = 1u << (a.src & 31);
-        s_list[0][0] = a.src;
+        s_bm[sw - (int)sowner * S] = 1u << (src & 31);
+        s_list[0][0] = src;
         sh.qn[0] = 1;
     }
-    if (threadIdx.x == 0 && a.src >= lo && a.src < hi) a.dist[a.src] = 0;
+    if (threadIdx.x == 0 && src >= lo && src < hi) dist[src] = 0;
     long long edges = 0;
     long long reached = 1;
     int levels = 0;
@@ -111,17 +146,17 @@ __global__ void __launch_bounds__(kClThreads, 1) cluster_sssp_kernel(ClArgs a) {
         const int qn_all = sh.qn[pc];
         const int own = min(qn_all, a.qcap);
         // plus its share of the frontier that spilled to the overflow list
-        const int32_t* ovf_cur = a.ovf + (long long)((level - 1) % 3) * a.n;
-        const unsigned on = __ldcg(a.ovf_n + (level - 1) % 3);
+        const int32_t* ovf_cur = ovf + (long long)((level - 1) % 3) * a.n;
+        const unsigned on = __ldcg(ovf_n + (level - 1) % 3);
         const long long olo = (long long)on * rank / C, ohi = (long long)on * (rank + 1) / C;
-        int32_t* ovf_next = a.ovf + (long long)(level % 3) * a.n;
-        unsigned* ovf_next_n = a.ovf_n + level % 3;
+        int32_t* ovf_next = ovf + (long long)(level % 3) * a.n;
+        unsigned* ovf_next_n = ovf_n + level % 3;
         const int items = own + (int)(ohi - olo);
         __syncthreads();  // every thread has read this list's count
         if (threadIdx.x == 0) {
             sh.qn[pc] = 0;      // appended to again at the next level, after the barrier
             sh.claims[pc] = 0;
-            if (rank == 0) a.ovf_n[(level + 1) % 3] = 0u;  // used from the next level on
+            if (rank == 0) ovf_n[(level + 1) % 3] = 0u;  // used from the next level on
         }
         int my_claims = 0;
         // one frontier vertex per thread and round; the loop bound is the same for the whole warp
@@ -165,7 +200,7 @@ __global__ void __launch_bounds__(kClThreads, 1) cluster_sssp_kernel(ClArgs a) {
                 int ltot = 0;
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
-                    if (won[q]) a.dist[x[q]] = level;
+                    if (won[q]) dist[x[q]] = level;
                     my_claims += won[q];
                     lb[q] = __ballot_sync(kFull, won[q] && owner[q] == rank);
                     ltot += __popc(lb[q]);
@@ -202,7 +237,7 @@ __global__ void __launch_bounds__(kClThreads, 1) cluster_sssp_kernel(ClArgs a) {
                     const uint32_t bit = 1u << (x & 31);
                     uint32_t* word = (ow == rank ? s_bm : cluster.map_shared_rank(s_bm, ow)) + (w - (int)ow * S);
                     if ((atomicOr(word, bit) & bit) == 0u) {
-                        a.dist[x] = level;
+                        dist[x] = level;
                         ++my_claims;
                         cl_append(cluster, ow, rank, x, s_list[pn], &sh.qn[pn], ovf_next, ovf_next_n, a.qcap);
                     }
@@ -237,7 +272,7 @@ __global__ void __launch_bounds__(kClThreads, 1) cluster_sssp_kernel(ClArgs a) {
         sh.edges[0] = e;
     }
     cluster.sync();  // every CTA's total is in place
-    if (rank == 0 && threadIdx.x == 0 && a.stats) {
+    if (rank == 0 && threadIdx.x == 0 && stats) {
         long long e = 0;
         for (unsigned r = 0; r < C; ++r) e += *cluster.map_shared_rank(&sh.edges[0], r);
         dawn_sssp_stats s;
@@ -247,83 +282,96 @@ __global__ void __launch_bounds__(kClThreads, 1) cluster_sssp_kernel(ClArgs a) {
         s.reserved = 0;
         s.reached = reached;
         s.edges = e;
-        *a.stats = s;
+        *stats = s;
     }
-    cluster.sync();  // no CTA leaves while its shared memory may still be read
+    cluster.sync();  // no CTA leaves (or starts over) while its shared memory may still be read
+    if (!a.srcs) break;
+  }
 }
 
 }  // namespace
 
-int cluster_launch(dawn_graph* g, int32_t src, int32_t* dist_dev, const dawn_sssp_opts* opts,
-                   dawn_sssp_stats* stats_dev, cudaStream_t st) {
-    if (opts && (opts->mode == DAWN_MODE_PULL || opts->trace))
-        return fail(DAWN_E_INVALID, "the cluster engine runs SOVM push only, without a trace");
-    if (g->cl_size == 0) {
-        // set up once: the largest cluster (16, else 8) whose CTAs can hold the
-        // bitmap slice and two frontier lists, and that the device can place
-        g->cl_size = -1;
-        int dev_smem = 0;
-        DAWN_CUDA_TRY(cudaDeviceGetAttribute(&dev_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, g->device));
-        DAWN_CUDA_TRY(cudaFuncSetAttribute(cluster_sssp_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
-        // the dynamic shared memory limit belongs to the kernel, not to the graph:
-        // raise it once to all the kernel can take, so that graphs set up later
-        // never lower it under an earlier graph's launches
-        cudaFuncAttributes fa;
-        DAWN_CUDA_TRY(cudaFuncGetAttributes(&fa, cluster_sssp_kernel));
-        const int dyn_max = dev_smem - (int)fa.sharedSizeBytes;
-        DAWN_CUDA_TRY(cudaFuncSetAttribute(cluster_sssp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_max));
-        for (int C : {16, 8}) {
-            const long long S = ((long long)g->nwords + C - 1) / C;
-            const long long room = (long long)dev_smem - (long long)sizeof(ClShared) - 1024 - S * 4;
-            const long long qcap = std::min<long long>(8192, room / 8);
-            if (qcap < 1024) continue;
-            const int smem = (int)(S * 4 + qcap * 8);
-            if (smem > dyn_max) continue;
-            cudaLaunchConfig_t cfg = {};
-            cudaLaunchAttribute attr[1];
-            attr[0].id = cudaLaunchAttributeClusterDimension;
-            attr[0].val.clusterDim.x = C;
-            attr[0].val.clusterDim.y = 1;
-            attr[0].val.clusterDim.z = 1;
-            cfg.gridDim = dim3(C);
-            cfg.blockDim = dim3(kClThreads);
-            cfg.dynamicSmemBytes = smem;
-            cfg.attrs = attr;
-            cfg.numAttrs = 1;
-            int nclusters = 0;
-            if (cudaOccupancyMaxActiveClusters(&nclusters, cluster_sssp_kernel, &cfg) != cudaSuccess) {
-                cudaGetLastError();
-                continue;
-            }
-            if (nclusters < 1) continue;
-            g->cl_size = C;
-            g->cl_smem = smem;
-            g->cl_qcap = (int)qcap;
-            break;
+namespace {
+
+// Set up once per graph: the largest cluster (16 CTAs, else 8) whose CTAs can
+// hold the bitmap slice and two frontier lists and that the device can place,
+// and how many such clusters fit on the device at once.  DAWN_E_INVALID when
+// none can.
+int cluster_setup(dawn_graph* g) {
+    if (g->cl_size != 0) return g->cl_size > 0 ? DAWN_OK : fail(DAWN_E_INVALID, "the cluster engine is not available for this graph");
+    g->cl_size = -1;
+    int dev_smem = 0;
+    DAWN_CUDA_TRY(cudaDeviceGetAttribute(&dev_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, g->device));
+    DAWN_CUDA_TRY(cudaFuncSetAttribute(cluster_sssp_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+    // the dynamic shared memory limit belongs to the kernel, not to the graph:
+    // raise it once to all the kernel can take, so that graphs set up later
+    // never lower it under an earlier graph's launches
+    cudaFuncAttributes fa;
+    DAWN_CUDA_TRY(cudaFuncGetAttributes(&fa, cluster_sssp_kernel));
+    const int dyn_max = dev_smem - (int)fa.sharedSizeBytes;
+    DAWN_CUDA_TRY(cudaFuncSetAttribute(cluster_sssp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_max));
+    for (int C : {16, 8}) {
+        const long long S = ((long long)g->nwords + C - 1) / C;
+        const long long room = (long long)dev_smem - (long long)sizeof(ClShared) - 1024 - S * 4;
+        const long long qcap = std::min<long long>(8192, room / 8);
+        if (qcap < 1024) continue;
+        const int smem = (int)(S * 4 + qcap * 8);
+        if (smem > dyn_max) continue;
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = C;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.gridDim = dim3(C);
+        cfg.blockDim = dim3(kClThreads);
+        cfg.dynamicSmemBytes = smem;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        int nclusters = 0;
+        if (cudaOccupancyMaxActiveClusters(&nclusters, cluster_sssp_kernel, &cfg) != cudaSuccess) {
+            cudaGetLastError();
+            continue;
         }
-        if (g->cl_size > 0) {
-            cudaError_t e = cudaMalloc((void**)&g->cl_ovf, sizeof(int32_t) * 3 * (size_t)std::max(g->n, 1));
-            if (e == cudaSuccess) e = cudaMalloc((void**)&g->cl_ovf_n, sizeof(unsigned) * 4);
-            if (e != cudaSuccess) {
-                cudaFree(g->cl_ovf);
-                g->cl_ovf = nullptr;
-                g->cl_size = 0;  // try again next time
-                return cuda_fail(e, "cluster engine buffers", __FILE__, __LINE__);
-            }
-        }
+        if (nclusters < 1) continue;
+        g->cl_size = C;
+        g->cl_smem = smem;
+        g->cl_qcap = (int)qcap;
+        g->cl_active = nclusters;
+        return DAWN_OK;
     }
-    if (g->cl_size < 0) return fail(DAWN_E_INVALID, "the cluster engine is not available for this graph");
-    ClArgs a;
+    return fail(DAWN_E_INVALID, "the cluster engine is not available for this graph");
+}
+
+// Overflow lists and counts for `clusters` clusters running at once (3n
+// entries and 4 counts each), plus the counter of a many-source launch after
+// the last cluster's counts.
+int cluster_buffers(dawn_graph* g, int clusters) {
+    if (g->cl_bufs >= clusters) return DAWN_OK;
+    cudaFree(g->cl_ovf);
+    cudaFree(g->cl_ovf_n);
+    g->cl_ovf = nullptr;
+    g->cl_ovf_n = nullptr;
+    g->cl_bufs = 0;
+    cudaError_t e = cudaMalloc((void**)&g->cl_ovf, sizeof(int32_t) * 3 * (size_t)std::max(g->n, 1) * (size_t)clusters);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&g->cl_ovf_n, sizeof(unsigned) * (4 * (size_t)clusters + 4));
+    if (e != cudaSuccess) {
+        cudaFree(g->cl_ovf);
+        g->cl_ovf = nullptr;
+        return cuda_fail(e, "cluster engine buffers", __FILE__, __LINE__);
+    }
+    g->cl_bufs = clusters;
+    return DAWN_OK;
+}
+
+int cluster_run(dawn_graph* g, ClArgs& a, int clusters, cudaStream_t st) {
     a.row_ptr = g->row_ptr;
     a.col_idx = g->col_idx;
-    a.dist = dist_dev;
     a.ovf = g->cl_ovf;
     a.ovf_n = g->cl_ovf_n;
     a.status = &g->ctl->status;
-    a.stats = stats_dev;
     a.n = g->n;
     a.nwords = g->nwords;
-    a.src = src;
     a.S = (g->nwords + g->cl_size - 1) / g->cl_size;
     a.qcap = g->cl_qcap;
     cudaLaunchConfig_t cfg = {};
@@ -332,7 +380,7 @@ int cluster_launch(dawn_graph* g, int32_t src, int32_t* dist_dev, const dawn_sss
     attr[0].val.clusterDim.x = g->cl_size;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
-    cfg.gridDim = dim3(g->cl_size);
+    cfg.gridDim = dim3(g->cl_size * clusters);
     cfg.blockDim = dim3(kClThreads);
     cfg.dynamicSmemBytes = g->cl_smem;
     cfg.stream = st;
@@ -340,6 +388,47 @@ int cluster_launch(dawn_graph* g, int32_t src, int32_t* dist_dev, const dawn_sss
     cfg.numAttrs = 1;
     DAWN_CUDA_TRY(cudaLaunchKernelEx(&cfg, cluster_sssp_kernel, a));
     return DAWN_OK;
+}
+
+}  // namespace
+
+int cluster_launch(dawn_graph* g, int32_t src, int32_t* dist_dev, const dawn_sssp_opts* opts,
+                   dawn_sssp_stats* stats_dev, cudaStream_t st) {
+    if (opts && (opts->mode == DAWN_MODE_PULL || opts->trace))
+        return fail(DAWN_E_INVALID, "the cluster engine runs SOVM push only, without a trace");
+    int rc = cluster_setup(g);
+    if (rc == DAWN_OK) rc = cluster_buffers(g, 1);
+    if (rc != DAWN_OK) return rc;
+    ClArgs a = {};
+    a.dist = dist_dev;
+    a.stats = stats_dev;
+    a.src = src;
+    a.srcs = nullptr;
+    a.next = nullptr;
+    a.k = 1;
+    a.dist_stride = 0;
+    return cluster_run(g, a, 1, st);
+}
+
+int cluster_launch_many(dawn_graph* g, const int32_t* srcs_dev, int32_t k, int32_t* dist_dev, long long stride,
+                        const dawn_sssp_opts* opts, dawn_sssp_stats* stats_dev, cudaStream_t st) {
+    if (opts && (opts->mode == DAWN_MODE_PULL || opts->trace))
+        return fail(DAWN_E_INVALID, "the cluster engine runs SOVM push only, without a trace");
+    int rc = cluster_setup(g);
+    if (rc != DAWN_OK) return rc;
+    const int clusters = std::max(1, std::min<int>(k, g->cl_active));
+    rc = cluster_buffers(g, clusters);
+    if (rc != DAWN_OK) return rc;
+    ClArgs a = {};
+    a.dist = dist_dev;
+    a.stats = stats_dev;
+    a.src = 0;
+    a.srcs = srcs_dev;
+    a.next = g->cl_ovf_n + 4 * (size_t)g->cl_bufs;
+    a.k = k;
+    a.dist_stride = stride;
+    DAWN_CUDA_TRY(cudaMemsetAsync(a.next, 0, sizeof(unsigned), st));
+    return cluster_run(g, a, clusters, st);
 }
 
 }  // namespace dawn

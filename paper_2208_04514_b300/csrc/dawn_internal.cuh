@@ -103,8 +103,10 @@ struct dawn_graph {
     int cl_size = 0;
     int cl_smem = 0;
     int cl_qcap = 0;
-    int32_t* cl_ovf = nullptr;        // 3 lists of n entries
-    unsigned* cl_ovf_n = nullptr;     // their 3 counts
+    int cl_active = 0;                // clusters of that size the device holds at once
+    int cl_bufs = 0;                  // clusters the overflow buffers below serve
+    int32_t* cl_ovf = nullptr;        // per cluster: 3 lists of n entries
+    unsigned* cl_ovf_n = nullptr;     // per cluster: their 3 counts (4 slots); then a many-source counter
     void* many_graph = nullptr;       // dawn_sssp_many: last captured CUDA graph of launches (many.cu)
     int64_t cand_cap = 0;             // entries per list
     dawn::Ctl* ctl = nullptr;         // device control block
@@ -144,4 +146,8 @@ int weighted_reset(dawn_graph* g, cudaStream_t st);
 // cluster.cu: one source on a single thread-block cluster; DAWN_E_INVALID when unavailable
 int cluster_launch(dawn_graph* g, int32_t src, int32_t* dist_dev, const dawn_sssp_opts* opts,
                    dawn_sssp_stats* stats_dev, cudaStream_t st);
+// cluster.cu: k sources (device array) on as many clusters as the device holds
+// at once, each taking the next source; row i at dist_dev + i * stride
+int cluster_launch_many(dawn_graph* g, const int32_t* srcs_dev, int32_t k, int32_t* dist_dev, long long stride,
+                        const dawn_sssp_opts* opts, dawn_sssp_stats* stats_dev, cudaStream_t st);
 }  // namespace dawn

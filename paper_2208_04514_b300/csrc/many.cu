@@ -6,6 +6,7 @@
 // behind the computation (pinned host memory is needed for the overlap).
 // With device rows the k launches are captured once as a CUDA graph and the
 // graph is replayed while the same call repeats.
+#include <algorithm>
 #include <cstring>
 #include <vector>
 
@@ -122,7 +123,41 @@ DAWN_API int dawn_sssp_many(dawn_graph_t g, const int32_t* sources, int32_t k, i
                          ((!opts || opts->engine == DAWN_ENGINE_AUTO) && g->m < 8 * (int64_t)g->n &&
                           (!opts || (opts->mode != DAWN_MODE_PULL && !opts->trace)));
     int32_t direct = k;  // launches issued one by one below
-    if (rc == DAWN_OK && ddev && !cluster && (!stats || sdev)) {
+    // several sources on the cluster engine: one launch of as many clusters as
+    // the device holds, each taking the next source (host rows go through a
+    // device staging block of one row per cluster, copied out per batch)
+    if (rc == DAWN_OK && cluster && k > 1) {
+        int32_t* srcs_dev = nullptr;
+        int32_t* block = nullptr;
+        e = cudaMallocAsync((void**)&srcs_dev, sizeof(int32_t) * (size_t)k, st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(srcs_dev, src.data(), sizeof(int32_t) * (size_t)k, cudaMemcpyHostToDevice, st);
+        int crc = e == cudaSuccess ? DAWN_OK : cuda_fail(e, "dawn_sssp_many (sources)", __FILE__, __LINE__);
+        if (crc == DAWN_OK && ddev) {
+            crc = cluster_launch_many(g, srcs_dev, k, dist, (long long)row, opts, st_dev, st);
+        } else if (crc == DAWN_OK) {
+            // the batch: one row per cluster the device holds at once (known after the first call)
+            const int32_t kb = std::max(1, std::min<int32_t>(k, g->cl_active > 0 ? g->cl_active : 8));
+            e = cudaMallocAsync((void**)&block, sizeof(int32_t) * row * (size_t)kb, st);
+            if (e != cudaSuccess) crc = cuda_fail(e, "dawn_sssp_many (staging)", __FILE__, __LINE__);
+            for (int32_t b0 = 0; crc == DAWN_OK && b0 < k; b0 += kb) {
+                const int32_t nb = std::min(kb, k - b0);
+                crc = cluster_launch_many(g, srcs_dev + b0, nb, block, (long long)row, opts,
+                                          st_dev ? st_dev + b0 : nullptr, st);
+                if (crc == DAWN_OK) {
+                    e = cudaMemcpyAsync(dist + (size_t)b0 * row, block, sizeof(int32_t) * row * (size_t)nb,
+                                        cudaMemcpyDeviceToHost, st);
+                    if (e != cudaSuccess) crc = cuda_fail(e, "dawn_sssp_many (rows)", __FILE__, __LINE__);
+                }
+            }
+        }
+        if (srcs_dev) cudaFreeAsync(srcs_dev, st);
+        if (block) cudaFreeAsync(block, st);
+        if (crc == DAWN_OK) direct = 0;
+        else if (g->cl_size >= 0 || (opts && opts->engine == DAWN_ENGINE_CLUSTER)) rc = crc;
+        // else the cluster engine is unavailable on this graph: one launch per source below
+    }
+    if (rc == DAWN_OK && direct > 0 && ddev && !cluster && (!stats || sdev)) {
         ManyGraph* c = static_cast<ManyGraph*>(g->many_graph);
         const bool hit = c && c->src == src && c->dist == dist && c->stats == st_dev && same_opts(*c, opts) &&
                          c->parity0 == (g->sssp_launches & 1u);

@@ -270,13 +270,21 @@ def test_lattice_4096_full_size(dawn):
     h = upload(dawn, g)
     try:
         d = torch.zeros(g.n, dtype=torch.int32, device="cuda")
-        for i, s in enumerate(gg.uniform_vertices(g.n, 16, seed=7)):
+        srcs = gg.uniform_vertices(g.n, 16, seed=7)
+        # the 16 sources in one call as well: several clusters side by side
+        rows = torch.full((16, g.n), -7, dtype=torch.int32, device="cuda")
+        mstats = torch.zeros((16, dawn.STATS_WORDS), dtype=torch.int64, device="cuda")
+        dawn.dawn_sssp_many(h, torch.from_numpy(srcs.astype(np.int32)).cuda(), dist=rows, stats=mstats)
+        mst = mstats.cpu().numpy()
+        for i, s in enumerate(srcs):
             st = dawn.dawn_sssp_ex(h, int(s), d)
             dh = d.cpu().numpy()
             np.testing.assert_array_equal(dh, oracle.bfs_queue(g.row_ptr, g.col_idx, int(s)))
             assert oracle.certificate(g.row_ptr, g.col_idx, int(s), dh) == (0, -1)
             check_stats(g, dh, st)
             assert st["levels"] > 4000
+            np.testing.assert_array_equal(rows[i].cpu().numpy(), dh)
+            check_stats(g, dh, dawn.stats_from_words(mst[i]))
             if i < 2:
                 # the grid-wide engine on the same source (AUTO takes the cluster here)
                 st = dawn.dawn_sssp_ex(h, int(s), d, {"engine": 1})
@@ -450,3 +458,29 @@ def test_symmetric_flag_is_checked_at_upload(dawn):
         np.testing.assert_array_equal(d, oracle.sssp_sovm(ok.row_ptr, ok.col_idx, 0))
     finally:
         dawn.dawn_graph_free(h2)
+
+
+@pytest.mark.parametrize("where", ["device", "host"])
+def test_many_sources_on_the_cluster_engine(dawn, where):
+    """dawn_sssp_many on a low-degree graph runs its sources on several
+    clusters at once, each taking the next source: more sources than clusters
+    the device holds, device and host rows, every row against Alg. 2 and the
+    per-source statistics against the rows."""
+    g = gg.lattice(300, 220, 0.1, seed=5)
+    h = upload(dawn, g)
+    try:
+        srcs = gg.uniform_vertices(g.n, 41, seed=3).astype(np.int32)
+        if where == "device":
+            rows_t = torch.full((41, g.n), -7, dtype=torch.int32, device="cuda")
+            st_t = torch.zeros((41, dawn.STATS_WORDS), dtype=torch.int64, device="cuda")
+            dawn.dawn_sssp_many(h, torch.from_numpy(srcs).cuda(), dist=rows_t, stats=st_t)
+            rows, st = rows_t.cpu().numpy(), st_t.cpu().numpy()
+        else:
+            rows = np.full((41, g.n), -7, dtype=np.int32)
+            st = np.zeros((41, dawn.STATS_WORDS), dtype=np.int64)
+            dawn.dawn_sssp_many(h, srcs, dist=rows, stats=st)
+        for i, s in enumerate(srcs):
+            np.testing.assert_array_equal(rows[i], oracle.bfs_queue(g.row_ptr, g.col_idx, int(s)))
+            check_stats(g, rows[i], dawn.stats_from_words(st[i]))
+    finally:
+        dawn.dawn_graph_free(h)
