@@ -674,45 +674,63 @@ def bench_serving(dawn, torch, nreq=48, seed=6):
         del outs
         return lat, len(reqs) / span, t_end - t0
 
+    def by_class(reqs, lat):
+        """p50 / p99 per graph class (RMAT graphs, lattices) and per request size."""
+        out_c = {}
+        for cname, pick in (("rmat", lambda gi: specs[gi][0].startswith("rmat")),
+                            ("lattice", lambda gi: specs[gi][0].startswith("lattice"))):
+            for kname, kpick in (("all_k", lambda k: True), ("k<=4", lambda k: k <= 4), ("k>=64", lambda k: k >= 64)):
+                sel = np.array([pick(gi) and kpick(len(srcs)) for gi, srcs in reqs])
+                if sel.sum() == 0:
+                    continue
+                out_c[f"{cname}_{kname}"] = {"requests": int(sel.sum()),
+                                             "p50_ms": 1e3 * float(np.percentile(lat[sel], 50)),
+                                             "p99_ms": 1e3 * float(np.percentile(lat[sel], 99))}
+        return out_c
+
     out = {"workload": "serve_8graphs", "graphs": [n for n, _ in specs], "requests_per_rate": nreq,
            "dist": "int16 rows written in place into device buffers", "rates": {}}
     cal = draw(nreq)
     lat, qps_sat, _ = serve(cal, np.zeros(nreq), check=True)
     out["saturated_queries_per_s"] = qps_sat
     out["saturated_sources_per_s"] = sum(len(x[1]) for x in cal) * qps_sat / nreq
-    stream_10 = None
+    stream_10 = stream_03 = None
     for frac in (0.3, 0.7, 1.0):
         reqs = draw(nreq)
         arrivals = np.cumsum(rng.exponential(1.0 / (frac * qps_sat), nreq))
         lat, qps, _ = serve(reqs, arrivals, check=frac == 1.0)
         out["rates"][f"{frac:.1f}x"] = {"offered_queries_per_s": frac * qps_sat, "queries_per_s": qps,
                                        "p50_ms": 1e3 * float(np.percentile(lat, 50)),
-                                       "p99_ms": 1e3 * float(np.percentile(lat, 99))}
+                                       "p99_ms": 1e3 * float(np.percentile(lat, 99)),
+                                       "by_class": by_class(reqs, lat)}
+        if frac == 0.3:
+            stream_03 = (reqs, arrivals)
         if frac == 1.0:
             stream_10 = (reqs, arrivals)
-    # plain path on the 1.0x stream
-    reqs, arrivals = stream_10
+    # plain path on the 0.3x and 1.0x streams: per-request service times
+    # measured back to back, latencies from the FIFO single-server recursion
     stream = torch.cuda.current_stream()
-    service = []
-    for gi, srcs in reqs:
-        rows = torch.empty((len(srcs), ns[gi]), dtype=torch.int32, device="cuda")
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for i, sv in enumerate(srcs):
-            dawn.dawn_sssp_async(handles[gi], int(sv), rows[i], None, None, stream)
-        e1.record(stream)
-        dawn.dawn_graph_sync(handles[gi], stream)
-        service.append(e0.elapsed_time(e1) * 1e-3)
-        del rows
-    done_prev, lat = 0.0, []
-    for at, sv in zip(arrivals, service):
-        start = max(at, done_prev)
-        done_prev = start + sv
-        lat.append(done_prev - at)
-    lat = np.array(lat)
-    out["plain_1.0x"] = {"queries_per_s": len(reqs) / (done_prev - arrivals[0]),
-                         "p50_ms": 1e3 * float(np.percentile(lat, 50)), "p99_ms": 1e3 * float(np.percentile(lat, 99)),
-                         "busy_s": float(sum(service))}
+    for tag, (reqs, arrivals) in (("plain_0.3x", stream_03), ("plain_1.0x", stream_10)):
+        service = []
+        for gi, srcs in reqs:
+            rows = torch.empty((len(srcs), ns[gi]), dtype=torch.int32, device="cuda")
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for i, sv in enumerate(srcs):
+                dawn.dawn_sssp_async(handles[gi], int(sv), rows[i], None, None, stream)
+            e1.record(stream)
+            dawn.dawn_graph_sync(handles[gi], stream)
+            service.append(e0.elapsed_time(e1) * 1e-3)
+            del rows
+        done_prev, lat = 0.0, []
+        for at, sv in zip(arrivals, service):
+            start = max(at, done_prev)
+            done_prev = start + sv
+            lat.append(done_prev - at)
+        lat = np.array(lat)
+        out[tag] = {"queries_per_s": len(reqs) / (done_prev - arrivals[0]),
+                    "p50_ms": 1e3 * float(np.percentile(lat, 50)), "p99_ms": 1e3 * float(np.percentile(lat, 99)),
+                    "busy_s": float(sum(service)), "by_class": by_class(reqs, lat)}
     for h in handles:
         dawn.dawn_graph_free(h)
     out["verified"] = {"rows_checked": checked["rows"], "graphs": sorted(checked["graphs"]),

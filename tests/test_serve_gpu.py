@@ -187,3 +187,38 @@ def test_bad_serve_modes(dawn, handles):
     with pytest.raises(dawn.DawnError) as ei:
         dawn.dawn_serve_create_ex(handles, 0, 64, [0, 1, 2, 3])
     assert ei.value.code == dawn.DAWN_E_INVALID
+
+
+@pytest.mark.parametrize("mode", ["frontier", "dense"])
+def test_serving_graphs_at_full_size(dawn, mode):
+    """The serving workload's largest resident graphs: the 4096^2 lattice
+    (p = 0.1, ~10^4 levels) and RMAT scale 22, both resident in one server, a
+    few requests each (a 1-source and a 3-source request per graph, int16
+    rows on the device), every served row against Alg. 2 (the oracle's FIFO
+    BFS), under the frontier push and under the dense pull."""
+    lat = gg.lattice(4096, 4096, 0.1, seed=3)
+    rm = gg.rmat(22, seed=122)
+    hs = [dawn.dawn_graph_upload(lat.row_ptr, lat.col_idx, flags=dawn.DAWN_SYMMETRIC),
+          dawn.dawn_graph_upload(rm.row_ptr, rm.col_idx, flags=dawn.DAWN_SYMMETRIC)]
+    step = dawn.DAWN_SERVE_FRONTIER if mode == "frontier" else dawn.DAWN_SERVE_DENSE
+    s = dawn.dawn_serve_create_ex(hs, 0, 64, [step, step])
+    try:
+        reqs = []
+        for gi, g in enumerate((lat, rm)):
+            pool = gg.sample_sources(g, 4, seed=31 + gi)
+            for srcs in (pool[:1], pool[1:]):
+                out = torch.full((len(srcs), g.n), 77, dtype=torch.int16, device="cuda")
+                rid = dawn.dawn_serve_submit(s, gi, np.ascontiguousarray(srcs, dtype=np.int32), dist_bytes=2,
+                                             dist_out=out)
+                reqs.append((g, srcs, out, rid))
+        dawn.dawn_serve_drain(s, 600000)
+        for g, srcs, out, rid in reqs:
+            assert dawn.dawn_serve_poll(s, rid) == dawn.DAWN_REQ_DONE
+            got = out.cpu().numpy()
+            for i, src in enumerate(srcs):
+                want = oracle.bfs_queue(g.row_ptr, g.col_idx, int(src)).astype(np.int16)
+                np.testing.assert_array_equal(got[i], want)
+    finally:
+        dawn.dawn_serve_destroy(s)
+        for h in hs:
+            dawn.dawn_graph_free(h)
