@@ -41,6 +41,9 @@ namespace {
 #ifndef DAWN_SSSP_MIN_CTAS
 #define DAWN_SSSP_MIN_CTAS 1  // CTAs per SM the register budget is sized for
 #endif
+#ifndef DAWN_CTL_PREFETCH
+#define DAWN_CTL_PREFETCH 1
+#endif
 #ifndef DAWN_SSSP_SMEM_BITMAP_MAX
 #define DAWN_SSSP_SMEM_BITMAP_MAX (200 * 1024)
 #endif
@@ -1141,6 +1144,19 @@ __global__ void __launch_bounds__(kThreads, DAWN_SSSP_MIN_CTAS) sssp_kernel(Sssp
     unsigned* bar = &ctl->bar[a.bar_parity].count;
     unsigned bar_target = 0;
     if (tracer) trace_rec(a, tslot, 0, 0, 1);
+#if DAWN_CTL_PREFETCH
+    // The control block's lines (this launch's barrier counter and counter
+    // slots) and the statistics record are touched first by the level-1
+    // atomics, the first grid barrier and the last write; the L2 may have
+    // lost them since the last launch, so bring them in now, off the chain.
+    if (blockIdx.x == 0 && threadIdx.x < 6) {
+        const void* p = threadIdx.x == 0 ? (const void*)&ctl->bar[a.bar_parity]
+                      : threadIdx.x <= 3 ? (const void*)&ctl->ctr[a.bar_parity][threadIdx.x - 1]
+                      : threadIdx.x == 4 ? (const void*)&ctl->status
+                                         : (const void*)a.stats;
+        if (p) asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+    }
+#endif
     const long long gtid = (long long)blockIdx.x * kThreads + threadIdx.x;
     const long long gthreads = (long long)gridDim.x * kThreads;
 
