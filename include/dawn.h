@@ -358,12 +358,31 @@ DAWN_API int dawn_set_tuning(dawn_graph_t g, const dawn_tuning* t);
 DAWN_API int dawn_msbfs(dawn_graph_t g, const int32_t* sources, int32_t k, void* dist_block,
                         int dist_bytes, int layout, int32_t* ecc, int64_t* dsum, void* stream);
 
+/* Kernels of the batched level loop (dawn_msbfs_opts.kernel).  Both give
+ * identical results.
+ *   DAWN_MSBFS_SLICED     in-arc rows cut into warp tasks by in-degree (one
+ *                         vertex per lane for short rows, row pieces for long
+ *                         ones); each level only ORs visited words, and the
+ *                         first-reach level of every (source, vertex) bit is
+ *                         kept bit-sliced, so each distance row is written
+ *                         once, whole, after the pass's last level.  Up to
+ *                         32767 levels.
+ *   DAWN_MSBFS_PER_LEVEL  distances written level by level as bits appear;
+ *                         any number of levels; dawn_centrality always uses it.
+ * 0 picks SLICED, and PER_LEVEL for a graph on which a run has needed more
+ * levels than SLICED's planes hold. */
+#define DAWN_MSBFS_SLICED 1
+#define DAWN_MSBFS_PER_LEVEL 2
+
 typedef struct {
     int32_t lanes;         /* sources per pass: 64, 128 or 256; 0 = tuned, else by k */
     int32_t trace_cap;     /* records that fit in trace */
     int64_t spin_limit;    /* as in dawn_sssp_opts */
     int64_t* trace;        /* device memory or NULL: one record of 4 int64 per level,
-                              {pass, level, vertices reached in the level, globaltimer ns} */
+                              {pass, level, lanes that reached a vertex in the level,
+                              globaltimer ns} */
+    int32_t kernel;        /* 0, DAWN_MSBFS_SLICED or DAWN_MSBFS_PER_LEVEL */
+    int32_t reserved;      /* 0 */
 } dawn_msbfs_opts;
 
 /* dawn_msbfs with the reached counts and options (reached, opts may be NULL). */

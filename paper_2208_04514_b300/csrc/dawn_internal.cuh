@@ -31,6 +31,7 @@ enum DeviceStatus : int {
     DEV_OK = 0,
     DEV_TIMEOUT = 1,   // a bounded grid-barrier wait expired
     DEV_OVERFLOW = 2,  // an int16 distance would exceed 32767
+    DEV_PLANES = 3,    // the sliced batched kernel needs more level planes than it was given
 };
 
 // A push level whose queue holds a row longer than this splits its work by
@@ -120,7 +121,14 @@ struct dawn_graph {
     // multi-source work buffers (allocated on first use)
     uint64_t* ms_vis[2] = {nullptr, nullptr};
     uint64_t* ms_acc = nullptr;       // per-vertex OR accumulators of dense batched levels
-    int ms_words_cap = 0;             // W capacity of ms_vis
+    int ms_words_cap = 0;             // W capacity of ms_vis (n + 1 rows of 4 words; row n stays zero)
+    void* ms_plan = nullptr;          // sliced batched kernel: in-arc rows cut into warp tasks (msbfs.cu)
+    uint64_t* ms_nb = nullptr;        // its per-level new bits: ms_nb_levels x (n + 1) x 4 words
+    int ms_nb_levels = 0;
+    uint64_t* ms_planes = nullptr;    // and bit-sliced levels past those: ms_planes_cap x (n + 1) x 4 words
+    int ms_planes_cap = 0;
+    int ms_sliced_off = 0;            // 1: a run needed more levels than the sliced kernel holds; use the per-level kernel
+    int ms_vis_dirty = 0;             // 1: ms_vis holds words a run left behind (the sliced kernel wants zeros)
     void* ms_scratch = nullptr;       // per-pass distance block when the caller passes none
     size_t ms_scratch_bytes = 0;
     int32_t* ms_counts = nullptr;     // per-lane per-level new-vertex counts
@@ -139,6 +147,8 @@ int sssp_occupancy(dawn_graph* g);
 int graph_sync_status(dawn_graph* g, cudaStream_t stream);
 // many.cu: release the captured graph of dawn_sssp_many
 void many_release(dawn_graph* g);
+// msbfs.cu: release the sliced batched kernel's plan and planes
+void ms_release(dawn_graph* g);
 // weighted.cu: release the weighted path's buffers; zero its control block
 // after a failed launch (graph_sync_status)
 void weighted_release(dawn_graph* g);

@@ -440,6 +440,7 @@ void release(dawn_graph* g) {
     f(g->ms_acc);
     f(g->ms_scratch);
     f(g->ms_counts);
+    ms_release(g);
     if (g->stats_host) cudaFreeHost(g->stats_host);
     if (g->status_host) cudaFreeHost(g->status_host);
     delete g;

@@ -20,7 +20,10 @@
 // (eccentricity = largest finite distance, distance sum, reached count, from
 // per-level counts) all run in one launch, separated by the bounded grid
 // barrier.
+#include <algorithm>
 #include <climits>
+#include <functional>
+#include <queue>
 #include <vector>
 
 #include "dawn_internal.cuh"
@@ -624,9 +627,12 @@ int ms_workspace(dawn_graph* g, int W) {
         if (g->ms_vis[0]) cudaFree(g->ms_vis[0]);
         if (g->ms_vis[1]) cudaFree(g->ms_vis[1]);
         g->ms_vis[0] = g->ms_vis[1] = nullptr;
-        const size_t bytes = sizeof(uint64_t) * (size_t)g->n * 4;  // room for W = 4
+        // room for W = 4; row n stays zero (the sliced kernel's padding arcs point there)
+        const size_t bytes = sizeof(uint64_t) * ((size_t)g->n + 1) * 4;
         DAWN_CUDA_TRY(cudaMalloc((void**)&g->ms_vis[0], bytes));
         DAWN_CUDA_TRY(cudaMalloc((void**)&g->ms_vis[1], bytes));
+        DAWN_CUDA_TRY(cudaMemset(g->ms_vis[0], 0, bytes));
+        DAWN_CUDA_TRY(cudaMemset(g->ms_vis[1], 0, bytes));
         if (g->ms_acc) cudaFree(g->ms_acc);
         g->ms_acc = nullptr;
         DAWN_CUDA_TRY(cudaMalloc((void**)&g->ms_acc, bytes));
@@ -641,6 +647,807 @@ int ms_workspace(dawn_graph* g, int W) {
         DAWN_CUDA_TRY(cudaMemset(g->ms_counts, 0, bytes));
         g->ms_counts_cap = bytes;
     }
+    return DAWN_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Sliced batched kernel.
+//
+// The same level, new[v] = (OR over in-neighbours u of V[u]) AND NOT V[v]
+// for all 64 * W lanes at once, with the work cut by in-degree once per
+// graph (ms_plan_build): vertices are sorted by in-degree, largest first.
+//   * a row longer than kSellDeg is a warp task: the warp reads 32
+//     consecutive in-arcs at a time and ORs their visited words lane by lane,
+//     then across the warp once per task.  Rows longer than the plan's piece
+//     length are split into pieces, all given to one CTA; the pieces OR into
+//     a shared-memory row that the CTA finishes after its tasks.
+//   * the other rows are cut into slices of 32 vertices, one vertex per
+//     lane; a slice's in-arcs are stored column by column (arc j of lane i at
+//     32 j + i), so each step reads 32 consecutive indices.
+// Tasks are split over the CTAs by estimated time and taken by the CTA's
+// warps from a shared counter.  A level reads one visited buffer and writes
+// the other for every vertex of a task; vertices without in-arcs keep the
+// seeded words that both buffers hold.  A vertex is covered once every lane
+// still growing has reached it: it can gain no bit in this pass.  A task
+// whose vertices were all covered in two consecutive levels has written its
+// final words to both buffers and is skipped for the rest of the pass.
+//
+// Nothing is written per (source, vertex) while the levels run: each level
+// t <= nb_levels stores the vertex's new bits in its own array NB[t] (zeroed
+// one level ahead, so only nonzero words are stored); later levels OR them
+// into bit-sliced planes (plane p = bit p of the level).  After the last
+// level each warp turns 32 consecutive vertices' arrays into their distance
+// cells, writing every cell of each row once, and reduces them per source
+// (reached, distance sum, largest distance) after a 32 x 32 bit transpose of
+// the level bits puts one source in each lane.
+// ---------------------------------------------------------------------------
+constexpr int kSellDeg = 16;     // in-degree of the one-vertex-per-lane class
+constexpr int kHubMax = 128;     // rows split into pieces, per CTA
+constexpr int kPieceMin = 256;   // arcs of a row piece, at least
+constexpr int kTaskSmem = 1536;  // tasks a CTA keeps in shared memory (and may skip)
+constexpr int kTrip = 4;         // a dependent memory round trip, in warp steps of 32 arcs
+constexpr int kNbLevelsMax = 15; // levels with their own new-bit array
+constexpr int kPlanesMax = 15;   // levels up to 32767
+constexpr size_t kNbBudget = 1ull << 30;      // device bytes for the new-bit arrays
+constexpr size_t kPlanesBudget = 8ull << 30;  // and for the planes of deeper levels
+
+struct MsPlan {
+    int sms = 0;
+    int32_t ntasks = 0, nhubs = 0, nslices = 0, piece = 0, max_hubs = 0, max_tasks = 0;
+    long long sell_len = 0;
+    void* blob = nullptr;        // one device allocation holding the arrays below
+    int4* tasks = nullptr;       // piece {v, first arc, end arc, CTA hub slot or -1}; slice {-1 - id, offset, width, 0}
+    int32_t* cta_task = nullptr; // [sms + 1]: CTA c runs tasks [cta_task[c], cta_task[c + 1])
+    int32_t* cta_hub = nullptr;  // [sms + 1]: and owns split rows [cta_hub[c], cta_hub[c + 1]) of hub_v
+    int32_t* hub_v = nullptr;
+    int2* sell_vd = nullptr;     // [nslices * 32]: {vertex or -1, in-degree}
+    int32_t* sell_idx = nullptr; // slice columns; entries past a vertex's degree hold -1
+};
+
+struct MsSliced {
+    const int4* __restrict__ tasks;
+    const int32_t* __restrict__ cta_task;
+    const int32_t* __restrict__ cta_hub;
+    const int32_t* __restrict__ hub_v;
+    const int2* __restrict__ sell_vd;
+    const int32_t* __restrict__ sell_idx;
+    uint64_t* nbl;               // NB[t] of vertex v (1 <= t <= nb_levels): nbl + ((t - 1) * (n + 1) + v) * W
+    uint64_t* planes;            // plane p of vertex v: planes + (p * (n + 1) + v) * W; may be null
+    int32_t nb_levels;
+    int32_t planes_cap;          // levels below 2^planes_cap fit (0: planes absent)
+};
+
+__device__ __forceinline__ unsigned long long warp_or_redux(unsigned long long x) {
+    const unsigned lo = __reduce_or_sync(kFull, (unsigned)x);
+    const unsigned hi = __reduce_or_sync(kFull, (unsigned)(x >> 32));
+    return ((unsigned long long)hi << 32) | lo;
+}
+
+// Lane j receives column j of the 32 x 32 bit matrix whose row i lane i holds.
+__device__ __forceinline__ unsigned bit_transpose32(unsigned x) {
+    const int lane = threadIdx.x & 31;
+    constexpr unsigned kMask[5] = {0x0000FFFFu, 0x00FF00FFu, 0x0F0F0F0Fu, 0x33333333u, 0x55555555u};
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+        const int k = 16 >> i;
+        const unsigned m = kMask[i];
+        const unsigned y = __shfl_xor_sync(kFull, x, k);
+        x = (lane & k) ? ((x & ~m) | ((y & ~m) >> k)) : ((x & m) | ((y & m) << k));
+    }
+    return x;
+}
+
+// W visited words of one vertex.  The visited buffers are written during the
+// launch, so reads go to L2 (a CTA could otherwise keep an older level's
+// line in L1).
+template <int W>
+__device__ __forceinline__ void vload(const uint64_t* p, unsigned long long (&x)[W]) {
+    if constexpr (W == 1) {
+        x[0] = __ldcg(reinterpret_cast<const unsigned long long*>(p));
+    } else {
+#pragma unroll
+        for (int i = 0; i < W / 2; ++i) {
+            const ulonglong2 t = __ldcg(reinterpret_cast<const ulonglong2*>(p) + i);
+            x[2 * i] = t.x;
+            x[2 * i + 1] = t.y;
+        }
+    }
+}
+
+template <int W>
+__device__ __forceinline__ void vor(const uint64_t* p, unsigned long long (&acc)[W]) {
+    unsigned long long x[W];
+    vload<W>(p, x);
+#pragma unroll
+    for (int w = 0; w < W; ++w) acc[w] |= x[w];
+}
+
+// OR of one in-neighbour's visited words into acc.  With DAWN_MS_GATHER_L1
+// the loads may be served from L1: the grid barrier's acquire orders them
+// after the previous level's stores (PTX memory model: a weak load that
+// follows an acquire, here through the CTA barrier, observes what the
+// release made visible), and a buffer is read only in the level after the
+// one that wrote it.
+#ifndef DAWN_MS_GATHER_L1
+#define DAWN_MS_GATHER_L1 1
+#endif
+template <int W>
+__device__ __forceinline__ void gor(const uint64_t* p, unsigned long long (&acc)[W]) {
+#if DAWN_MS_GATHER_L1
+    if constexpr (W == 1) {
+        acc[0] |= *reinterpret_cast<const unsigned long long*>(p);
+    } else {
+#pragma unroll
+        for (int i = 0; i < W / 2; ++i) {
+            const ulonglong2 t = reinterpret_cast<const ulonglong2*>(p)[i];
+            acc[2 * i] |= t.x;
+            acc[2 * i + 1] |= t.y;
+        }
+    }
+#else
+    vor<W>(p, acc);
+#endif
+}
+
+template <int W>
+__device__ __forceinline__ void vstore(uint64_t* p, const unsigned long long (&x)[W]) {
+    if constexpr (W == 1) {
+        *reinterpret_cast<unsigned long long*>(p) = x[0];
+    } else {
+#pragma unroll
+        for (int i = 0; i < W / 2; ++i) reinterpret_cast<ulonglong2*>(p)[i] = make_ulonglong2(x[2 * i], x[2 * i + 1]);
+    }
+}
+
+template <int W>
+__device__ __forceinline__ bool vcovered(const unsigned long long (&acc)[W], const unsigned long long (&vv)[W],
+                                         const unsigned long long (&fin)[W]) {
+    bool c = true;
+#pragma unroll
+    for (int w = 0; w < W; ++w) c &= (acc[w] | vv[w] | fin[w]) == ~0ull;
+    return c;
+}
+
+// Zero `words` words from p on with the whole grid (16-byte stores; p is
+// 8-byte aligned: a level array of W = 1 starts mid-line when n + 1 is odd).
+__device__ __forceinline__ void grid_zero(uint64_t* p, long long words) {
+    const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long nthreads = (long long)gridDim.x * blockDim.x;
+    if (words <= 0) return;
+    if (reinterpret_cast<uintptr_t>(p) & 15u) {
+        if (gtid == 0) p[0] = 0ull;
+        ++p;
+        --words;
+    }
+    ulonglong2* p2 = reinterpret_cast<ulonglong2*>(p);
+    for (long long i = gtid; i < (words >> 1); i += nthreads) p2[i] = make_ulonglong2(0ull, 0ull);
+    if ((words & 1) && gtid == 0) p[words - 1] = 0ull;
+}
+
+// A vertex's new bits at level t: next visited words, level record, growing lanes.
+template <int W>
+__device__ __forceinline__ void settle(const MsArgs& a, const MsSliced& p, uint64_t* vn, int t, int v,
+                                       const unsigned long long (&vv)[W], const unsigned long long (&acc)[W],
+                                       const unsigned long long (&fin)[W], unsigned long long (&grow)[W]) {
+    unsigned long long nb[W], nx[W];
+    bool any = false;
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+        nb[w] = acc[w] & ~vv[w] & ~fin[w];
+        nx[w] = vv[w] | nb[w];
+        grow[w] |= nb[w];
+        any |= nb[w] != 0ull;
+    }
+    vstore<W>(vn + (long long)v * W, nx);
+    if (!any) return;
+    const long long stride = (long long)(a.n + 1) * W;
+    if (t <= p.nb_levels) {
+        vstore<W>(p.nbl + (t - 1) * stride + (long long)v * W, nb);
+    } else {
+        uint64_t* pv = p.planes + (long long)v * W;
+        for (int b = 0; b < p.planes_cap; ++b) {
+            if (!((t >> b) & 1)) continue;
+#pragma unroll
+            for (int w = 0; w < W; ++w)
+                if (nb[w]) atomicOr(reinterpret_cast<unsigned long long*>(pv + b * stride + w), nb[w]);
+        }
+    }
+}
+
+template <int W>
+__global__ void __launch_bounds__(kMsThreads, 1) msbfs_sliced_kernel(MsArgs a, MsSliced p) {
+    __shared__ unsigned long long s_hacc[kHubMax][W];
+    __shared__ unsigned long long s_newmask[W];
+    __shared__ unsigned long long s_lanes[W];
+    __shared__ unsigned long long s_fin[W];  // lanes that can no longer grow: unused, then finished
+    __shared__ int s_reached[kMsMaxLanes];
+    __shared__ int s_ecc[kMsMaxLanes];
+    __shared__ long long s_dsum[kMsMaxLanes];
+    __shared__ int4 s_tasks[kTaskSmem];
+    __shared__ unsigned char s_cov[kTaskSmem];  // consecutive levels a task was fully covered
+    __shared__ int s_next, s_status;
+
+    MsCtl* ctl = a.ctl;
+    if (threadIdx.x == 0) s_status = ms_ld_relaxed_s32(&ctl->status);
+    __syncthreads();
+    if (s_status != DEV_OK) return;
+    unsigned* bar = &ctl->bar[a.bar_parity].count;
+    unsigned bar_target = 0;
+    int tslot = 0;
+    constexpr int L = 64 * W;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const long long gtid = (long long)blockIdx.x * kMsThreads + threadIdx.x;
+    const int n = a.n;
+    const long long stride = (long long)(n + 1) * W;
+    const int nbatches = (a.k + L - 1) / L;
+    const int tbeg = __ldg(p.cta_task + blockIdx.x), tend = __ldg(p.cta_task + blockIdx.x + 1);
+    const int tsm = min(tend - tbeg, kTaskSmem);
+    const int h0 = __ldg(p.cta_hub + blockIdx.x), nh = __ldg(p.cta_hub + blockIdx.x + 1) - h0;
+    const int ngroups = (n + 31) >> 5;
+    const int gA = (int)((long long)ngroups * blockIdx.x / gridDim.x);
+    const int gB = (int)((long long)ngroups * (blockIdx.x + 1) / gridDim.x);
+
+    for (int i = threadIdx.x; i < kHubMax * W; i += kMsThreads) (&s_hacc[0][0])[i] = 0ull;
+    for (int i = threadIdx.x; i < tsm; i += kMsThreads) s_tasks[i] = __ldg(p.tasks + tbeg + i);
+    for (int i = threadIdx.x; i < kMsMaxLanes; i += kMsThreads) {
+        s_reached[i] = 0;
+        s_ecc[i] = 0;
+        s_dsum[i] = 0;
+    }
+    if (threadIdx.x < W) s_newmask[threadIdx.x] = 0ull;
+    if (threadIdx.x == 0) s_next = tbeg;
+
+    for (int b = 0; b < nbatches; ++b) {
+        const int s0 = b * L;
+        const int kb = min(L, a.k - s0);
+        // ---- seeds: both visited buffers are zero here (cleared by the
+        // previous pass's read-out, or since allocation); NB[1] is zeroed
+        if (gtid < kb) {
+            const int s = (int)gtid;
+            const int src = __ldg(a.sources + s0 + s);
+            const unsigned long long bit = 1ull << (s & 63);
+            atomicOr(reinterpret_cast<unsigned long long*>(&a.V0[(long long)src * W + (s >> 6)]), bit);
+            atomicOr(reinterpret_cast<unsigned long long*>(&a.V1[(long long)src * W + (s >> 6)]), bit);
+        }
+        if (p.nb_levels >= 1) grid_zero(p.nbl, stride);
+        if (blockIdx.x == 0 && threadIdx.x < 3 * W) ctl->lanes_new[threadIdx.x / W][threadIdx.x % W] = 0ull;
+        for (int i = threadIdx.x; i < tsm; i += kMsThreads) s_cov[i] = 0;
+        if (threadIdx.x < W) {
+            const int lo = threadIdx.x * 64;
+            s_fin[threadIdx.x] = kb >= lo + 64 ? 0ull : (kb <= lo ? ~0ull : ~0ull << (kb - lo));
+        }
+        if (!ms_barrier(ctl, bar, bar_target, a.spin_limit)) return;
+
+        const unsigned long long (&fin)[W] = s_fin;
+        const uint64_t* vp = a.V0;
+        uint64_t* vn = a.V1;
+        int tlast = 0;
+        for (int t = 1;; ++t) {
+            if (a.dist_bytes == 2 && t > 32767) {
+                if (gtid == 0) atomicCAS(&ctl->status, DEV_OK, DEV_OVERFLOW);
+                return;
+            }
+            if (t > p.nb_levels && t >= (1 << p.planes_cap)) {
+                if (gtid == 0) atomicCAS(&ctl->status, DEV_OK, DEV_PLANES);
+                return;
+            }
+            // the next level's record starts zero
+            if (t + 1 <= p.nb_levels) grid_zero(p.nbl + t * stride, stride);
+            else if (t == p.nb_levels) grid_zero(p.planes, (long long)p.planes_cap * stride);
+            unsigned long long grow[W];
+#pragma unroll
+            for (int w = 0; w < W; ++w) grow[w] = 0ull;
+            // ---- this CTA's tasks, one warp at a time
+            while (true) {
+                int i = 0;
+                if (lane == 0) i = atomicAdd(&s_next, 1);
+                i = __shfl_sync(kFull, i, 0);
+                if (i >= tend) break;
+                const int li = i - tbeg;
+                if (li < kTaskSmem && s_cov[li] >= 2) continue;
+                const int4 tk = li < kTaskSmem ? s_tasks[li] : __ldg(p.tasks + i);
+                unsigned long long vv[W], acc[W];
+#pragma unroll
+                for (int w = 0; w < W; ++w) acc[w] = 0ull;
+                bool covered;
+                if (tk.x >= 0) {
+                    // row piece: arcs [tk.y, tk.z) of vertex tk.x, 128 per round;
+                    // each round's indices load with the previous round's words
+                    const int v = tk.x;
+                    const int j1 = tk.z;
+                    int j = tk.y + lane;
+                    int u0 = j < j1 ? __ldg(a.in_idx + j) : -1;
+                    int u1 = j + 32 < j1 ? __ldg(a.in_idx + j + 32) : -1;
+                    int u2 = j + 64 < j1 ? __ldg(a.in_idx + j + 64) : -1;
+                    int u3 = j + 96 < j1 ? __ldg(a.in_idx + j + 96) : -1;
+                    vload<W>(vp + (long long)v * W, vv);
+                    bool need = false;
+#pragma unroll
+                    for (int w = 0; w < W; ++w) need |= (vv[w] | fin[w]) != ~0ull;
+                    covered = !need;
+                    if (need) {
+                        for (int base = tk.y; base < j1; base += 128) {
+                            j += 128;
+                            int n0 = -1, n1 = -1, n2 = -1, n3 = -1;
+                            if (base + 128 < j1) {
+                                n0 = j < j1 ? __ldg(a.in_idx + j) : -1;
+                                n1 = j + 32 < j1 ? __ldg(a.in_idx + j + 32) : -1;
+                                n2 = j + 64 < j1 ? __ldg(a.in_idx + j + 64) : -1;
+                                n3 = j + 96 < j1 ? __ldg(a.in_idx + j + 96) : -1;
+                            }
+                            if (u0 >= 0) gor<W>(vp + (long long)u0 * W, acc);
+                            if (u1 >= 0) gor<W>(vp + (long long)u1 * W, acc);
+                            if (u2 >= 0) gor<W>(vp + (long long)u2 * W, acc);
+                            if (u3 >= 0) gor<W>(vp + (long long)u3 * W, acc);
+                            u0 = n0;
+                            u1 = n1;
+                            u2 = n2;
+                            u3 = n3;
+                        }
+#pragma unroll
+                        for (int w = 0; w < W; ++w) acc[w] = warp_or_redux(acc[w]);
+                    }
+                    if (tk.w >= 0) {
+                        if (need && lane == 0) {
+#pragma unroll
+                            for (int w = 0; w < W; ++w)
+                                if (acc[w]) atomicOr(&s_hacc[tk.w][w], acc[w]);
+                        }
+                    } else if (lane == 0) {
+                        settle<W>(a, p, vn, t, v, vv, acc, fin, grow);
+                    }
+                } else {
+                    // slice: lane = vertex, its in-arcs four columns per round.  The
+                    // first two rounds' indices load with the vertex, the first
+                    // round's words with its own words (before it is known whether
+                    // the vertex still needs them), later indices a round ahead.
+                    const int sid = -1 - tk.x;
+                    const int D = tk.z;
+                    const int32_t* col = p.sell_idx + tk.y + lane;
+                    const int2 vd = __ldg(p.sell_vd + (long long)sid * 32 + lane);
+                    int u0 = D > 0 ? __ldg(col) : -1;
+                    int u1 = D > 1 ? __ldg(col + 32) : -1;
+                    int u2 = D > 2 ? __ldg(col + 64) : -1;
+                    int u3 = D > 3 ? __ldg(col + 96) : -1;
+                    int n0 = D > 4 ? __ldg(col + 128) : -1;
+                    int n1 = D > 5 ? __ldg(col + 160) : -1;
+                    int n2 = D > 6 ? __ldg(col + 192) : -1;
+                    int n3 = D > 7 ? __ldg(col + 224) : -1;
+                    const int v = vd.x;
+                    bool need = false;
+                    if (v >= 0) vload<W>(vp + (long long)v * W, vv);
+                    if (u0 >= 0) gor<W>(vp + (long long)u0 * W, acc);
+                    if (u1 >= 0) gor<W>(vp + (long long)u1 * W, acc);
+                    if (u2 >= 0) gor<W>(vp + (long long)u2 * W, acc);
+                    if (u3 >= 0) gor<W>(vp + (long long)u3 * W, acc);
+                    if (v >= 0) {
+#pragma unroll
+                        for (int w = 0; w < W; ++w) need |= (vv[w] | fin[w]) != ~0ull;
+                    }
+                    covered = __all_sync(kFull, !need);
+                    for (int j = 4; !covered && j < D; j += 4) {
+                        if (__all_sync(kFull, !need || vcovered<W>(acc, vv, fin))) break;
+                        u0 = n0;
+                        u1 = n1;
+                        u2 = n2;
+                        u3 = n3;
+                        n0 = n1 = n2 = n3 = -1;
+                        if (j + 4 < D) {
+                            n0 = __ldg(col + 32 * (j + 4));
+                            n1 = j + 5 < D ? __ldg(col + 32 * (j + 5)) : -1;
+                            n2 = j + 6 < D ? __ldg(col + 32 * (j + 6)) : -1;
+                            n3 = j + 7 < D ? __ldg(col + 32 * (j + 7)) : -1;
+                        }
+                        if (need) {
+                            if (u0 >= 0) gor<W>(vp + (long long)u0 * W, acc);
+                            if (u1 >= 0) gor<W>(vp + (long long)u1 * W, acc);
+                            if (u2 >= 0) gor<W>(vp + (long long)u2 * W, acc);
+                            if (u3 >= 0) gor<W>(vp + (long long)u3 * W, acc);
+                        }
+                    }
+                    if (v >= 0) {
+                        if (!need) {
+#pragma unroll
+                            for (int w = 0; w < W; ++w) acc[w] = 0ull;
+                        }
+                        settle<W>(a, p, vn, t, v, vv, acc, fin, grow);
+                    }
+                }
+                if (lane == 0 && li < kTaskSmem) s_cov[li] = covered ? s_cov[li] + 1 : 0;
+            }
+            __syncthreads();  // every piece of this CTA's split rows is in s_hacc
+            for (int h = warp; h < nh; h += kMsWarps) {
+                if (lane == 0) {
+                    const int v = __ldg(p.hub_v + h0 + h);
+                    unsigned long long vv[W], acc[W];
+                    vload<W>(vp + (long long)v * W, vv);
+#pragma unroll
+                    for (int w = 0; w < W; ++w) {
+                        acc[w] = s_hacc[h][w];
+                        s_hacc[h][w] = 0ull;
+                    }
+                    settle<W>(a, p, vn, t, v, vv, acc, fin, grow);
+                }
+            }
+#pragma unroll
+            for (int w = 0; w < W; ++w) {
+                const unsigned long long x = warp_or_redux(grow[w]);
+                if (lane == 0 && x) atomicOr(&s_newmask[w], x);
+            }
+            if (threadIdx.x == 0) s_next = tbeg;
+            __syncthreads();
+            if (threadIdx.x < W && s_newmask[threadIdx.x]) {
+                atomicOr(&ctl->lanes_new[t % 3][threadIdx.x], s_newmask[threadIdx.x]);
+                s_newmask[threadIdx.x] = 0ull;
+            }
+            if (blockIdx.x == 0 && threadIdx.x >= 32 && threadIdx.x < 32 + W)
+                ctl->lanes_new[(t + 1) % 3][threadIdx.x - 32] = 0ull;
+            if (!ms_barrier(ctl, bar, bar_target, a.spin_limit, ctl->lanes_new[t % 3], W, s_lanes)) return;
+            int growing = 0;
+            bool done = true;
+#pragma unroll
+            for (int w = 0; w < W; ++w) {
+                growing += __popcll(s_lanes[w]);
+                done &= (fin[w] | ~s_lanes[w]) == ~0ull;
+            }
+            __syncthreads();  // every thread has read s_fin
+            if (threadIdx.x < W) s_fin[threadIdx.x] |= ~s_lanes[threadIdx.x];
+            __syncthreads();
+            if (growing) tlast = t;
+            if (a.trace && blockIdx.x == 0 && threadIdx.x == 0 && tslot < a.trace_cap) {
+                unsigned long long tnow;
+                asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(tnow));
+                long long* r = a.trace + 4 * (long long)tslot;
+                r[0] = b;
+                r[1] = t;
+                r[2] = growing;
+                r[3] = (long long)tnow;
+            }
+            ++tslot;
+            const uint64_t* tmp = vn;
+            vn = const_cast<uint64_t*>(vp);
+            vp = tmp;
+            if (done) break;
+        }
+        // ---- read-out: 32 consecutive vertices per warp, lane = vertex.  vp
+        // holds the final visited words; bit p of the level at which source s
+        // reached v is bit s of level plane p, OR-ed from the level arrays
+        // (and the stored planes of deeper levels).
+        const int np = tlast ? 32 - __clz(tlast) : 0;
+        const int tnb = min(tlast, p.nb_levels);
+        for (int gi = gA + warp; gi < gB; gi += kMsWarps) {
+            const int v = gi * 32 + lane;
+            const bool valid = v < n;
+            const int vr = valid ? v : n;  // the zero row stands in for lanes past n
+            unsigned long long R[W];
+            vload<W>(vp + (long long)vr * W, R);
+            if (valid) {
+                unsigned long long z[W];
+#pragma unroll
+                for (int w = 0; w < W; ++w) z[w] = 0ull;
+                vstore<W>(a.V0 + (long long)v * W, z);
+                vstore<W>(a.V1 + (long long)v * W, z);
+            }
+#pragma unroll
+            for (int hw = 0; hw < 2 * W; ++hw) {
+                const int sb = hw * 32;
+                if (sb >= kb) break;
+                const unsigned r32 = (unsigned)(R[hw >> 1] >> (32 * (hw & 1)));
+                // levels below 16 (bits 0..3) from the level arrays
+                unsigned pl0 = 0u, pl1 = 0u, pl2 = 0u, pl3 = 0u;
+                const unsigned* nb32 = reinterpret_cast<const unsigned*>(p.nbl + (long long)vr * W) + hw;
+                for (int t = 1; t <= tnb; ++t) {
+                    const unsigned x = __ldcg(nb32 + 2 * (t - 1) * stride);
+                    if (t & 1) pl0 |= x;
+                    if (t & 2) pl1 |= x;
+                    if (t & 4) pl2 |= x;
+                    if (t & 8) pl3 |= x;
+                }
+                const unsigned* pp = reinterpret_cast<const unsigned*>(p.planes + (long long)vr * W) + hw;
+                const bool deep = tlast > p.nb_levels;  // deeper levels are in the planes
+                unsigned vals[16];
+#pragma unroll
+                for (int i = 0; i < 16; ++i) vals[i] = 0u;
+                const unsigned rt = bit_transpose32(r32);  // lane = source sb + lane: reached vertices
+                unsigned cand = rt;
+                int ecc = 0;
+                long long dsum = 0;
+                for (int q = np - 1; q >= 0; --q) {
+                    unsigned d = q == 0 ? pl0 : q == 1 ? pl1 : q == 2 ? pl2 : q == 3 ? pl3 : 0u;
+                    if (deep) d |= __ldcg(pp + 2 * q * stride);
+#pragma unroll
+                    for (int i = 0; i < 16; ++i)
+                        vals[i] |= (((d >> (2 * i)) & 1u) | (((d >> (2 * i + 1)) & 1u) << 16)) << q;
+                    const unsigned dt = bit_transpose32(d);
+                    dsum += (long long)__popc(dt) << q;
+                    const unsigned c = cand & dt;
+                    if (c) {
+                        cand = c;
+                        ecc |= 1 << q;
+                    }
+                }
+                if (sb + lane < kb) {
+                    atomicAdd(&s_reached[sb + lane], __popc(rt));
+                    atomicAdd(reinterpret_cast<unsigned long long*>(&s_dsum[sb + lane]), (unsigned long long)dsum);
+                    atomicMax(&s_ecc[sb + lane], ecc);
+                }
+                if (valid) {
+                    const int nsrc = min(32, kb - sb);
+                    char* base;
+                    long long step;
+                    if (a.layout == DAWN_SOURCE_MAJOR) {
+                        const long long row0 = a.per_pass ? sb : s0 + sb;
+                        base = static_cast<char*>(a.out) + (row0 * a.out_row_stride + v) * a.dist_bytes;
+                        step = a.out_row_stride * a.dist_bytes;
+                    } else {
+                        base = static_cast<char*>(a.out) + ((long long)v * a.out_row_stride + s0 + sb) * a.dist_bytes;
+                        step = a.dist_bytes;
+                    }
+#pragma unroll
+                    for (int i = 0; i < 32; ++i) {
+                        if (i >= nsrc) break;
+                        const int d = (int)((vals[i >> 1] >> (16 * (i & 1))) & 0xFFFFu);
+                        const int val = ((r32 >> i) & 1u) ? d : -1;
+                        if (a.dist_bytes == 2) *reinterpret_cast<int16_t*>(base + i * step) = (int16_t)val;
+                        else *reinterpret_cast<int32_t*>(base + i * step) = val;
+                    }
+                }
+            }
+        }
+        __syncthreads();  // every warp's read-out sums are in
+        // ---- batch reductions: per-CTA partials, then one thread per lane
+        for (int s = threadIdx.x; s < L; s += kMsThreads) {
+            a.part_i[((long long)blockIdx.x * 2 + 0) * kMsMaxLanes + s] = s_reached[s];
+            a.part_i[((long long)blockIdx.x * 2 + 1) * kMsMaxLanes + s] = s_ecc[s];
+            a.part_l[(long long)blockIdx.x * kMsMaxLanes + s] = s_dsum[s];
+            s_reached[s] = 0;
+            s_ecc[s] = 0;
+            s_dsum[s] = 0;
+        }
+        if (!ms_barrier(ctl, bar, bar_target, a.spin_limit)) return;
+        if (gtid < kb) {
+            const int s = (int)gtid;
+            int r = 0, e = 0;
+            long long sum = 0;
+            for (int c = 0; c < (int)gridDim.x; ++c) {
+                r += __ldcg(a.part_i + ((long long)c * 2 + 0) * kMsMaxLanes + s);
+                e = max(e, __ldcg(a.part_i + ((long long)c * 2 + 1) * kMsMaxLanes + s));
+                sum += __ldcg(a.part_l + (long long)c * kMsMaxLanes + s);
+            }
+            a.reached[s0 + s] = r;
+            a.ecc[s0 + s] = e;
+            a.dsum[s0 + s] = sum;
+        }
+        // the next pass's first barrier orders these reads before the partials are rewritten
+    }
+    if (gtid == 0) ctl->bar[a.bar_parity ^ 1].count = 0;
+}
+
+__global__ void ms_sell_fill_kernel(const int4* __restrict__ slices, int32_t ns, const int2* __restrict__ vd,
+                                    const int32_t* __restrict__ in_ptr, const int32_t* __restrict__ in_idx,
+                                    int32_t* __restrict__ sell) {
+    const int lane = threadIdx.x & 31;
+    const long long nw = (long long)gridDim.x * (blockDim.x >> 5);
+    for (long long s = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); s < ns; s += nw) {
+        const int4 tk = slices[s];
+        const int2 x = vd[s * 32 + lane];
+        const int b = x.x >= 0 ? in_ptr[x.x] : 0;
+        for (int j = 0; j < tk.z; ++j) sell[(long long)tk.y + 32LL * j + lane] = j < x.y ? in_idx[b + j] : -1;
+    }
+}
+
+// Cut the in-arc rows into the sliced kernel's tasks (once per graph).
+int ms_plan_build(dawn_graph* g, cudaStream_t st) {
+    if (g->ms_plan && static_cast<MsPlan*>(g->ms_plan)->sms == g->sms) return DAWN_OK;
+    ms_release(g);
+    const int n = g->n, sms = g->sms;
+    std::vector<int32_t> ip((size_t)n + 1);
+    DAWN_CUDA_TRY(cudaMemcpyAsync(ip.data(), g->in_ptr, sizeof(int32_t) * ((size_t)n + 1), cudaMemcpyDeviceToHost, st));
+    DAWN_CUDA_TRY(cudaStreamSynchronize(st));
+    auto deg = [&](int v) { return ip[(size_t)v + 1] - ip[v]; };
+    // Short rows of vertices outside the largest component go last: lanes of
+    // the large component never reach them, so their slices stay uncovered
+    // all pass, and grouped they keep few slices busy.
+    int32_t big = 0;
+    for (int32_t c : g->csize_host) big = std::max(big, c);
+    auto minor = [&](int v) { return !g->csize_host.empty() && g->csize_host[(size_t)v] < big ? 1 : 0; };
+    std::vector<int32_t> order;
+    order.reserve((size_t)n);
+    for (int v = 0; v < n; ++v)
+        if (deg(v) > 0) order.push_back(v);
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+        const int dx = deg(x), dy = deg(y);
+        if ((dx > kSellDeg) != (dy > kSellDeg)) return dx > kSellDeg;
+        if (dx <= kSellDeg && minor(x) != minor(y)) return minor(x) < minor(y);
+        return dx > dy;
+    });
+    const long long M = ip[(size_t)n];
+    const long long nwarps = (long long)sms * kMsWarps;
+
+    // Estimated warp time: the dependent memory round trips (kTrip each;
+    // levels are latency bound) plus one per warp step of 32 arcs.
+    auto piece_cost = [](int len) -> long long {
+        const int rounds = (len + 127) / 128, steps = (len + 31) / 32;
+        return (long long)kTrip * (2 + rounds) + steps;
+    };
+    auto slice_cost = [](int D) -> long long {
+        const int rounds = (D + 3) / 4;
+        return (long long)kTrip * (2 + std::max(0, rounds - 1) + (rounds > 2 ? rounds - 2 : 0)) + D;
+    };
+    struct Unit {
+        int first, count;  // tasks
+        long long cost;    // piece_cost / slice_cost of its tasks
+        int split;         // a row cut into several pieces
+    };
+    std::vector<int4> tasks;
+    std::vector<Unit> units;
+    std::vector<int2> vd;
+    std::vector<int32_t> cta_task((size_t)sms + 1), cta_hub((size_t)sms + 1), hub_v;
+    long long piece = std::max<long long>(kPieceMin, ((M / (2 * nwarps)) + 31) / 32 * 32);
+    long long sell_len = 0;
+    int nslices = 0, max_hubs = 0, max_tasks = 0, first_slice = 0;
+    std::vector<int4> slice_tasks;  // the slice tasks in slice-id order (for filling sell_idx)
+    for (;; piece *= 2) {
+        tasks.clear();
+        units.clear();
+        vd.clear();
+        hub_v.clear();
+        size_t i = 0;
+        for (; i < order.size() && deg(order[i]) > kSellDeg; ++i) {
+            const int v = order[i], d = deg(v), b = ip[v];
+            if (d <= piece) {
+                units.push_back({(int)tasks.size(), 1, piece_cost(d), 0});
+                tasks.push_back(make_int4(v, b, b + d, -1));
+            } else {
+                const long long np0 = (d + piece - 1) / piece;
+                const int ps = (int)(((d + np0 - 1) / np0 + 31) / 32 * 32);
+                Unit u{(int)tasks.size(), 0, kTrip, 1};
+                for (int j0 = b; j0 < b + d; j0 += ps) {
+                    const int j1 = std::min(b + d, j0 + ps);
+                    tasks.push_back(make_int4(v, j0, j1, 0));
+                    u.count += 1;
+                    u.cost += piece_cost(j1 - j0);
+                }
+                units.push_back(u);
+            }
+        }
+        first_slice = (int)tasks.size();
+        sell_len = 0;
+        nslices = 0;
+        for (; i < order.size(); i += 32) {
+            int D = 0;
+            for (size_t l = 0; l < 32; ++l) {
+                const size_t idx = i + l;
+                vd.push_back(idx < order.size() ? make_int2(order[idx], deg(order[idx])) : make_int2(-1, 0));
+                if (idx < order.size()) D = std::max(D, deg(order[idx]));
+            }
+            units.push_back({(int)tasks.size(), 1, slice_cost(D), 0});
+            tasks.push_back(make_int4(-1 - nslices, (int)sell_len, D, 0));
+            sell_len += 32LL * D;
+            ++nslices;
+            if (sell_len >= (1LL << 31)) return fail(DAWN_E_INVALID, "graph too large for the sliced batched kernel");
+        }
+        // Units to CTAs, largest first, each to the least loaded CTA so far:
+        // every CTA gets a mix of row lengths, and the rows that stay
+        // uncovered longest (the short ones) are spread over the grid.
+        std::vector<std::vector<int>> mine((size_t)sms);
+        {
+            using Load = std::pair<long long, int>;
+            std::priority_queue<Load, std::vector<Load>, std::greater<Load>> heap;
+            for (int c = 0; c < sms; ++c) heap.push({0, c});
+            for (size_t x = 0; x < units.size(); ++x) {
+                Load l = heap.top();
+                heap.pop();
+                mine[(size_t)l.second].push_back((int)x);
+                l.first += units[x].cost;
+                heap.push(l);
+            }
+        }
+        std::vector<int4> by_cta;
+        by_cta.reserve(tasks.size());
+        max_hubs = 0;
+        max_tasks = 0;
+        for (int c = 0; c < sms; ++c) {
+            cta_task[(size_t)c] = (int)by_cta.size();
+            cta_hub[(size_t)c] = (int)hub_v.size();
+            int local = 0;
+            for (int x : mine[(size_t)c]) {
+                const Unit& u = units[(size_t)x];
+                for (int t = u.first; t < u.first + u.count; ++t) {
+                    int4 tk = tasks[(size_t)t];
+                    if (u.split) tk.w = local;
+                    by_cta.push_back(tk);
+                }
+                if (u.split) {
+                    hub_v.push_back(tasks[(size_t)u.first].x);
+                    ++local;
+                }
+            }
+            max_hubs = std::max(max_hubs, local);
+            max_tasks = std::max(max_tasks, (int)by_cta.size() - cta_task[(size_t)c]);
+        }
+        cta_task[(size_t)sms] = (int)by_cta.size();
+        cta_hub[(size_t)sms] = (int)hub_v.size();
+        slice_tasks.assign(tasks.begin() + first_slice, tasks.end());
+        tasks.swap(by_cta);
+        if (max_hubs <= kHubMax) break;
+    }
+
+    auto* pl = new MsPlan();
+    pl->sms = sms;
+    pl->ntasks = (int)tasks.size();
+    pl->nhubs = (int)hub_v.size();
+    pl->nslices = nslices;
+    pl->piece = (int)piece;
+    pl->max_hubs = max_hubs;
+    pl->max_tasks = max_tasks;
+    pl->sell_len = sell_len;
+    auto al = [](size_t b) { return (b + 255) / 256 * 256; };
+    const size_t o_tasks = 0, o_ct = o_tasks + al(sizeof(int4) * tasks.size() + 16);
+    const size_t o_ch = o_ct + al(sizeof(int32_t) * ((size_t)sms + 1));
+    const size_t o_hv = o_ch + al(sizeof(int32_t) * ((size_t)sms + 1));
+    const size_t o_vd = o_hv + al(sizeof(int32_t) * hub_v.size() + 4);
+    const size_t o_si = o_vd + al(sizeof(int2) * vd.size() + 8);
+    const size_t bytes = o_si + al(sizeof(int32_t) * (size_t)sell_len + 4);
+    cudaError_t e = cudaMalloc(&pl->blob, bytes);
+    if (e != cudaSuccess) {
+        delete pl;
+        return cuda_fail(e, "cudaMalloc (batched plan)", __FILE__, __LINE__);
+    }
+    g->ms_plan = pl;
+    char* base = static_cast<char*>(pl->blob);
+    pl->tasks = reinterpret_cast<int4*>(base + o_tasks);
+    pl->cta_task = reinterpret_cast<int32_t*>(base + o_ct);
+    pl->cta_hub = reinterpret_cast<int32_t*>(base + o_ch);
+    pl->hub_v = reinterpret_cast<int32_t*>(base + o_hv);
+    pl->sell_vd = reinterpret_cast<int2*>(base + o_vd);
+    pl->sell_idx = reinterpret_cast<int32_t*>(base + o_si);
+    if (!tasks.empty())
+        DAWN_CUDA_TRY(cudaMemcpyAsync(pl->tasks, tasks.data(), sizeof(int4) * tasks.size(), cudaMemcpyHostToDevice, st));
+    DAWN_CUDA_TRY(cudaMemcpyAsync(pl->cta_task, cta_task.data(), sizeof(int32_t) * cta_task.size(), cudaMemcpyHostToDevice, st));
+    DAWN_CUDA_TRY(cudaMemcpyAsync(pl->cta_hub, cta_hub.data(), sizeof(int32_t) * cta_hub.size(), cudaMemcpyHostToDevice, st));
+    if (!hub_v.empty())
+        DAWN_CUDA_TRY(cudaMemcpyAsync(pl->hub_v, hub_v.data(), sizeof(int32_t) * hub_v.size(), cudaMemcpyHostToDevice, st));
+    if (nslices > 0) {
+        int4* sl = nullptr;  // slice descriptors in slice-id order
+        DAWN_CUDA_TRY(cudaMallocAsync((void**)&sl, sizeof(int4) * slice_tasks.size(), st));
+        DAWN_CUDA_TRY(cudaMemcpyAsync(sl, slice_tasks.data(), sizeof(int4) * slice_tasks.size(), cudaMemcpyHostToDevice, st));
+        DAWN_CUDA_TRY(cudaMemcpyAsync(pl->sell_vd, vd.data(), sizeof(int2) * vd.size(), cudaMemcpyHostToDevice, st));
+        ms_sell_fill_kernel<<<sms * 4, 256, 0, st>>>(sl, nslices, pl->sell_vd, g->in_ptr, g->in_idx, pl->sell_idx);
+        DAWN_CUDA_TRY(cudaGetLastError());
+        DAWN_CUDA_TRY(cudaFreeAsync(sl, st));
+    }
+    DAWN_CUDA_TRY(cudaStreamSynchronize(st));  // the host vectors go out of scope
+    return DAWN_OK;
+}
+
+// The per-level new-bit arrays (levels 1 .. ms_nb_levels, sized for W = 4):
+// as many as kNbBudget holds, at least 4, at most kNbLevelsMax.
+int ms_nb_alloc(dawn_graph* g) {
+    if (g->ms_nb) return DAWN_OK;
+    const size_t per = sizeof(uint64_t) * 4 * ((size_t)g->n + 1);
+    const int levels = (int)std::max<size_t>(4, std::min<size_t>(kNbLevelsMax, kNbBudget / per));
+    DAWN_CUDA_TRY(cudaMalloc((void**)&g->ms_nb, per * (size_t)levels));
+    g->ms_nb_levels = levels;
+    return DAWN_OK;
+}
+
+// Level planes for levels past the new-bit arrays (sized for W = 4).
+int ms_planes_alloc(dawn_graph* g, int planes) {
+    if (g->ms_planes && g->ms_planes_cap >= planes) return DAWN_OK;
+    if (g->ms_planes) cudaFree(g->ms_planes);
+    g->ms_planes = nullptr;
+    g->ms_planes_cap = 0;
+    DAWN_CUDA_TRY(cudaMalloc((void**)&g->ms_planes, sizeof(uint64_t) * 4 * ((size_t)g->n + 1) * (size_t)planes));
+    g->ms_planes_cap = planes;
+    return DAWN_OK;
+}
+
+template <int W>
+int ms_launch_sliced_w(dawn_graph* g, MsArgs& a, MsSliced& p, cudaStream_t st) {
+    dim3 grid(g->sms), block(kMsThreads);
+    void* args[] = {&a, &p};
+    DAWN_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)msbfs_sliced_kernel<W>, grid, block, args, 0, st));
     return DAWN_OK;
 }
 
@@ -694,6 +1501,11 @@ int msbfs_run(dawn_graph* g, const int32_t* sources, int32_t k, void* dist_block
     if (lanes == 0) lanes = k <= 64 ? 64 : (k <= 128 ? 128 : 256);
     const int W = lanes / 64;
     const long long spin = (opts && opts->spin_limit > 0) ? opts->spin_limit : kDefaultSpin;
+    const int want = opts ? opts->kernel : 0;
+    if (want != 0 && want != DAWN_MSBFS_SLICED && want != DAWN_MSBFS_PER_LEVEL)
+        return fail(DAWN_E_INVALID, "kernel = %d: need 0, DAWN_MSBFS_SLICED or DAWN_MSBFS_PER_LEVEL", want);
+    const size_t plane_bytes = sizeof(uint64_t) * 4 * ((size_t)g->n + 1);  // one level array or plane
+    const bool sliced = !nostore && (want == DAWN_MSBFS_SLICED || (want == 0 && !g->ms_sliced_off));
 
     // sources: checked on the host whatever memory they live in
     std::vector<int32_t> hsrc((size_t)k);
@@ -703,6 +1515,15 @@ int msbfs_run(dawn_graph* g, const int32_t* sources, int32_t k, void* dist_block
 
     int rc = ms_workspace(g, W);
     if (rc != DAWN_OK) return rc;
+    if (sliced) {
+        if ((rc = ms_plan_build(g, st)) != DAWN_OK) return rc;
+        if ((rc = ms_nb_alloc(g)) != DAWN_OK) return rc;
+        if (g->ms_vis_dirty) {
+            DAWN_CUDA_TRY(cudaMemsetAsync(g->ms_vis[0], 0, plane_bytes, st));
+            DAWN_CUDA_TRY(cudaMemsetAsync(g->ms_vis[1], 0, plane_bytes, st));
+            g->ms_vis_dirty = 0;
+        }
+    }
 
     const size_t cell = (size_t)dist_bytes;
     const bool out_dev = dist_block && is_device_ptr(dist_block);
@@ -784,11 +1605,29 @@ int msbfs_run(dawn_graph* g, const int32_t* sources, int32_t k, void* dist_block
         a.out_row_stride = layout == DAWN_SOURCE_MAJOR ? (long long)g->n : (long long)k;
     }
     int lrc = DAWN_OK;
-    if (e == cudaSuccess) {
+    if (e == cudaSuccess && sliced) {
+        const MsPlan* pl = static_cast<const MsPlan*>(g->ms_plan);
+        MsSliced sp;
+        sp.tasks = pl->tasks;
+        sp.cta_task = pl->cta_task;
+        sp.cta_hub = pl->cta_hub;
+        sp.hub_v = pl->hub_v;
+        sp.sell_vd = pl->sell_vd;
+        sp.sell_idx = pl->sell_idx;
+        sp.nbl = g->ms_nb;
+        sp.nb_levels = std::min(kNbLevelsMax, g->ms_nb_levels * 4 / W);
+        sp.planes = g->ms_planes;
+        sp.planes_cap = g->ms_planes ? std::min(kPlanesMax, g->ms_planes_cap * 4 / W) : 0;
+        if (W == 1) lrc = ms_launch_sliced_w<1>(g, a, sp, st);
+        else if (W == 2) lrc = ms_launch_sliced_w<2>(g, a, sp, st);
+        else lrc = ms_launch_sliced_w<4>(g, a, sp, st);
+        if (lrc == DAWN_OK) g->ms_launches += 1;
+    } else if (e == cudaSuccess) {
         if (W == 1) lrc = ms_launch_w<1>(g, a, st);
         else if (W == 2) lrc = ms_launch_w<2>(g, a, st);
         else lrc = ms_launch_w<4>(g, a, st);
         if (lrc == DAWN_OK) g->ms_launches += 1;
+        g->ms_vis_dirty = 1;  // the per-level kernel leaves its last pass's words behind
     }
     if (e == cudaSuccess && lrc == DAWN_OK && dist_block && !out_dev)
         e = cudaMemcpyAsync(dist_block, d_out, (size_t)k * g->n * cell, cudaMemcpyDeviceToHost, st);
@@ -817,9 +1656,23 @@ int msbfs_run(dawn_graph* g, const int32_t* sources, int32_t k, void* dist_block
     if (e != cudaSuccess) return cuda_fail(e, "dawn_msbfs", __FILE__, __LINE__);
     if (status != DEV_OK) {
         DAWN_CUDA_TRY(cudaMemsetAsync(ctl, 0, sizeof(MsCtl), st));
-        // a pass cut short can leave accumulator slots set
+        // a pass cut short can leave accumulator slots and visited words set
         DAWN_CUDA_TRY(cudaMemsetAsync(g->ms_acc, 0, sizeof(uint64_t) * (size_t)g->n * 4, st));
+        g->ms_vis_dirty = 1;
         DAWN_CUDA_TRY(cudaStreamSynchronize(st));
+        if (status == DEV_PLANES) {
+            // more levels than the level arrays hold: 15 planes, else the per-level kernel
+            if (g->ms_planes_cap < kPlanesMax && (size_t)kPlanesMax * plane_bytes <= kPlanesBudget) {
+                if ((rc = ms_planes_alloc(g, kPlanesMax)) != DAWN_OK) return rc;
+            } else if (want == DAWN_MSBFS_SLICED) {
+                return fail(DAWN_E_INVALID, "a pass needs more levels than the sliced kernel's planes hold "
+                                            "(%d); use DAWN_MSBFS_PER_LEVEL", (1 << kPlanesMax) - 1);
+            } else {
+                g->ms_sliced_off = 1;
+            }
+            return msbfs_run(g, sources, k, dist_block, dist_bytes, layout, ecc, dsum, reached, opts, st,
+                             closeness, harmonic, summary, nostore);
+        }
         if (status == DEV_OVERFLOW) return fail(DAWN_E_OVERFLOW, "a distance exceeded the int16 range (32767)");
         if (status == DEV_TIMEOUT) return fail(DAWN_E_TIMEOUT, "a grid-barrier wait on the device ran out of its spin budget");
         return fail(DAWN_E_CUDA, "unknown device status %d", status);
@@ -834,6 +1687,22 @@ int msbfs_run(dawn_graph* g, const int32_t* sources, int32_t k, void* dist_block
 }
 
 }  // namespace
+
+void ms_release(dawn_graph* g) {
+    if (g->ms_plan) {
+        auto* pl = static_cast<MsPlan*>(g->ms_plan);
+        if (pl->blob) cudaFree(pl->blob);
+        delete pl;
+        g->ms_plan = nullptr;
+    }
+    if (g->ms_planes) cudaFree(g->ms_planes);
+    g->ms_planes = nullptr;
+    g->ms_planes_cap = 0;
+    if (g->ms_nb) cudaFree(g->ms_nb);
+    g->ms_nb = nullptr;
+    g->ms_nb_levels = 0;
+}
+
 }  // namespace dawn
 
 extern "C" {

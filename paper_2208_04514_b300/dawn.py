@@ -35,6 +35,9 @@ DAWN_MODE_PULL = 2
 DAWN_SOURCE_MAJOR = 0
 DAWN_VERTEX_MAJOR = 1
 
+DAWN_MSBFS_SLICED = 1
+DAWN_MSBFS_PER_LEVEL = 2
+
 DAWN_REQ_PENDING = 0
 DAWN_REQ_RUNNING = 1
 DAWN_REQ_DONE = 2
@@ -83,7 +86,7 @@ class dawn_tuning(ctypes.Structure):
 
 class dawn_msbfs_opts(ctypes.Structure):
     _fields_ = [("lanes", ctypes.c_int32), ("trace_cap", ctypes.c_int32), ("spin_limit", ctypes.c_int64),
-                ("trace", ctypes.c_void_p)]
+                ("trace", ctypes.c_void_p), ("kernel", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class dawn_wsssp_stats(ctypes.Structure):

@@ -2,10 +2,12 @@
 oracle's SOVM-per-source batch (Sec. 3.3, APSP as one SSSP per source),
 element by element.  Distances are integers: bit-exact.
 
-Covers every lane width (64/128/256), int16 and int32 blocks, both layouts,
-host and device outputs, ragged source counts (not a multiple of 64),
-duplicate and isolated sources, directed graphs (pull over the in-adjacency),
-the full-size RMAT scale-16 all-sources workload (1,024 sampled rows bit-exact,
+Covers both kernels (DAWN_MSBFS_SLICED and DAWN_MSBFS_PER_LEVEL), every lane
+width (64/128/256), int16 and int32 blocks, both layouts, host and device
+outputs, ragged source counts (not a multiple of 64), duplicate and isolated
+sources, directed graphs (pull over the in-adjacency), rows split into pieces
+(a star's hub), more levels than the sliced kernel's first planes hold, the
+full-size RMAT scale-16 all-sources workload (1,024 sampled rows bit-exact,
 every source's reached count = its component size), the int16 overflow
 report and the bounded-wait timeout.
 """
@@ -24,7 +26,10 @@ def upload(dawn, g):
                                   flags=dawn.DAWN_SYMMETRIC if g.symmetric else dawn.DAWN_DIRECTED)
 
 
-def run(dawn, h, n, srcs, lanes, dist_bytes=2, layout=0, device=True, with_block=True):
+KERNELS = [1, 2]  # DAWN_MSBFS_SLICED, DAWN_MSBFS_PER_LEVEL
+
+
+def run(dawn, h, n, srcs, lanes, dist_bytes=2, layout=0, device=True, with_block=True, kernel=0):
     k = len(srcs)
     dt = torch.int16 if dist_bytes == 2 else torch.int32
     shape = (k, n) if layout == 0 else (n, k)
@@ -40,7 +45,7 @@ def run(dawn, h, n, srcs, lanes, dist_bytes=2, layout=0, device=True, with_block
         dsum = np.zeros(k, dtype=np.int64)
         reached = np.zeros(k, dtype=np.int32)
         src = np.asarray(srcs, dtype=np.int32)
-    dawn.dawn_msbfs_ex(h, src, k, block, dist_bytes, layout, ecc, dsum, reached, {"lanes": lanes})
+    dawn.dawn_msbfs_ex(h, src, k, block, dist_bytes, layout, ecc, dsum, reached, {"lanes": lanes, "kernel": kernel})
     conv = (lambda x: x.cpu().numpy()) if device else (lambda x: x)
     b = None
     if with_block:
@@ -67,16 +72,18 @@ def test_small_digraphs_all_sources(dawn, seed):
     h = upload(dawn, g)
     try:
         srcs = np.arange(g.n, dtype=np.int32)
-        for lanes in (64, 128, 256):
-            check(g, srcs, run(dawn, h, g.n, srcs, lanes))
+        for kernel in KERNELS:
+            for lanes in (64, 128, 256):
+                check(g, srcs, run(dawn, h, g.n, srcs, lanes, kernel=kernel))
     finally:
         dawn.dawn_graph_free(h)
 
 
+@pytest.mark.parametrize("kernel", KERNELS)
 @pytest.mark.parametrize("lanes", [64, 128, 256])
 @pytest.mark.parametrize("dist_bytes,layout,device", [(2, 0, True), (4, 0, True), (2, 1, True),
                                                        (4, 1, False), (2, 0, False)])
-def test_rmat12_ragged_batches(dawn, lanes, dist_bytes, layout, device):
+def test_rmat12_ragged_batches(dawn, lanes, dist_bytes, layout, device, kernel):
     g = gg.rmat(12, seed=2)
     deg = g.out_degree()
     rng = np.random.default_rng(lanes + dist_bytes)
@@ -86,7 +93,7 @@ def test_rmat12_ragged_batches(dawn, lanes, dist_bytes, layout, device):
     srcs[11] = int(np.argmax(deg))                            # the largest hub
     h = upload(dawn, g)
     try:
-        check(g, srcs, run(dawn, h, g.n, srcs, lanes, dist_bytes, layout, device))
+        check(g, srcs, run(dawn, h, g.n, srcs, lanes, dist_bytes, layout, device, kernel=kernel))
     finally:
         dawn.dawn_graph_free(h)
 
@@ -96,8 +103,54 @@ def test_directed_graph_batches(dawn):
     h = upload(dawn, g)
     try:
         srcs = np.arange(0, g.n, 7, dtype=np.int32)
-        for lanes in (64, 256):
-            check(g, srcs, run(dawn, h, g.n, srcs, lanes))
+        # alternating kernels on one handle: each starts from what the other left
+        for kernel in (2, 1, 2, 1):
+            for lanes in (64, 256):
+                check(g, srcs, run(dawn, h, g.n, srcs, lanes, kernel=kernel))
+    finally:
+        dawn.dawn_graph_free(h)
+
+
+def test_split_rows_and_short_rows(dawn):
+    """A star whose hub has 5,000 in-arcs (a row cut into pieces), leaves of
+    in-degree 1..3 (one vertex per lane), a tail of 20 mid-degree rows and
+    isolated vertices, directed: the pieces' shared-memory OR and the slices
+    against the oracle, from hub, leaf, tail and isolated sources."""
+    rng = np.random.default_rng(3)
+    nleaf, ntail = 5000, 20
+    n = 1 + nleaf + ntail + 7
+    leaves = np.arange(1, nleaf + 1)
+    tail = np.arange(nleaf + 1, nleaf + 1 + ntail)
+    src = [leaves, np.zeros(nleaf, np.int64)]  # leaf -> hub
+    dst = [np.zeros(nleaf, np.int64), leaves]  # hub -> leaf
+    extra = rng.integers(1, nleaf + 1, (3000, 2))  # leaf -> leaf, in-degree up to a few
+    src.append(extra[:, 0]); dst.append(extra[:, 1])
+    for i, t in enumerate(tail):  # tail vertex t: in-arcs from 40 + i leaves, out-arc to the next
+        fr = rng.choice(leaves, 40 + i, replace=False)
+        src.append(fr); dst.append(np.full(fr.size, t))
+        if i + 1 < ntail:
+            src.append([t]); dst.append([t + 1])
+    g = gg.from_arcs(n, np.concatenate(src), np.concatenate(dst))
+    h = upload(dawn, g)
+    try:
+        srcs = np.r_[0, 1, 2, tail[0], tail[-1], n - 1, rng.integers(0, n, 100)].astype(np.int32)
+        for kernel in KERNELS:
+            check(g, srcs, run(dawn, h, g.n, srcs, 128, kernel=kernel))
+    finally:
+        dawn.dawn_graph_free(h)
+
+
+def test_more_levels_than_first_planes(dawn):
+    """A path of 700 vertices: 699 levels, past the 255 that the sliced
+    kernel's first planes hold; it widens them and runs the call again."""
+    n = 700
+    s = np.arange(n - 1)
+    g = gg.from_arcs(n, np.r_[s, s + 1], np.r_[s + 1, s], symmetric=True)
+    h = upload(dawn, g)
+    try:
+        srcs = np.array([0, 350, n - 1, 5], dtype=np.int32)
+        for dist_bytes in (2, 4):
+            check(g, srcs, run(dawn, h, n, srcs, 64, dist_bytes, kernel=1))
     finally:
         dawn.dawn_graph_free(h)
 
@@ -161,9 +214,13 @@ def test_bad_arguments_and_timeout(dawn):
         with pytest.raises(dawn.DawnError):
             dawn.dawn_msbfs_ex(h, src, 3, None, 3, 0, None, None, None)
         with pytest.raises(dawn.DawnError) as ei:
-            dawn.dawn_msbfs_ex(h, src, 3, None, 2, 0, None, None, None, {"spin_limit": 1})
-        assert ei.value.code == dawn.DAWN_E_TIMEOUT
-        check(g, src, run(dawn, h, g.n, src, 64))  # usable again afterwards
+            dawn.dawn_msbfs_ex(h, src, 3, None, 2, 0, None, None, None, {"kernel": 3})
+        assert ei.value.code == dawn.DAWN_E_INVALID
+        for kernel in KERNELS:
+            with pytest.raises(dawn.DawnError) as ei:
+                dawn.dawn_msbfs_ex(h, src, 3, None, 2, 0, None, None, None, {"spin_limit": 1, "kernel": kernel})
+            assert ei.value.code == dawn.DAWN_E_TIMEOUT
+            check(g, src, run(dawn, h, g.n, src, 64, kernel=kernel))  # usable again afterwards
     finally:
         dawn.dawn_graph_free(h)
 
