@@ -696,7 +696,7 @@ struct MsPlan {
     int32_t ntasks = 0, nhubs = 0, nslices = 0, piece = 0, max_hubs = 0, max_tasks = 0;
     long long sell_len = 0;
     void* blob = nullptr;        // one device allocation holding the arrays below
-    int4* tasks = nullptr;       // piece {v, first arc, end arc, CTA hub slot or -1}; slice {-1 - id, offset, width, 0}
+    int4* tasks = nullptr;       // piece {v, first arc, end arc, -1 or CTA slot | pieces << 8}; slice {-1 - id, offset, width, 0}
     int32_t* cta_task = nullptr; // [sms + 1]: CTA c runs tasks [cta_task[c], cta_task[c + 1])
     int32_t* cta_hub = nullptr;  // [sms + 1]: and owns split rows [cta_hub[c], cta_hub[c + 1]) of hub_v
     int32_t* hub_v = nullptr;
@@ -705,6 +705,8 @@ struct MsPlan {
 };
 
 struct MsSliced {
+    const int32_t* __restrict__ out_ptr;  // CSR: level 1 pushes along the sources' out-arcs
+    const int32_t* __restrict__ out_idx;
     const int4* __restrict__ tasks;
     const int32_t* __restrict__ cta_task;
     const int32_t* __restrict__ cta_hub;
@@ -854,6 +856,61 @@ __device__ __forceinline__ void settle(const MsArgs& a, const MsSliced& p, uint6
     }
 }
 
+// Level 1 as a push: bit s to every out-neighbour v != src of source s, in
+// the next visited words and NB[1]; the grid splits the sources' out-arcs
+// evenly (s_pre: prefix of their out-degrees).  Kept out of line: it runs
+// once per pass and its registers would crowd the level loop.
+template <int W>
+__device__ __noinline__ void push_sources(const MsArgs& a, const MsSliced& p, int kb, const int* s_pre,
+                                          const int* s_src, unsigned long long* s_newmask) {
+    const long long total = s_pre[kb];
+    const long long nthreads = (long long)gridDim.x * blockDim.x;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += nthreads) {
+        int lo = 0, hi = kb - 1;  // the last s with s_pre[s] <= e
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (s_pre[mid] <= e) lo = mid; else hi = mid - 1;
+        }
+        const int src = s_src[lo];
+        const int v = __ldg(p.out_idx + __ldg(p.out_ptr + src) + (e - s_pre[lo]));
+        if (v == src) continue;
+        const unsigned long long bit = 1ull << (lo & 63);
+        atomicOr(reinterpret_cast<unsigned long long*>(&a.V1[(long long)v * W + (lo >> 6)]), bit);
+        atomicOr(reinterpret_cast<unsigned long long*>(&p.nbl[(long long)v * W + (lo >> 6)]), bit);
+        atomicOr(&s_newmask[lo >> 6], bit);
+    }
+}
+
+// After a level's barrier (s_lanes = lanes that grew at level t): finished
+// lanes, the last level with growth, the trace record.  True when every
+// lane has finished.
+template <int W>
+__device__ __forceinline__ bool level_end(const MsArgs& a, int b, int t, const unsigned long long* s_lanes,
+                                          unsigned long long* s_fin, int& tlast, int& tslot) {
+    int growing = 0;
+    bool done = true;
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+        growing += __popcll(s_lanes[w]);
+        done &= (s_fin[w] | ~s_lanes[w]) == ~0ull;
+    }
+    __syncthreads();  // every thread has read s_fin
+    if (threadIdx.x < W) s_fin[threadIdx.x] |= ~s_lanes[threadIdx.x];
+    __syncthreads();
+    if (growing) tlast = t;
+    if (a.trace && blockIdx.x == 0 && threadIdx.x == 0 && tslot < a.trace_cap) {
+        unsigned long long tnow;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(tnow));
+        long long* r = a.trace + 4 * (long long)tslot;
+        r[0] = b;
+        r[1] = t;
+        r[2] = growing;
+        r[3] = (long long)tnow;
+    }
+    ++tslot;
+    return done;
+}
+
 template <int W>
 __global__ void __launch_bounds__(kMsThreads, 1) msbfs_sliced_kernel(MsArgs a, MsSliced p) {
     __shared__ unsigned long long s_hacc[kHubMax][W];
@@ -865,6 +922,9 @@ __global__ void __launch_bounds__(kMsThreads, 1) msbfs_sliced_kernel(MsArgs a, M
     __shared__ long long s_dsum[kMsMaxLanes];
     __shared__ int4 s_tasks[kTaskSmem];
     __shared__ unsigned char s_cov[kTaskSmem];  // consecutive levels a task was fully covered
+    __shared__ int s_hcnt[kHubMax];             // pieces of each split row done this level
+    __shared__ int s_pre[kMsMaxLanes + 1];      // level 1: prefix of the sources' out-degrees
+    __shared__ int s_src[kMsMaxLanes];
     __shared__ int s_next, s_status;
 
     MsCtl* ctl = a.ctl;
@@ -882,12 +942,13 @@ __global__ void __launch_bounds__(kMsThreads, 1) msbfs_sliced_kernel(MsArgs a, M
     const int nbatches = (a.k + L - 1) / L;
     const int tbeg = __ldg(p.cta_task + blockIdx.x), tend = __ldg(p.cta_task + blockIdx.x + 1);
     const int tsm = min(tend - tbeg, kTaskSmem);
-    const int h0 = __ldg(p.cta_hub + blockIdx.x), nh = __ldg(p.cta_hub + blockIdx.x + 1) - h0;
+    const int h0 = __ldg(p.cta_hub + blockIdx.x);
     const int ngroups = (n + 31) >> 5;
     const int gA = (int)((long long)ngroups * blockIdx.x / gridDim.x);
     const int gB = (int)((long long)ngroups * (blockIdx.x + 1) / gridDim.x);
 
     for (int i = threadIdx.x; i < kHubMax * W; i += kMsThreads) (&s_hacc[0][0])[i] = 0ull;
+    for (int i = threadIdx.x; i < kHubMax; i += kMsThreads) s_hcnt[i] = 0;
     for (int i = threadIdx.x; i < tsm; i += kMsThreads) s_tasks[i] = __ldg(p.tasks + tbeg + i);
     for (int i = threadIdx.x; i < kMsMaxLanes; i += kMsThreads) {
         s_reached[i] = 0;
@@ -900,29 +961,70 @@ __global__ void __launch_bounds__(kMsThreads, 1) msbfs_sliced_kernel(MsArgs a, M
     for (int b = 0; b < nbatches; ++b) {
         const int s0 = b * L;
         const int kb = min(L, a.k - s0);
-        // ---- seeds: both visited buffers are zero here (cleared by the
-        // previous pass's read-out, or since allocation); NB[1] is zeroed
-        if (gtid < kb) {
-            const int s = (int)gtid;
+        // ---- seeds and level 1.  The visited buffers and NB[1] are zero here
+        // (cleared by the previous pass's read-out, or since allocation).
+        // Level 1's frontier is the sources alone, so it is a push over their
+        // out-arcs: bit s goes to every out-neighbour of source s but itself.
+        const unsigned long long (&fin)[W] = s_fin;
+        for (int s = threadIdx.x; s < kb; s += kMsThreads) {
             const int src = __ldg(a.sources + s0 + s);
-            const unsigned long long bit = 1ull << (s & 63);
-            atomicOr(reinterpret_cast<unsigned long long*>(&a.V0[(long long)src * W + (s >> 6)]), bit);
-            atomicOr(reinterpret_cast<unsigned long long*>(&a.V1[(long long)src * W + (s >> 6)]), bit);
+            s_src[s] = src;
+            s_pre[s + 1] = __ldg(p.out_ptr + src + 1) - __ldg(p.out_ptr + src);
         }
-        if (p.nb_levels >= 1) grid_zero(p.nbl, stride);
-        if (blockIdx.x == 0 && threadIdx.x < 3 * W) ctl->lanes_new[threadIdx.x / W][threadIdx.x % W] = 0ull;
-        for (int i = threadIdx.x; i < tsm; i += kMsThreads) s_cov[i] = 0;
+        if (threadIdx.x == 0) s_pre[0] = 0;
         if (threadIdx.x < W) {
             const int lo = threadIdx.x * 64;
             s_fin[threadIdx.x] = kb >= lo + 64 ? 0ull : (kb <= lo ? ~0ull : ~0ull << (kb - lo));
         }
-        if (!ms_barrier(ctl, bar, bar_target, a.spin_limit)) return;
+        for (int i = threadIdx.x; i < tsm; i += kMsThreads) s_cov[i] = 0;
+        __syncthreads();
+        if (warp == 0) {  // inclusive scan of s_pre[1..kb], 8 entries per lane
+            int run = 0;
+            for (int c = 0; c < kMsMaxLanes / 32; ++c) {
+                const int i = 1 + lane * (kMsMaxLanes / 32) + c;
+                if (i <= kb) run += s_pre[i];
+            }
+            int incl = run;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(kFull, incl, o);
+                if (lane >= o) incl += y;
+            }
+            int acc = incl - run;
+            for (int c = 0; c < kMsMaxLanes / 32; ++c) {
+                const int i = 1 + lane * (kMsMaxLanes / 32) + c;
+                if (i <= kb) {
+                    acc += s_pre[i];
+                    s_pre[i] = acc;
+                }
+            }
+        }
+        __syncthreads();
+        if (gtid < kb) {
+            const int s = (int)gtid;
+            const int src = s_src[s];
+            const unsigned long long bit = 1ull << (s & 63);
+            atomicOr(reinterpret_cast<unsigned long long*>(&a.V0[(long long)src * W + (s >> 6)]), bit);
+            atomicOr(reinterpret_cast<unsigned long long*>(&a.V1[(long long)src * W + (s >> 6)]), bit);
+            a.reached[s0 + s] = 0;  // the read-out adds every CTA's sums
+            a.dsum[s0 + s] = 0;
+            a.ecc[s0 + s] = 0;
+        }
+        push_sources<W>(a, p, kb, s_pre, s_src, s_newmask);
+        if (p.nb_levels >= 2) grid_zero(p.nbl + stride, stride);  // NB[2]
+        __syncthreads();
+        if (threadIdx.x < W && s_newmask[threadIdx.x]) {
+            atomicOr(&ctl->lanes_new[1][threadIdx.x], s_newmask[threadIdx.x]);
+            s_newmask[threadIdx.x] = 0ull;
+        }
+        if (blockIdx.x == 0 && threadIdx.x >= 32 && threadIdx.x < 32 + W) ctl->lanes_new[2][threadIdx.x - 32] = 0ull;
+        if (!ms_barrier(ctl, bar, bar_target, a.spin_limit, ctl->lanes_new[1], W, s_lanes)) return;
 
-        const unsigned long long (&fin)[W] = s_fin;
-        const uint64_t* vp = a.V0;
-        uint64_t* vn = a.V1;
         int tlast = 0;
-        for (int t = 1;; ++t) {
+        bool finished = level_end<W>(a, b, 1, s_lanes, s_fin, tlast, tslot);
+        const uint64_t* vp = a.V1;
+        uint64_t* vn = a.V0;
+        for (int t = 2; !finished; ++t) {
             if (a.dist_bytes == 2 && t > 32767) {
                 if (gtid == 0) atomicCAS(&ctl->status, DEV_OK, DEV_OVERFLOW);
                 return;
@@ -944,16 +1046,19 @@ __global__ void __launch_bounds__(kMsThreads, 1) msbfs_sliced_kernel(MsArgs a, M
                 i = __shfl_sync(kFull, i, 0);
                 if (i >= tend) break;
                 const int li = i - tbeg;
-                if (li < kTaskSmem && s_cov[li] >= 2) continue;
+                if (li < kTaskSmem && s_cov[li] >= 2) continue;  // never a split row's piece
                 const int4 tk = li < kTaskSmem ? s_tasks[li] : __ldg(p.tasks + i);
                 unsigned long long vv[W], acc[W];
 #pragma unroll
                 for (int w = 0; w < W; ++w) acc[w] = 0ull;
                 bool covered;
+                bool settle_it;  // this lane settles vertex sv below
+                int sv;
                 if (tk.x >= 0) {
                     // row piece: arcs [tk.y, tk.z) of vertex tk.x, 128 per round;
                     // each round's indices load with the previous round's words
                     const int v = tk.x;
+                    sv = v;
                     const int j1 = tk.z;
                     int j = tk.y + lane;
                     int u0 = j < j1 ? __ldg(a.in_idx + j) : -1;
@@ -987,14 +1092,27 @@ __global__ void __launch_bounds__(kMsThreads, 1) msbfs_sliced_kernel(MsArgs a, M
 #pragma unroll
                         for (int w = 0; w < W; ++w) acc[w] = warp_or_redux(acc[w]);
                     }
+                    settle_it = lane == 0;
                     if (tk.w >= 0) {
-                        if (need && lane == 0) {
+                        // a split row: the CTA's last piece to finish settles it
+                        settle_it = false;
+                        if (lane == 0) {
+                            const int slot = tk.w & 255, npieces = tk.w >> 8;
+                            if (need) {
 #pragma unroll
-                            for (int w = 0; w < W; ++w)
-                                if (acc[w]) atomicOr(&s_hacc[tk.w][w], acc[w]);
+                                for (int w = 0; w < W; ++w)
+                                    if (acc[w]) atomicOr(&s_hacc[slot][w], acc[w]);
+                            }
+                            __threadfence_block();
+                            if (atomicAdd(&s_hcnt[slot], 1) == npieces - 1) {
+                                __threadfence_block();
+#pragma unroll
+                                for (int w = 0; w < W; ++w) acc[w] = atomicExch(&s_hacc[slot][w], 0ull);
+                                s_hcnt[slot] = 0;
+                                settle_it = true;
+                            }
                         }
-                    } else if (lane == 0) {
-                        settle<W>(a, p, vn, t, v, vv, acc, fin, grow);
+                        covered = false;  // split rows are never skipped
                     }
                 } else {
                     // slice: lane = vertex, its in-arcs four columns per round.  The
@@ -1005,6 +1123,7 @@ __global__ void __launch_bounds__(kMsThreads, 1) msbfs_sliced_kernel(MsArgs a, M
                     const int D = tk.z;
                     const int32_t* col = p.sell_idx + tk.y + lane;
                     const int2 vd = __ldg(p.sell_vd + (long long)sid * 32 + lane);
+                    sv = vd.x;
                     int u0 = D > 0 ? __ldg(col) : -1;
                     int u1 = D > 1 ? __ldg(col + 32) : -1;
                     int u2 = D > 2 ? __ldg(col + 64) : -1;
@@ -1045,37 +1164,22 @@ __global__ void __launch_bounds__(kMsThreads, 1) msbfs_sliced_kernel(MsArgs a, M
                             if (u3 >= 0) gor<W>(vp + (long long)u3 * W, acc);
                         }
                     }
-                    if (v >= 0) {
-                        if (!need) {
+                    if (!need) {
 #pragma unroll
-                            for (int w = 0; w < W; ++w) acc[w] = 0ull;
-                        }
-                        settle<W>(a, p, vn, t, v, vv, acc, fin, grow);
+                        for (int w = 0; w < W; ++w) acc[w] = 0ull;
                     }
+                    settle_it = v >= 0;
                 }
+                if (settle_it) settle<W>(a, p, vn, t, sv, vv, acc, fin, grow);
                 if (lane == 0 && li < kTaskSmem) s_cov[li] = covered ? s_cov[li] + 1 : 0;
-            }
-            __syncthreads();  // every piece of this CTA's split rows is in s_hacc
-            for (int h = warp; h < nh; h += kMsWarps) {
-                if (lane == 0) {
-                    const int v = __ldg(p.hub_v + h0 + h);
-                    unsigned long long vv[W], acc[W];
-                    vload<W>(vp + (long long)v * W, vv);
-#pragma unroll
-                    for (int w = 0; w < W; ++w) {
-                        acc[w] = s_hacc[h][w];
-                        s_hacc[h][w] = 0ull;
-                    }
-                    settle<W>(a, p, vn, t, v, vv, acc, fin, grow);
-                }
             }
 #pragma unroll
             for (int w = 0; w < W; ++w) {
                 const unsigned long long x = warp_or_redux(grow[w]);
                 if (lane == 0 && x) atomicOr(&s_newmask[w], x);
             }
+            __syncthreads();  // every warp has left the task loop
             if (threadIdx.x == 0) s_next = tbeg;
-            __syncthreads();
             if (threadIdx.x < W && s_newmask[threadIdx.x]) {
                 atomicOr(&ctl->lanes_new[t % 3][threadIdx.x], s_newmask[threadIdx.x]);
                 s_newmask[threadIdx.x] = 0ull;
@@ -1083,142 +1187,114 @@ __global__ void __launch_bounds__(kMsThreads, 1) msbfs_sliced_kernel(MsArgs a, M
             if (blockIdx.x == 0 && threadIdx.x >= 32 && threadIdx.x < 32 + W)
                 ctl->lanes_new[(t + 1) % 3][threadIdx.x - 32] = 0ull;
             if (!ms_barrier(ctl, bar, bar_target, a.spin_limit, ctl->lanes_new[t % 3], W, s_lanes)) return;
-            int growing = 0;
-            bool done = true;
-#pragma unroll
-            for (int w = 0; w < W; ++w) {
-                growing += __popcll(s_lanes[w]);
-                done &= (fin[w] | ~s_lanes[w]) == ~0ull;
-            }
-            __syncthreads();  // every thread has read s_fin
-            if (threadIdx.x < W) s_fin[threadIdx.x] |= ~s_lanes[threadIdx.x];
-            __syncthreads();
-            if (growing) tlast = t;
-            if (a.trace && blockIdx.x == 0 && threadIdx.x == 0 && tslot < a.trace_cap) {
-                unsigned long long tnow;
-                asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(tnow));
-                long long* r = a.trace + 4 * (long long)tslot;
-                r[0] = b;
-                r[1] = t;
-                r[2] = growing;
-                r[3] = (long long)tnow;
-            }
-            ++tslot;
+            finished = level_end<W>(a, b, t, s_lanes, s_fin, tlast, tslot);
             const uint64_t* tmp = vn;
             vn = const_cast<uint64_t*>(vp);
             vp = tmp;
-            if (done) break;
         }
-        // ---- read-out: 32 consecutive vertices per warp, lane = vertex.  vp
-        // holds the final visited words; bit p of the level at which source s
+        // ---- read-out.  One item = 32 consecutive vertices (lane = vertex) x
+        // 32 lanes of sources; a CTA's items cover its vertex range.  vp holds
+        // the final visited words; bit p of the level at which source s
         // reached v is bit s of level plane p, OR-ed from the level arrays
-        // (and the stored planes of deeper levels).
+        // (and from the stored planes of deeper levels).
         const int np = tlast ? 32 - __clz(tlast) : 0;
         const int tnb = min(tlast, p.nb_levels);
-        for (int gi = gA + warp; gi < gB; gi += kMsWarps) {
+        const bool deep = tlast > p.nb_levels;
+        constexpr int H = 2 * W;  // 32-lane halves of a vertex's words
+        for (int it = gA * H + warp; it < gB * H; it += kMsWarps) {
+            const int gi = it / H, hw = it - gi * H;
+            const int sb = hw * 32;
+            if (sb >= kb) continue;
             const int v = gi * 32 + lane;
             const bool valid = v < n;
             const int vr = valid ? v : n;  // the zero row stands in for lanes past n
-            unsigned long long R[W];
-            vload<W>(vp + (long long)vr * W, R);
-            if (valid) {
-                unsigned long long z[W];
+            const unsigned* r32p = reinterpret_cast<const unsigned*>(vp + (long long)vr * W) + hw;
+            const unsigned* nb32 = reinterpret_cast<const unsigned*>(p.nbl + (long long)vr * W) + hw;
+            const unsigned r32 = __ldcg(r32p);
+            // levels below 16 (bits 0..3) from the level arrays, all loads at once
+            unsigned x[kNbLevelsMax];
 #pragma unroll
-                for (int w = 0; w < W; ++w) z[w] = 0ull;
-                vstore<W>(a.V0 + (long long)v * W, z);
-                vstore<W>(a.V1 + (long long)v * W, z);
+            for (int t = 1; t <= kNbLevelsMax; ++t) x[t - 1] = t <= tnb ? __ldcg(nb32 + 2 * (t - 1) * stride) : 0u;
+            unsigned pl0 = 0u, pl1 = 0u, pl2 = 0u, pl3 = 0u;
+#pragma unroll
+            for (int t = 1; t <= kNbLevelsMax; ++t) {
+                if (t & 1) pl0 |= x[t - 1];
+                if (t & 2) pl1 |= x[t - 1];
+                if (t & 4) pl2 |= x[t - 1];
+                if (t & 8) pl3 |= x[t - 1];
             }
+            const unsigned* pp = reinterpret_cast<const unsigned*>(p.planes + (long long)vr * W) + hw;
+            unsigned vals[16];
 #pragma unroll
-            for (int hw = 0; hw < 2 * W; ++hw) {
-                const int sb = hw * 32;
-                if (sb >= kb) break;
-                const unsigned r32 = (unsigned)(R[hw >> 1] >> (32 * (hw & 1)));
-                // levels below 16 (bits 0..3) from the level arrays
-                unsigned pl0 = 0u, pl1 = 0u, pl2 = 0u, pl3 = 0u;
-                const unsigned* nb32 = reinterpret_cast<const unsigned*>(p.nbl + (long long)vr * W) + hw;
-                for (int t = 1; t <= tnb; ++t) {
-                    const unsigned x = __ldcg(nb32 + 2 * (t - 1) * stride);
-                    if (t & 1) pl0 |= x;
-                    if (t & 2) pl1 |= x;
-                    if (t & 4) pl2 |= x;
-                    if (t & 8) pl3 |= x;
+            for (int i = 0; i < 16; ++i) vals[i] = 0u;
+            const unsigned rt = bit_transpose32(r32);  // lane = source sb + lane: reached vertices
+            unsigned cand = rt;
+            int ecc = 0;
+            long long dsum = 0;
+            for (int q = np - 1; q >= 0; --q) {
+                unsigned d = q == 0 ? pl0 : q == 1 ? pl1 : q == 2 ? pl2 : q == 3 ? pl3 : 0u;
+                if (deep) d |= __ldcg(pp + 2 * q * stride);
+#pragma unroll
+                for (int i = 0; i < 16; ++i)
+                    vals[i] |= (((d >> (2 * i)) & 1u) | (((d >> (2 * i + 1)) & 1u) << 16)) << q;
+                const unsigned dt = bit_transpose32(d);
+                dsum += (long long)__popc(dt) << q;
+                const unsigned c = cand & dt;
+                if (c) {
+                    cand = c;
+                    ecc |= 1 << q;
                 }
-                const unsigned* pp = reinterpret_cast<const unsigned*>(p.planes + (long long)vr * W) + hw;
-                const bool deep = tlast > p.nb_levels;  // deeper levels are in the planes
-                unsigned vals[16];
-#pragma unroll
-                for (int i = 0; i < 16; ++i) vals[i] = 0u;
-                const unsigned rt = bit_transpose32(r32);  // lane = source sb + lane: reached vertices
-                unsigned cand = rt;
-                int ecc = 0;
-                long long dsum = 0;
-                for (int q = np - 1; q >= 0; --q) {
-                    unsigned d = q == 0 ? pl0 : q == 1 ? pl1 : q == 2 ? pl2 : q == 3 ? pl3 : 0u;
-                    if (deep) d |= __ldcg(pp + 2 * q * stride);
-#pragma unroll
-                    for (int i = 0; i < 16; ++i)
-                        vals[i] |= (((d >> (2 * i)) & 1u) | (((d >> (2 * i + 1)) & 1u) << 16)) << q;
-                    const unsigned dt = bit_transpose32(d);
-                    dsum += (long long)__popc(dt) << q;
-                    const unsigned c = cand & dt;
-                    if (c) {
-                        cand = c;
-                        ecc |= 1 << q;
-                    }
+            }
+            if (sb + lane < kb) {
+                atomicAdd(&s_reached[sb + lane], __popc(rt));
+                atomicAdd(reinterpret_cast<unsigned long long*>(&s_dsum[sb + lane]), (unsigned long long)dsum);
+                atomicMax(&s_ecc[sb + lane], ecc);
+            }
+            if (valid) {
+                const int nsrc = min(32, kb - sb);
+                char* base;
+                long long step;
+                if (a.layout == DAWN_SOURCE_MAJOR) {
+                    const long long row0 = a.per_pass ? sb : s0 + sb;
+                    base = static_cast<char*>(a.out) + (row0 * a.out_row_stride + v) * a.dist_bytes;
+                    step = a.out_row_stride * a.dist_bytes;
+                } else {
+                    base = static_cast<char*>(a.out) + ((long long)v * a.out_row_stride + s0 + sb) * a.dist_bytes;
+                    step = a.dist_bytes;
                 }
-                if (sb + lane < kb) {
-                    atomicAdd(&s_reached[sb + lane], __popc(rt));
-                    atomicAdd(reinterpret_cast<unsigned long long*>(&s_dsum[sb + lane]), (unsigned long long)dsum);
-                    atomicMax(&s_ecc[sb + lane], ecc);
-                }
-                if (valid) {
-                    const int nsrc = min(32, kb - sb);
-                    char* base;
-                    long long step;
-                    if (a.layout == DAWN_SOURCE_MAJOR) {
-                        const long long row0 = a.per_pass ? sb : s0 + sb;
-                        base = static_cast<char*>(a.out) + (row0 * a.out_row_stride + v) * a.dist_bytes;
-                        step = a.out_row_stride * a.dist_bytes;
-                    } else {
-                        base = static_cast<char*>(a.out) + ((long long)v * a.out_row_stride + s0 + sb) * a.dist_bytes;
-                        step = a.dist_bytes;
-                    }
 #pragma unroll
-                    for (int i = 0; i < 32; ++i) {
-                        if (i >= nsrc) break;
-                        const int d = (int)((vals[i >> 1] >> (16 * (i & 1))) & 0xFFFFu);
-                        const int val = ((r32 >> i) & 1u) ? d : -1;
-                        if (a.dist_bytes == 2) *reinterpret_cast<int16_t*>(base + i * step) = (int16_t)val;
-                        else *reinterpret_cast<int32_t*>(base + i * step) = val;
-                    }
+                for (int i = 0; i < 32; ++i) {
+                    if (i >= nsrc) break;
+                    const int d = (int)((vals[i >> 1] >> (16 * (i & 1))) & 0xFFFFu);
+                    const int val = ((r32 >> i) & 1u) ? d : -1;
+                    if (a.dist_bytes == 2) *reinterpret_cast<int16_t*>(base + i * step) = (int16_t)val;
+                    else *reinterpret_cast<int32_t*>(base + i * step) = val;
                 }
             }
         }
-        __syncthreads();  // every warp's read-out sums are in
-        // ---- batch reductions: per-CTA partials, then one thread per lane
-        for (int s = threadIdx.x; s < L; s += kMsThreads) {
-            a.part_i[((long long)blockIdx.x * 2 + 0) * kMsMaxLanes + s] = s_reached[s];
-            a.part_i[((long long)blockIdx.x * 2 + 1) * kMsMaxLanes + s] = s_ecc[s];
-            a.part_l[(long long)blockIdx.x * kMsMaxLanes + s] = s_dsum[s];
+        __syncthreads();  // every item of this CTA has read its visited words and summed
+        // both visited buffers back to zero over this CTA's vertices
+        {
+            const long long w0 = (long long)gA * 32 * W, w1 = (long long)min(gB * 32, n) * W;
+            for (long long i = w0 + threadIdx.x; i < w1; i += kMsThreads) {
+                a.V0[i] = 0ull;
+                a.V1[i] = 0ull;
+                p.nbl[i] = 0ull;  // NB[1]: the next pass's level-1 push ORs into it
+            }
+        }
+        // the level slots start the next pass at zero (every CTA has read them)
+        if (blockIdx.x == 0 && threadIdx.x < 3 * W) ctl->lanes_new[threadIdx.x / W][threadIdx.x % W] = 0ull;
+        // per-source sums into the outputs (zeroed at the pass's start)
+        for (int s = threadIdx.x; s < kb; s += kMsThreads) {
+            if (s_reached[s]) atomicAdd(&a.reached[s0 + s], s_reached[s]);
+            if (s_dsum[s]) atomicAdd(reinterpret_cast<unsigned long long*>(&a.dsum[s0 + s]), (unsigned long long)s_dsum[s]);
+            if (s_ecc[s]) atomicMax(&a.ecc[s0 + s], s_ecc[s]);
             s_reached[s] = 0;
             s_ecc[s] = 0;
             s_dsum[s] = 0;
         }
-        if (!ms_barrier(ctl, bar, bar_target, a.spin_limit)) return;
-        if (gtid < kb) {
-            const int s = (int)gtid;
-            int r = 0, e = 0;
-            long long sum = 0;
-            for (int c = 0; c < (int)gridDim.x; ++c) {
-                r += __ldcg(a.part_i + ((long long)c * 2 + 0) * kMsMaxLanes + s);
-                e = max(e, __ldcg(a.part_i + ((long long)c * 2 + 1) * kMsMaxLanes + s));
-                sum += __ldcg(a.part_l + (long long)c * kMsMaxLanes + s);
-            }
-            a.reached[s0 + s] = r;
-            a.ecc[s0 + s] = e;
-            a.dsum[s0 + s] = sum;
-        }
-        // the next pass's first barrier orders these reads before the partials are rewritten
+        // the next pass seeds the visited buffers this pass has just cleared
+        if (b + 1 < nbatches && !ms_barrier(ctl, bar, bar_target, a.spin_limit)) return;
     }
     if (gtid == 0) ctl->bar[a.bar_parity ^ 1].count = 0;
 }
@@ -1355,7 +1431,7 @@ int ms_plan_build(dawn_graph* g, cudaStream_t st) {
                 const Unit& u = units[(size_t)x];
                 for (int t = u.first; t < u.first + u.count; ++t) {
                     int4 tk = tasks[(size_t)t];
-                    if (u.split) tk.w = local;
+                    if (u.split) tk.w = local | (u.count << 8);  // CTA slot, pieces of the row
                     by_cta.push_back(tk);
                 }
                 if (u.split) {
@@ -1428,6 +1504,7 @@ int ms_nb_alloc(dawn_graph* g) {
     const size_t per = sizeof(uint64_t) * 4 * ((size_t)g->n + 1);
     const int levels = (int)std::max<size_t>(4, std::min<size_t>(kNbLevelsMax, kNbBudget / per));
     DAWN_CUDA_TRY(cudaMalloc((void**)&g->ms_nb, per * (size_t)levels));
+    DAWN_CUDA_TRY(cudaMemset(g->ms_nb, 0, per));  // NB[1] starts zero; later levels are zeroed ahead
     g->ms_nb_levels = levels;
     return DAWN_OK;
 }
@@ -1518,11 +1595,6 @@ int msbfs_run(dawn_graph* g, const int32_t* sources, int32_t k, void* dist_block
     if (sliced) {
         if ((rc = ms_plan_build(g, st)) != DAWN_OK) return rc;
         if ((rc = ms_nb_alloc(g)) != DAWN_OK) return rc;
-        if (g->ms_vis_dirty) {
-            DAWN_CUDA_TRY(cudaMemsetAsync(g->ms_vis[0], 0, plane_bytes, st));
-            DAWN_CUDA_TRY(cudaMemsetAsync(g->ms_vis[1], 0, plane_bytes, st));
-            g->ms_vis_dirty = 0;
-        }
     }
 
     const size_t cell = (size_t)dist_bytes;
@@ -1577,6 +1649,21 @@ int msbfs_run(dawn_graph* g, const int32_t* sources, int32_t k, void* dist_block
         (reinterpret_cast<uintptr_t>(cbase + (size_t)g->sms * kMsMaxLanes * (2 * sizeof(int32_t) + sizeof(long long))) + 255) &
         ~(uintptr_t)255);
     a.ctl = ctl;
+    // NB[1] of another lane width overlaps that width's NB[2], which is not
+    // cleared after a run
+    if (sliced && g->ms_sliced_w != W) g->ms_vis_dirty = 1;
+    if (e == cudaSuccess && sliced && g->ms_vis_dirty) {
+        // the sliced kernel starts from zero visited words, a zero NB[1] and
+        // zero level slots; the per-level kernel or a failed run left others
+        e = cudaMemsetAsync(g->ms_vis[0], 0, plane_bytes, st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(g->ms_vis[1], 0, plane_bytes, st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(g->ms_nb, 0, plane_bytes, st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(&ctl->lanes_new[0][0], 0, sizeof(ctl->lanes_new), st);
+        if (e == cudaSuccess) {
+            g->ms_vis_dirty = 0;
+            g->ms_sliced_w = W;
+        }
+    }
     a.spin_limit = spin;
     a.n = g->n;
     a.k = k;
@@ -1608,6 +1695,8 @@ int msbfs_run(dawn_graph* g, const int32_t* sources, int32_t k, void* dist_block
     if (e == cudaSuccess && sliced) {
         const MsPlan* pl = static_cast<const MsPlan*>(g->ms_plan);
         MsSliced sp;
+        sp.out_ptr = g->row_ptr;
+        sp.out_idx = g->col_idx;
         sp.tasks = pl->tasks;
         sp.cta_task = pl->cta_task;
         sp.cta_hub = pl->cta_hub;
