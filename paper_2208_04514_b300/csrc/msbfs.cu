@@ -1234,9 +1234,15 @@ __global__ void __launch_bounds__(kMsThreads, 1) msbfs_sliced_kernel(MsArgs a, M
             for (int q = np - 1; q >= 0; --q) {
                 unsigned d = q == 0 ? pl0 : q == 1 ? pl1 : q == 2 ? pl2 : q == 3 ? pl3 : 0u;
                 if (deep) d |= __ldcg(pp + 2 * q * stride);
+                // bit 2i of d to bit q of vals[i], bit 2i + 1 to bit 16 + q: (ehi:elo)
+                // is d << q in 64 bits, and a funnel shift picks any 32 of them
+                const unsigned elo = d << q, ehi = q ? d >> (32 - q) : 0u;
+                const unsigned m0 = 1u << q, m1 = 0x10000u << q;
 #pragma unroll
-                for (int i = 0; i < 16; ++i)
-                    vals[i] |= (((d >> (2 * i)) & 1u) | (((d >> (2 * i + 1)) & 1u) << 16)) << q;
+                for (int i = 0; i < 16; ++i) {
+                    vals[i] |= __funnelshift_r(elo, ehi, 2 * i) & m0;
+                    vals[i] |= (2 * i + 1 <= 16 ? elo << (15 - 2 * i) : __funnelshift_r(elo, ehi, 2 * i - 15)) & m1;
+                }
                 const unsigned dt = bit_transpose32(d);
                 dsum += (long long)__popc(dt) << q;
                 const unsigned c = cand & dt;
@@ -1251,24 +1257,37 @@ __global__ void __launch_bounds__(kMsThreads, 1) msbfs_sliced_kernel(MsArgs a, M
                 atomicMax(&s_ecc[sb + lane], ecc);
             }
             if (valid) {
+                // unreached cells read -1
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                    const unsigned rm = (((r32 >> (2 * i)) & 1u) ? 0x0000FFFFu : 0u) | (((r32 >> (2 * i + 1)) & 1u) ? 0xFFFF0000u : 0u);
+                    vals[i] = (vals[i] & rm) | ~rm;
+                }
                 const int nsrc = min(32, kb - sb);
-                char* base;
+                char* cell;
                 long long step;
                 if (a.layout == DAWN_SOURCE_MAJOR) {
                     const long long row0 = a.per_pass ? sb : s0 + sb;
-                    base = static_cast<char*>(a.out) + (row0 * a.out_row_stride + v) * a.dist_bytes;
+                    cell = static_cast<char*>(a.out) + (row0 * a.out_row_stride + v) * a.dist_bytes;
                     step = a.out_row_stride * a.dist_bytes;
                 } else {
-                    base = static_cast<char*>(a.out) + ((long long)v * a.out_row_stride + s0 + sb) * a.dist_bytes;
+                    cell = static_cast<char*>(a.out) + ((long long)v * a.out_row_stride + s0 + sb) * a.dist_bytes;
                     step = a.dist_bytes;
                 }
+                if (a.dist_bytes == 2) {
 #pragma unroll
-                for (int i = 0; i < 32; ++i) {
-                    if (i >= nsrc) break;
-                    const int d = (int)((vals[i >> 1] >> (16 * (i & 1))) & 0xFFFFu);
-                    const int val = ((r32 >> i) & 1u) ? d : -1;
-                    if (a.dist_bytes == 2) *reinterpret_cast<int16_t*>(base + i * step) = (int16_t)val;
-                    else *reinterpret_cast<int32_t*>(base + i * step) = val;
+                    for (int i = 0; i < 32; ++i) {
+                        if (i >= nsrc) break;
+                        *reinterpret_cast<unsigned short*>(cell) = (unsigned short)(vals[i >> 1] >> (16 * (i & 1)));
+                        cell += step;
+                    }
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 32; ++i) {
+                        if (i >= nsrc) break;
+                        *reinterpret_cast<int32_t*>(cell) = (int32_t)(short)(vals[i >> 1] >> (16 * (i & 1)));
+                        cell += step;
+                    }
                 }
             }
         }
