@@ -137,6 +137,7 @@ struct dawn_graph {
     int ms_blocks_per_sm = 0;
     unsigned ms_launches = 0;         // picks the barrier counter of the next batched launch
     void* weighted = nullptr;         // weights and work buffers of the (min, +) path (weighted.cu)
+    int32_t* tree_flag = nullptr;     // tree.cu: 1 when the last tree pass pushes level 2 (set on the device)
 };
 
 namespace dawn {

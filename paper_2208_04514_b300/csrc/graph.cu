@@ -441,6 +441,7 @@ void release(dawn_graph* g) {
     f(g->ms_scratch);
     f(g->ms_counts);
     ms_release(g);
+    f(g->tree_flag);
     if (g->stats_host) cudaFreeHost(g->stats_host);
     if (g->status_host) cudaFreeHost(g->status_host);
     delete g;

@@ -17,7 +17,8 @@
 // hubs.  A hub would scan thousands of in-arcs to meet the smallest of those
 // few, so the out-rows of the level-1 vertices are pushed instead: every arc
 // (u, v) with d(u) = 1 and d(v) = 2 takes an atomic minimum on parent[v].  It
-// is the same minimum, reached from the other end of the arcs.
+// is the same minimum, reached from the other end of the arcs.  The push is
+// taken only while the level-1 rows are a small share of the graph.
 #include <algorithm>
 
 #include "dawn_internal.cuh"
@@ -45,10 +46,32 @@ constexpr int kTreePushMax = 2048;  // source rows up to this long push level 2
 // level 1 (the source itself on a self-loop) contribute no arcs.  It runs
 // after parent_kernel, which leaves -1 (all bits set) at level 2, so the
 // atomic minimum over unsigned values keeps the smallest predecessor.
+// Whether level 2 is pushed: the arcs of the level-1 vertices' rows (the
+// push reads each once; a repeated arc of the source row counts twice, as
+// the push reads it twice) against `limit`.  One CTA.
+__global__ void __launch_bounds__(kTreeThreads, 1) level2_decide_kernel(const int32_t* __restrict__ row_ptr,
+                                                                        const int32_t* __restrict__ col_idx,
+                                                                        const int32_t* __restrict__ dist, int srb,
+                                                                        int k, long long limit, int32_t* push2) {
+    __shared__ unsigned long long s_sum;
+    if (threadIdx.x == 0) s_sum = 0ull;
+    __syncthreads();
+    unsigned long long sum = 0ull;
+    for (int i = threadIdx.x; i < k; i += kTreeThreads) {
+        const int u = col_idx[srb + i];
+        if (dist[u] == 1) sum += (unsigned long long)(row_ptr[u + 1] - row_ptr[u]);
+    }
+    if (sum) atomicAdd(&s_sum, sum);
+    __syncthreads();
+    if (threadIdx.x == 0) *push2 = s_sum <= (unsigned long long)limit ? 1 : 0;
+}
+
 __global__ void __launch_bounds__(kTreeThreads, 1) push_level2_kernel(const int32_t* __restrict__ row_ptr,
                                                                       const int32_t* __restrict__ col_idx,
                                                                       const int32_t* __restrict__ dist,
-                                                                      int32_t* parent, int srb, int k) {
+                                                                      int32_t* parent, int srb, int k,
+                                                                      const int32_t* __restrict__ push2) {
+    if (!*push2) return;  // level2_decide_kernel left level 2 to parent_kernel
     __shared__ long long s_off[kTreePushMax + 1];
     __shared__ int s_u[kTreePushMax], s_rb[kTreePushMax];
     __shared__ long long s_part[kTreeThreads / 32];
@@ -115,7 +138,9 @@ __global__ void __launch_bounds__(kTreeThreads, 1) push_level2_kernel(const int3
 __global__ void __launch_bounds__(kTreeThreads, 2) parent_kernel(const int32_t* __restrict__ in_ptr,
                                                                  const int32_t* __restrict__ in_idx,
                                                                  const int32_t* __restrict__ dist, int32_t* parent,
-                                                                 int32_t n, int32_t src, int sorted, int level2_done) {
+                                                                 int32_t n, int32_t src, int sorted,
+                                                                 const int32_t* __restrict__ push2) {
+    const bool level2_done = push2 && *push2;  // level 2 is left to push_level2_kernel
     const unsigned kFull = 0xffffffffu;
     __shared__ int s_hcount;
     __shared__ int s_hv[kTreeHeavyMax], s_hj[kTreeHeavyMax], s_hie[kTreeHeavyMax], s_hd[kTreeHeavyMax];
@@ -215,12 +240,27 @@ int tree_pass(dawn_graph* g, int32_t src, const int32_t* dist_dev, int32_t* pare
     const int blocks = (int)std::min<long long>(want, 2LL * g->sms);
     const int srb = g->row_ptr_host[src];
     const int k = g->row_ptr_host[src + 1] - srb;
-    const int push = k > 0 && k <= kTreePushMax;
+    // Level 2 is pushed when the source row is short and the level-1 rows
+    // hold at most an eighth of the arcs (level2_decide_kernel counts them on
+    // the device, at least 2^16 allowed); past that the push would read a
+    // large share of the graph, and the level-2 vertices' in-row scans, which
+    // stop at the first qualifying arc, are left to do it.  parent_kernel leaves -1 at
+    // level 2 when the flag is set and push_level2_kernel then takes its
+    // atomic minimum over them: the three launches stay on stream `st`, in
+    // this order.
+    const bool push = k > 0 && k <= kTreePushMax;
+    if (push) {
+        if (!g->tree_flag) DAWN_CUDA_TRY(cudaMalloc((void**)&g->tree_flag, sizeof(int32_t)));
+        const long long limit = std::max<long long>(1LL << 16, (long long)g->m / 8);
+        level2_decide_kernel<<<1, kTreeThreads, 0, st>>>(g->row_ptr, g->col_idx, dist_dev, srb, k, limit, g->tree_flag);
+        DAWN_CUDA_TRY(cudaGetLastError());
+    }
     parent_kernel<<<blocks, kTreeThreads, 0, st>>>(g->in_ptr, g->in_idx, dist_dev, parent_dev, g->n, src,
-                                                   g->in_sorted, push);
+                                                   g->in_sorted, push ? g->tree_flag : nullptr);
     if (push) {
         DAWN_CUDA_TRY(cudaGetLastError());
-        push_level2_kernel<<<g->sms, kTreeThreads, 0, st>>>(g->row_ptr, g->col_idx, dist_dev, parent_dev, srb, k);
+        push_level2_kernel<<<g->sms, kTreeThreads, 0, st>>>(g->row_ptr, g->col_idx, dist_dev, parent_dev, srb, k,
+                                                            g->tree_flag);
     }
     DAWN_CUDA_TRY(cudaGetLastError());
     return DAWN_OK;

@@ -168,3 +168,39 @@ def test_hub_row_with_late_predecessor(dawn, shuffle):
                 np.testing.assert_array_equal(p, wp, err_msg=f"{gr.name} source {s}")
         finally:
             dawn.dawn_graph_free(h)
+
+
+@pytest.mark.parametrize("row_len", [10, 40])
+def test_level2_from_a_wide_source_row(dawn, row_len):
+    """A source with about 2,000 level-1 neighbours (some arcs repeated) whose
+    out-rows overlap, repeat arcs and reach back into level 1, directed.  With
+    10 arcs per neighbour row the level-1 rows hold few enough arcs for the
+    level-2 push; with 40 they hold more than the push takes and the level-2
+    vertices scan their in-rows.  Parents against oracle.parents either way."""
+    rng = np.random.default_rng(row_len)
+    n1, n2, n3 = 2000, 3000, 500
+    n = 1 + n1 + n2 + n3
+    lv1 = np.arange(1, 1 + n1)
+    lv2 = np.arange(1 + n1, 1 + n1 + n2)
+    lv3 = np.arange(1 + n1 + n2, n)
+    dup = rng.choice(lv1, 40, replace=False)                    # 2,040 arcs in the source row
+    src = [np.zeros(n1 + dup.size, np.int64)]
+    dst = [np.r_[lv1, dup]]
+    u = np.repeat(lv1, row_len)                                  # level 1 -> level 2 (overlapping, repeats)
+    v = rng.choice(lv2, u.size)
+    v[::7] = rng.choice(lv1, v[::7].size)                         # and some back into level 1
+    src.append(u); dst.append(v)
+    w = rng.choice(lv2, 4000)                                    # level 2 -> level 3
+    src.append(w); dst.append(rng.choice(lv3, w.size))
+    g = gg.from_arcs(n, np.concatenate(src), np.concatenate(dst))
+    assert g.row_ptr[1] - g.row_ptr[0] == n1 + dup.size <= 2048
+    h = upload(dawn, g)
+    try:
+        d_want, p_want = want(g, 0)
+        assert (d_want == 2).sum() > 1000
+        for run in (run_host, run_device):
+            dist, par = run(dawn, h, n, 0)
+            np.testing.assert_array_equal(dist, d_want)
+            np.testing.assert_array_equal(par, p_want)
+    finally:
+        dawn.dawn_graph_free(h)
