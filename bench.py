@@ -600,17 +600,19 @@ def bench_centrality(dawn, torch, flush, lanes=256):
             "timing": "wall clock of the synchronous call (inputs on the device), L2 flushed before"}
 
 
-def bench_serving(dawn, torch, nreq=48, seed=6):
+def bench_serving(dawn, torch, nreq=48, seed=6, rates=(0.3, 0.7, 1.0), ncal=None):
     """Continuous-batching server on 8 resident graphs: RMAT scales 14, 16, 18,
     20, 22 (edge factor 16, symmetrised) and 1024^2, 2048^2, 4096^2 lattices
     (bonds deleted with p = 0.1).  Requests: graph uniform over the 8, k =
     floor(256^U) sources in [1, 256] (log-uniform), sources uniform, int16
     rows written in place into device buffers.  Saturated throughput is
-    measured first (all requests at once); then Poisson arrival streams at
-    0.3x, 0.7x and 1.0x of it.  The plain path serves the 1.0x stream FIFO,
-    one dawn_sssp launch per source (int32 rows): its per-request service
-    times are measured back to back and its latencies follow from the FIFO
-    single-server recursion start = max(arrival, previous done)."""
+    measured first (ncal requests, default nreq, all at once); then Poisson
+    arrival streams of nreq requests at each of `rates` x that throughput
+    (0.3x, 0.7x and 1.0x by default).  The plain path serves the 0.3x and 1.0x
+    streams FIFO, one dawn_sssp launch per source (int32 rows): its
+    per-request service times are measured back to back and its latencies
+    follow from the FIFO single-server recursion start = max(arrival, previous
+    done)."""
     from paper_2208_04514_b300 import graphgen as gg
     specs = [("rmat14", lambda: gg.rmat(14, seed=114)), ("rmat16", lambda: gg.rmat(16, seed=116)),
              ("rmat18", lambda: gg.rmat(18, seed=118)), ("rmat20", lambda: gg.rmat(20, seed=120)),
@@ -690,15 +692,17 @@ def bench_serving(dawn, torch, nreq=48, seed=6):
 
     out = {"workload": "serve_8graphs", "graphs": [n for n, _ in specs], "requests_per_rate": nreq,
            "dist": "int16 rows written in place into device buffers", "rates": {}}
-    cal = draw(nreq)
-    lat, qps_sat, _ = serve(cal, np.zeros(nreq), check=True)
+    ncal = ncal or nreq
+    cal = draw(ncal)
+    lat, qps_sat, _ = serve(cal, np.zeros(ncal), check=True)
     out["saturated_queries_per_s"] = qps_sat
-    out["saturated_sources_per_s"] = sum(len(x[1]) for x in cal) * qps_sat / nreq
+    out["saturated_sources_per_s"] = sum(len(x[1]) for x in cal) * qps_sat / ncal
+    out["calibration_requests"] = ncal
     stream_10 = stream_03 = None
-    for frac in (0.3, 0.7, 1.0):
+    for frac in rates:
         reqs = draw(nreq)
         arrivals = np.cumsum(rng.exponential(1.0 / (frac * qps_sat), nreq))
-        lat, qps, _ = serve(reqs, arrivals, check=frac == 1.0)
+        lat, qps, _ = serve(reqs, arrivals, check=True)
         out["rates"][f"{frac:.1f}x"] = {"offered_queries_per_s": frac * qps_sat, "queries_per_s": qps,
                                        "p50_ms": 1e3 * float(np.percentile(lat, 50)),
                                        "p99_ms": 1e3 * float(np.percentile(lat, 99)),
@@ -710,7 +714,10 @@ def bench_serving(dawn, torch, nreq=48, seed=6):
     # plain path on the 0.3x and 1.0x streams: per-request service times
     # measured back to back, latencies from the FIFO single-server recursion
     stream = torch.cuda.current_stream()
-    for tag, (reqs, arrivals) in (("plain_0.3x", stream_03), ("plain_1.0x", stream_10)):
+    for tag, stream_x in (("plain_0.3x", stream_03), ("plain_1.0x", stream_10)):
+        if stream_x is None:
+            continue
+        reqs, arrivals = stream_x
         service = []
         for gi, srcs in reqs:
             rows = torch.empty((len(srcs), ns[gi]), dtype=torch.int32, device="cuda")
@@ -734,7 +741,7 @@ def bench_serving(dawn, torch, nreq=48, seed=6):
     for h in handles:
         dawn.dawn_graph_free(h)
     out["verified"] = {"rows_checked": checked["rows"], "graphs": sorted(checked["graphs"]),
-                       "what": "first row of the first request on each graph in the saturated and 1.0x runs, "
+                       "what": "first row of the first request on each graph in every run, "
                                "against Alg. 2 (oracle FIFO BFS)"}
     return out
 
@@ -936,7 +943,9 @@ def run_one(args):
     elif args.workload == "batched":
         out = bench_batched(dawn, torch, flush, k=args.batched_k, lanes_list=(args.batched_lanes,) if args.batched_lanes else (64, 128, 256))
     else:
-        out = bench_serving(dawn, torch, nreq=args.serve_requests)
+        out = bench_serving(dawn, torch, nreq=args.serve_requests,
+                            rates=tuple(float(x) for x in args.serve_rates.split(",")),
+                            ncal=args.serve_calibration or None)
     print(json.dumps(out), flush=True)
     return 0
 
@@ -956,6 +965,10 @@ def main():
                     help="use only the first N of the 64 sources (small profiling runs; not a bench value)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end host-buffer pass")
     ap.add_argument("--serve-requests", type=int, default=48, help="requests per arrival rate in the serving mix")
+    ap.add_argument("--serve-rates", default="0.3,0.7,1.0",
+                    help="with --workload serving: arrival rates as fractions of the saturated throughput")
+    ap.add_argument("--serve-calibration", type=int, default=0,
+                    help="with --workload serving: requests of the saturated run (0 = --serve-requests)")
     ap.add_argument("--workload", choices=["all", "lattice", "batched", "serving", "tree", "centrality", "modes", "many", "weighted"], default="all",
                     help="run one secondary workload alone and print its figures (profiling runs; not a bench line)")
     ap.add_argument("--batched-k", type=int, default=0, help="with --workload batched: sources (0 = all)")
