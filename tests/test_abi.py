@@ -60,3 +60,34 @@ def test_binding_rejects_noncontiguous(dawn):
     a = np.zeros((4, 4), dtype=np.int32)[:, 0]
     with pytest.raises(ValueError):
         dawn._ptr(a)
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """Every struct the binding mirrors has the header's size and field
+    offsets: a C program built against include/dawn.h prints them (gcc, no
+    CUDA), and they are compared with the ctypes classes."""
+    import shutil
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("gcc not found")
+    structs = {name: cls for name, cls in vars(dawn).items()
+               if isinstance(cls, type) and issubclass(cls, ctypes.Structure) and name.startswith("dawn_")}
+    assert {"dawn_sssp_opts", "dawn_msbfs_opts", "dawn_tuning"} <= set(structs)
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "dawn.h"', "int main(void) {"]
+    for name, cls in structs.items():
+        lines.append(f'    printf("{name} size %zu\\n", sizeof({name}));')
+        for field, _ in cls._fields_:
+            lines.append(f'    printf("{name} {field} %zu\\n", offsetof({name}, {field}));')
+    lines += ["    return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([gcc, "-std=c11", "-I", str(_build.INCLUDE), str(src), "-o", str(exe)], check=True)
+    got = {}
+    for line in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.splitlines():
+        name, field, value = line.split()
+        got[(name, field)] = int(value)
+    for name, cls in structs.items():
+        assert got[(name, "size")] == ctypes.sizeof(cls), name
+        for field, _ in cls._fields_:
+            assert got[(name, field)] == getattr(cls, field).offset, (name, field)
