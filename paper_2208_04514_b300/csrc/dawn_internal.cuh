@@ -130,6 +130,7 @@ struct dawn_graph {
     int ms_sliced_off = 0;            // 1: a run needed more levels than the sliced kernel holds; use the per-level kernel
     int ms_vis_dirty = 0;             // 1: ms_vis holds words a run left behind (the sliced kernel wants zeros)
     int ms_sliced_w = 0;              // lane words of the last sliced run (its level arrays are laid out by it)
+    int ms_harm_deep = 0;             // 1: a harmonic-centrality pass outran the sliced kernel's level arrays
     void* ms_scratch = nullptr;       // per-pass distance block when the caller passes none
     size_t ms_scratch_bytes = 0;
     int32_t* ms_counts = nullptr;     // per-lane per-level new-vertex counts

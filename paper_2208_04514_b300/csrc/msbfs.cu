@@ -717,6 +717,8 @@ struct MsSliced {
     uint64_t* planes;            // plane p of vertex v: planes + (p * (n + 1) + v) * W; may be null
     int32_t nb_levels;
     int32_t planes_cap;          // levels below 2^planes_cap fit (0: planes absent)
+    int32_t* hist;               // harmonic centrality: [kNbLevelsMax + 1][kMsMaxLanes] vertices per level of
+                                 // the pass (null: not wanted); zero between passes
 };
 
 __device__ __forceinline__ unsigned long long warp_or_redux(unsigned long long x) {
@@ -926,6 +928,7 @@ __global__ void __launch_bounds__(kMsThreads, 1) msbfs_sliced_kernel(MsArgs a, M
     __shared__ int s_pre[kMsMaxLanes + 1];      // level 1: prefix of the sources' out-degrees
     __shared__ int s_src[kMsMaxLanes];
     __shared__ int s_next, s_status;
+    extern __shared__ int s_hist[];  // with p.hist: [kNbLevelsMax + 1][64 * W] this CTA's level counts
 
     MsCtl* ctl = a.ctl;
     if (threadIdx.x == 0) s_status = ms_ld_relaxed_s32(&ctl->status);
@@ -936,6 +939,8 @@ __global__ void __launch_bounds__(kMsThreads, 1) msbfs_sliced_kernel(MsArgs a, M
     int tslot = 0;
     constexpr int L = 64 * W;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (p.hist)
+        for (int i = threadIdx.x; i < (kNbLevelsMax + 1) * L; i += kMsThreads) s_hist[i] = 0;
     const long long gtid = (long long)blockIdx.x * kMsThreads + threadIdx.x;
     const int n = a.n;
     const long long stride = (long long)(n + 1) * W;
@@ -1029,7 +1034,8 @@ __global__ void __launch_bounds__(kMsThreads, 1) msbfs_sliced_kernel(MsArgs a, M
                 if (gtid == 0) atomicCAS(&ctl->status, DEV_OK, DEV_OVERFLOW);
                 return;
             }
-            if (t > p.nb_levels && t >= (1 << p.planes_cap)) {
+            // (harmonic centrality counts levels in the level arrays only)
+            if (t > p.nb_levels && (t >= (1 << p.planes_cap) || p.hist)) {
                 if (gtid == 0) atomicCAS(&ctl->status, DEV_OK, DEV_PLANES);
                 return;
             }
@@ -1231,19 +1237,26 @@ __global__ void __launch_bounds__(kMsThreads, 1) msbfs_sliced_kernel(MsArgs a, M
             unsigned cand = rt;
             int ecc = 0;
             long long dsum = 0;
+            unsigned dt0 = 0u, dt1 = 0u, dt2 = 0u, dt3 = 0u;  // the low planes, transposed (for p.hist)
             for (int q = np - 1; q >= 0; --q) {
                 unsigned d = q == 0 ? pl0 : q == 1 ? pl1 : q == 2 ? pl2 : q == 3 ? pl3 : 0u;
                 if (deep) d |= __ldcg(pp + 2 * q * stride);
-                // bit 2i of d to bit q of vals[i], bit 2i + 1 to bit 16 + q: (ehi:elo)
-                // is d << q in 64 bits, and a funnel shift picks any 32 of them
-                const unsigned elo = d << q, ehi = q ? d >> (32 - q) : 0u;
-                const unsigned m0 = 1u << q, m1 = 0x10000u << q;
+                if (!a.nostore) {
+                    // bit 2i of d to bit q of vals[i], bit 2i + 1 to bit 16 + q: (ehi:elo)
+                    // is d << q in 64 bits, and a funnel shift picks any 32 of them
+                    const unsigned elo = d << q, ehi = q ? d >> (32 - q) : 0u;
+                    const unsigned m0 = 1u << q, m1 = 0x10000u << q;
 #pragma unroll
-                for (int i = 0; i < 16; ++i) {
-                    vals[i] |= __funnelshift_r(elo, ehi, 2 * i) & m0;
-                    vals[i] |= (2 * i + 1 <= 16 ? elo << (15 - 2 * i) : __funnelshift_r(elo, ehi, 2 * i - 15)) & m1;
+                    for (int i = 0; i < 16; ++i) {
+                        vals[i] |= __funnelshift_r(elo, ehi, 2 * i) & m0;
+                        vals[i] |= (2 * i + 1 <= 16 ? elo << (15 - 2 * i) : __funnelshift_r(elo, ehi, 2 * i - 15)) & m1;
+                    }
                 }
                 const unsigned dt = bit_transpose32(d);
+                if (q == 0) dt0 = dt;
+                else if (q == 1) dt1 = dt;
+                else if (q == 2) dt2 = dt;
+                else if (q == 3) dt3 = dt;
                 dsum += (long long)__popc(dt) << q;
                 const unsigned c = cand & dt;
                 if (c) {
@@ -1255,8 +1268,17 @@ __global__ void __launch_bounds__(kMsThreads, 1) msbfs_sliced_kernel(MsArgs a, M
                 atomicAdd(&s_reached[sb + lane], __popc(rt));
                 atomicAdd(reinterpret_cast<unsigned long long*>(&s_dsum[sb + lane]), (unsigned long long)dsum);
                 atomicMax(&s_ecc[sb + lane], ecc);
+                if (p.hist) {
+                    // vertices of this item at each level t >= 1: the reached ones
+                    // whose level bits spell t (tlast <= nb_levels <= 15 here)
+                    for (int t = 1; t <= tlast; ++t) {
+                        const unsigned m = rt & ((t & 1) ? dt0 : ~dt0) & ((t & 2) ? dt1 : ~dt1) &
+                                           ((t & 4) ? dt2 : ~dt2) & ((t & 8) ? dt3 : ~dt3);
+                        if (m) atomicAdd(&s_hist[t * L + sb + lane], __popc(m));
+                    }
+                }
             }
-            if (valid) {
+            if (valid && !a.nostore) {
                 // unreached cells read -1
 #pragma unroll
                 for (int i = 0; i < 16; ++i) {
@@ -1312,8 +1334,38 @@ __global__ void __launch_bounds__(kMsThreads, 1) msbfs_sliced_kernel(MsArgs a, M
             s_ecc[s] = 0;
             s_dsum[s] = 0;
         }
-        // the next pass seeds the visited buffers this pass has just cleared
-        if (b + 1 < nbatches && !ms_barrier(ctl, bar, bar_target, a.spin_limit)) return;
+        if (p.hist) {
+            for (int i = threadIdx.x; i < (tlast + 1) * L; i += kMsThreads) {
+                if (s_hist[i]) atomicAdd(&p.hist[(i / L) * kMsMaxLanes + (i % L)], s_hist[i]);
+                s_hist[i] = 0;
+            }
+        }
+        // the next pass seeds the visited buffers this pass has just cleared;
+        // centrality products read every CTA's sums
+        const bool products = p.hist || a.clos;
+        if ((b + 1 < nbatches || products) && !ms_barrier(ctl, bar, bar_target, a.spin_limit)) return;
+        if (products && blockIdx.x == 0) {
+            for (int s = threadIdx.x; s < kb; s += kMsThreads) {
+                if (p.hist) {
+                    // sum over distances t = 1, 2, ... of (vertices at distance t) / t, ascending
+                    double h = 0.0;
+                    for (int t = 1; t <= tlast; ++t) {
+                        int32_t* c = p.hist + t * kMsMaxLanes + s;
+                        const int cnt = __ldcg(c);
+                        if (cnt) {
+                            h += (double)cnt / (double)t;
+                            *c = 0;
+                        }
+                    }
+                    a.harm[s0 + s] = h;
+                }
+                if (a.clos) {
+                    const int r = __ldcg(a.reached + s0 + s);
+                    const long long sum = __ldcg(a.dsum + s0 + s);
+                    a.clos[s0 + s] = r > 1 ? (double)(r - 1) / (double)sum : 0.0;
+                }
+            }
+        }
     }
     if (gtid == 0) ctl->bar[a.bar_parity ^ 1].count = 0;
 }
@@ -1543,7 +1595,11 @@ template <int W>
 int ms_launch_sliced_w(dawn_graph* g, MsArgs& a, MsSliced& p, cudaStream_t st) {
     dim3 grid(g->sms), block(kMsThreads);
     void* args[] = {&a, &p};
-    DAWN_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)msbfs_sliced_kernel<W>, grid, block, args, 0, st));
+    const int hist_bytes = (int)sizeof(int) * (kNbLevelsMax + 1) * 64 * W;
+    DAWN_CUDA_TRY(cudaFuncSetAttribute((const void*)msbfs_sliced_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       hist_bytes));
+    DAWN_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)msbfs_sliced_kernel<W>, grid, block, args,
+                                              p.hist ? hist_bytes : 0, st));
     return DAWN_OK;
 }
 
@@ -1601,7 +1657,10 @@ int msbfs_run(dawn_graph* g, const int32_t* sources, int32_t k, void* dist_block
     if (want != 0 && want != DAWN_MSBFS_SLICED && want != DAWN_MSBFS_PER_LEVEL)
         return fail(DAWN_E_INVALID, "kernel = %d: need 0, DAWN_MSBFS_SLICED or DAWN_MSBFS_PER_LEVEL", want);
     const size_t plane_bytes = sizeof(uint64_t) * 4 * ((size_t)g->n + 1);  // one level array or plane
-    const bool sliced = !nostore && (want == DAWN_MSBFS_SLICED || (want == 0 && !g->ms_sliced_off));
+    // harmonic centrality on the sliced kernel counts levels in its level arrays
+    // only; a graph on which a pass went deeper keeps the per-level kernel for it
+    const bool sliced = want == DAWN_MSBFS_SLICED ||
+                        (want == 0 && !g->ms_sliced_off && !(harmonic && g->ms_harm_deep));
 
     // sources: checked on the host whatever memory they live in
     std::vector<int32_t> hsrc((size_t)k);
@@ -1630,7 +1689,8 @@ int msbfs_run(dawn_graph* g, const int32_t* sources, int32_t k, void* dist_block
     size_t off_harm = off_clos + 256 * (((size_t)k * 8 + 255) / 256);
     size_t off_ring = off_harm + 256 * (((size_t)k * 8 + 255) / 256);
     size_t off_sum = off_ring + 256 * ((3 * kMsMaxLanes * sizeof(int32_t) + 255) / 256);
-    size_t off_dist = off_sum + 256;
+    size_t off_hist = off_sum + 256;
+    size_t off_dist = off_hist + 256 * (((size_t)(kNbLevelsMax + 1) * kMsMaxLanes * sizeof(int32_t) + 255) / 256);
     size_t dist_cells = 0;
     if (nostore) dist_cells = 0;                               // reductions only
     else if (!dist_block) dist_cells = (size_t)lanes * g->n;   // one pass's block, kept on the device
@@ -1647,8 +1707,11 @@ int msbfs_run(dawn_graph* g, const int32_t* sources, int32_t k, void* dist_block
     double* d_harm = harmonic ? (harm_dev ? harmonic : reinterpret_cast<double*>(t8 + off_harm)) : nullptr;
     int32_t* d_ring = reinterpret_cast<int32_t*>(t8 + off_ring);
     long long* d_sum = reinterpret_cast<long long*>(t8 + off_sum);
+    int32_t* d_hist = reinterpret_cast<int32_t*>(t8 + off_hist);
     cudaError_t e = cudaMemcpyAsync(d_src, hsrc.data(), sizeof(int32_t) * (size_t)k, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess && d_harm) e = cudaMemsetAsync(d_ring, 0, 3 * kMsMaxLanes * sizeof(int32_t), st);
+    if (e == cudaSuccess && d_harm && sliced)
+        e = cudaMemsetAsync(d_hist, 0, (size_t)(kNbLevelsMax + 1) * kMsMaxLanes * sizeof(int32_t), st);
 
     MsArgs a;
     a.in_ptr = g->in_ptr;
@@ -1726,6 +1789,7 @@ int msbfs_run(dawn_graph* g, const int32_t* sources, int32_t k, void* dist_block
         sp.nb_levels = std::min(kNbLevelsMax, g->ms_nb_levels * 4 / W);
         sp.planes = g->ms_planes;
         sp.planes_cap = g->ms_planes ? std::min(kPlanesMax, g->ms_planes_cap * 4 / W) : 0;
+        sp.hist = d_harm ? d_hist : nullptr;
         if (W == 1) lrc = ms_launch_sliced_w<1>(g, a, sp, st);
         else if (W == 2) lrc = ms_launch_sliced_w<2>(g, a, sp, st);
         else lrc = ms_launch_sliced_w<4>(g, a, sp, st);
@@ -1770,7 +1834,13 @@ int msbfs_run(dawn_graph* g, const int32_t* sources, int32_t k, void* dist_block
         DAWN_CUDA_TRY(cudaStreamSynchronize(st));
         if (status == DEV_PLANES) {
             // more levels than the level arrays hold: 15 planes, else the per-level kernel
-            if (g->ms_planes_cap < kPlanesMax && (size_t)kPlanesMax * plane_bytes <= kPlanesBudget) {
+            // (harmonic centrality: the per-level kernel, which sums the levels as they end)
+            if (harmonic && want != DAWN_MSBFS_SLICED) {
+                g->ms_harm_deep = 1;
+            } else if (harmonic) {
+                return fail(DAWN_E_INVALID, "harmonic centrality on the sliced kernel needs at most %d levels; "
+                                            "use DAWN_MSBFS_PER_LEVEL", kNbLevelsMax);
+            } else if (g->ms_planes_cap < kPlanesMax && (size_t)kPlanesMax * plane_bytes <= kPlanesBudget) {
                 if ((rc = ms_planes_alloc(g, kPlanesMax)) != DAWN_OK) return rc;
             } else if (want == DAWN_MSBFS_SLICED) {
                 return fail(DAWN_E_INVALID, "a pass needs more levels than the sliced kernel's planes hold "

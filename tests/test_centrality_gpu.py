@@ -5,10 +5,12 @@ Closeness and harmonic centrality are IEEE doubles computed on both sides by
 the same operations in the same order (harmonic: vertices at distance d over
 d, added in ascending d), so they are compared bit for bit as well.
 
-Covers every lane width, ragged source counts, duplicate and isolated
-sources, directed graphs, a high-diameter lattice (levels past int16: no rows
-are stored, so no overflow), host and device outputs, the all-sources RMAT
-scale-16 workload, and bad arguments.
+Covers both batched kernels (the sliced one, which counts each pass's
+levels from its level bits, and the per-level one), every lane width, ragged
+source counts, duplicate and isolated sources, directed graphs, a
+high-diameter lattice and a path past int16 (levels beyond the sliced
+kernel's level arrays: the call moves to the per-level kernel), host and
+device outputs, the all-sources RMAT scale-16 workload, and bad arguments.
 """
 import numpy as np
 import pytest
@@ -25,7 +27,10 @@ def upload(dawn, g):
                                   flags=dawn.DAWN_SYMMETRIC if g.symmetric else dawn.DAWN_DIRECTED)
 
 
-def run(dawn, h, srcs, lanes=0, device=False):
+KERNELS = [1, 2]  # DAWN_MSBFS_SLICED, DAWN_MSBFS_PER_LEVEL
+
+
+def run(dawn, h, srcs, lanes=0, device=False, kernel=0):
     k = len(srcs)
     if device:
         out = {"ecc": torch.zeros(k, dtype=torch.int32, device="cuda"),
@@ -39,7 +44,7 @@ def run(dawn, h, srcs, lanes=0, device=False):
                "closeness": np.zeros(k, np.float64), "harmonic": np.zeros(k, np.float64)}
         src = np.asarray(srcs, dtype=np.int32)
     summ = dawn.dawn_centrality(h, src, k, out["ecc"], out["dsum"], out["reached"], out["closeness"],
-                                out["harmonic"], {"lanes": lanes} if lanes else None)
+                                out["harmonic"], {"lanes": lanes, "kernel": kernel})
     if device:
         out = {key: v.cpu().numpy() for key, v in out.items()}
     out["summary"] = summ
@@ -62,14 +67,16 @@ def test_small_digraphs_all_sources(dawn, seed):
     h = upload(dawn, g)
     try:
         srcs = np.arange(g.n, dtype=np.int32)
-        for lanes in (64, 128, 256):
-            check(g, srcs, run(dawn, h, srcs, lanes))
+        for kernel in KERNELS:
+            for lanes in (64, 128, 256):
+                check(g, srcs, run(dawn, h, srcs, lanes, kernel=kernel))
     finally:
         dawn.dawn_graph_free(h)
 
 
+@pytest.mark.parametrize("kernel", KERNELS)
 @pytest.mark.parametrize("device", [False, True])
-def test_rmat_and_directed_ragged(dawn, device):
+def test_rmat_and_directed_ragged(dawn, device, kernel):
     for g in (gg.rmat(12, seed=2), gg.rmat(11, seed=9, symmetrise=False)):
         h = upload(dawn, g)
         try:
@@ -79,7 +86,7 @@ def test_rmat_and_directed_ragged(dawn, device):
             if (deg == 0).any():
                 srcs[10] = int(np.nonzero(deg == 0)[0][0])
             srcs[11] = int(np.argmax(deg))
-            check(g, srcs, run(dawn, h, srcs, 256, device))
+            check(g, srcs, run(dawn, h, srcs, 256, device, kernel))
         finally:
             dawn.dawn_graph_free(h)
 
@@ -92,9 +99,12 @@ def test_long_path_past_int16(dawn):
     h = upload(dawn, g)
     try:
         srcs = np.array([0, n // 2, n - 1], dtype=np.int32)
-        got = run(dawn, h, srcs, 64)
+        got = run(dawn, h, srcs, 64)  # the sliced kernel stops at level 16 and the per-level one runs
         check(g, srcs, got)
         assert got["ecc"].tolist() == [n - 1, n // 2, n - 1]
+        with pytest.raises(dawn.DawnError) as ei:  # asked for by name, the sliced kernel reports it
+            run(dawn, h, srcs, 64, kernel=1)
+        assert ei.value.code == dawn.DAWN_E_INVALID
     finally:
         dawn.dawn_graph_free(h)
 
