@@ -248,3 +248,33 @@ def test_rmat16_all_sources_full_size(dawn):
         np.testing.assert_array_equal(dsum[sample], d2)
     finally:
         dawn.dawn_graph_free(h)
+
+
+def test_rmat20_sliced_long_pieces(dawn):
+    """RMAT scale 20: the sliced kernel's row pieces are longer than on the
+    small graphs (the piece length grows with the arcs per warp) and CTAs own
+    many split rows.  256 sampled sources: every source's reached count is the
+    size of its component, and 4 rows against Alg. 2 (FIFO BFS), bit-exact,
+    for both kernels."""
+    g = gg.rmat(20, 16, 0.57, 0.19, 0.19, seed=2, symmetrise=True)
+    n = g.n
+    h = upload(dawn, g)
+    try:
+        srcs = gg.sample_sources(g, 256, seed=9).astype(np.int32)
+        lab = oracle.wcc(g.row_ptr, g.col_idx)
+        comp = np.bincount(lab, minlength=n)
+        for kernel in KERNELS:
+            block = torch.full((256, n), 77, dtype=torch.int16, device="cuda")
+            reached = torch.zeros(256, dtype=torch.int32, device="cuda")
+            ecc = torch.zeros(256, dtype=torch.int32, device="cuda")
+            dawn.dawn_msbfs_ex(h, torch.from_numpy(srcs).cuda(), 256, block, 2, 0, ecc, None, reached,
+                               {"lanes": 256, "kernel": kernel})
+            np.testing.assert_array_equal(reached.cpu().numpy(), comp[lab[srcs]])
+            rows = block[:4].cpu().numpy().astype(np.int32)
+            for i in range(4):
+                want = oracle.bfs_queue(g.row_ptr, g.col_idx, int(srcs[i]))
+                np.testing.assert_array_equal(rows[i], want)
+                assert ecc[i].item() == want.max()
+            del block
+    finally:
+        dawn.dawn_graph_free(h)
