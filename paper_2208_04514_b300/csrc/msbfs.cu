@@ -15,11 +15,17 @@
 // A lane whose level reached nothing is finished (its frontier is empty);
 // finished and unused lanes count as covered, so a vertex stops scanning its
 // in-neighbours as soon as every still-running lane is covered, and a vertex
-// covered for every running lane is skipped.  The kernel is persistent and
+// covered for every running lane is skipped.  Both kernels are persistent and
 // cooperative: batches, their levels and the per-batch reductions
-// (eccentricity = largest finite distance, distance sum, reached count, from
-// per-level counts) all run in one launch, separated by the bounded grid
-// barrier.
+// (eccentricity = largest finite distance, distance sum, reached count) all
+// run in one launch, separated by the bounded grid barrier.
+//
+// Two kernels compute the same results.  msbfs_kernel (per level) writes each
+// distance as its bit appears and counts each level's vertices per lane; it
+// handles any depth and serves centrality past 15 levels.  msbfs_sliced_kernel
+// (the default, further down) cuts the in-arc rows by in-degree into warp
+// tasks, pushes level 1 from the sources, and writes every distance cell once
+// per pass from per-level new-bit arrays.
 #include <algorithm>
 #include <climits>
 #include <functional>
