@@ -358,19 +358,20 @@ DAWN_API int dawn_set_tuning(dawn_graph_t g, const dawn_tuning* t);
 DAWN_API int dawn_msbfs(dawn_graph_t g, const int32_t* sources, int32_t k, void* dist_block,
                         int dist_bytes, int layout, int32_t* ecc, int64_t* dsum, void* stream);
 
-/* Kernels of the batched level loop (dawn_msbfs_opts.kernel).  Both give
- * identical results.
+/* Kernels of the batched level loop (dawn_msbfs_opts.kernel, also read by
+ * dawn_centrality).  Both give identical results.
  *   DAWN_MSBFS_SLICED     in-arc rows cut into warp tasks by in-degree (one
  *                         vertex per lane for short rows, row pieces for long
- *                         ones); each level only ORs visited words, and the
- *                         first-reach level of every (source, vertex) bit is
- *                         kept bit-sliced, so each distance row is written
- *                         once, whole, after the pass's last level.  Up to
- *                         32767 levels.
+ *                         ones); level 1 pushed from the sources; each level
+ *                         only ORs visited words and keeps its new bits, so
+ *                         each distance row is written once, whole, after the
+ *                         pass's last level.  Up to 32767 levels; harmonic
+ *                         centrality up to 15 (DAWN_E_INVALID past that when
+ *                         asked for by name).
  *   DAWN_MSBFS_PER_LEVEL  distances written level by level as bits appear;
- *                         any number of levels; dawn_centrality always uses it.
+ *                         any number of levels.
  * 0 picks SLICED, and PER_LEVEL for a graph on which a run has needed more
- * levels than SLICED's planes hold. */
+ * levels than SLICED holds (for harmonic centrality: more than 15). */
 #define DAWN_MSBFS_SLICED 1
 #define DAWN_MSBFS_PER_LEVEL 2
 
