@@ -476,7 +476,7 @@ def bench_batched(dawn, torch, flush, plain_sample=4096, k=0, lanes_list=(64, 12
     # L2-bound figure: the graph and the lane words live in L2, so the batched
     # loop is compared with this GPU's L2 read bandwidth, not with HBM
     l2_pass = recorded_value(ROOT / "paper_2208_04514_b300" / "csrc" / "msbfs.cu",
-                             ROOT / "profiles" / "msbfs_kernel_rmat16.md", "l2_bytes_per_pass")
+                             ROOT / "profiles" / "msbfs_sliced_kernel_rmat16.md", "l2_bytes_per_pass")
     l2_gbs = dawn.dawn_l2_read_gbs(64 << 20, 50)
     passes = (k + 255) // 256
     t256 = out["lanes"].get("256", best)["ms"] * 1e-3
