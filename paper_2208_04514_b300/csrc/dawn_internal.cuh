@@ -48,8 +48,10 @@ struct alignas(128) CtrSlot {
     unsigned long long qpack;  // queue size: entries (high 32 bits) | arcs (low 32 bits)
     unsigned long long nf;     // vertices first reached at this level
     unsigned long long mf;     // sum of their out-degrees
-    unsigned long long nc;     // pull levels: vertices still unreached (candidate lists)
-    unsigned long long lr;     // nonzero when a queued row has more than kEntryArcs arcs
+    unsigned long long nc;     // pull levels: vertices still unreached (candidate lists), low 32 bits;
+                               // list pulls: vertices their look-ahead showed at the next level, high 32 bits
+    unsigned long long lr;     // nonzero when a queued row has more than kEntryArcs arcs; list pulls
+                               // (which queue nothing): the out-degree sum of the look-ahead's vertices
     unsigned long long pad[11];
 };
 

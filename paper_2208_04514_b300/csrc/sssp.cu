@@ -44,6 +44,9 @@ namespace {
 #ifndef DAWN_CTL_PREFETCH
 #define DAWN_CTL_PREFETCH 1
 #endif
+#ifndef DAWN_LOOKAHEAD
+#define DAWN_LOOKAHEAD 1  // list pulls look one level ahead for the stop at the component's size
+#endif
 #ifndef DAWN_SSSP_SMEM_BITMAP_MAX
 #define DAWN_SSSP_SMEM_BITMAP_MAX (200 * 1024)
 #endif
@@ -711,6 +714,40 @@ __device__ void pull_level(const SsspArgs& a, int step, const uint32_t* vcur, ui
     }
 }
 
+// The look-ahead's second hop: whether one of u's first two in-neighbours
+// (h0 for u = f2.x, h1 for u = f2.y; -1 past a row's end) was reached before
+// the level `step` (the same step-start test as the list pull's).
+__device__ __forceinline__ bool two_hop_hit(const SsspArgs& a, int2 h0, int2 h1, int step) {
+    const int ws[4] = {h0.x, h0.y, h1.x, h1.y};
+    int dw[4];
+#pragma unroll
+    for (int x = 0; x < 4; ++x) dw[x] = ws[x] >= 0 ? __ldcg(a.dist + ws[x]) : -1;
+    bool hit = false;
+#pragma unroll
+    for (int x = 0; x < 4; ++x) hit |= dw[x] >= 0 && dw[x] < step;
+    return hit;
+}
+
+// A vertex v the look-ahead placed at level step + 1 (lanes with `ahead`;
+// called by the lanes that ran the test, possibly divergent): dist is
+// written now, and the count and out-degrees go straight to the level's
+// counter slot (step % 3, as the loop picks it) with one pair of atomics
+// per warp: the count in nc's high word, the degrees in lr (a list pull
+// queues nothing).  indeg: v's in-degree (its out-degree on a symmetric graph).
+__device__ __forceinline__ void look_ahead(const SsspArgs& a, bool ahead, int v, int indeg, int lane, int step,
+                                           bool symmetric) {
+    const unsigned hb = __ballot_sync(__activemask(), ahead);
+    if (!ahead) return;
+    a.dist[v] = step + 1;
+    const unsigned deg = (unsigned)(symmetric ? indeg : (__ldg(a.row_ptr + v + 1) - __ldg(a.row_ptr + v)));
+    const unsigned dsum = __reduce_add_sync(hb, deg);  // < m < 2^31: row_ptr is int32
+    if (lane == __ffs(hb) - 1) {
+        CtrSlot* out = &a.ctl->ctr[a.bar_parity][step % 3];
+        atomicAdd(&out->nc, (unsigned long long)__popc(hb) << 32);
+        atomicAdd(&out->lr, (unsigned long long)dsum);
+    }
+}
+
 // BOVM pull over this CTA's list of candidates (the vertices a pull left
 // unreached), instead of the whole bitmap.  The step-start visited test reads
 // the distances: 0 <= dist[u] < step exactly when u was reached before this
@@ -722,6 +759,8 @@ __device__ void pull_level(const SsspArgs& a, int step, const uint32_t* vcur, ui
 __device__ __noinline__ LevelCount list_pull_level(const SsspArgs& a, int step, uint32_t* vis, const int32_t* cand,
                                                   int ncand, int32_t* keep, int* s_cn) {
     const int lane = threadIdx.x & 31;
+    // the look-ahead below serves the stop at the component's size (known on symmetric graphs)
+    const bool look = DAWN_LOOKAHEAD && a.mode == DAWN_MODE_AUTO && a.reach_target <= a.n;
     long long nf = 0, mf = 0;
     const bool symmetric = a.in_ptr == a.row_ptr;
     // one candidate per thread and round; the loop bound is the same for the whole warp
@@ -792,6 +831,22 @@ __device__ __noinline__ LevelCount list_pull_level(const SsspArgs& a, int step, 
             atomicOr(vis + (v >> 5), 1u << (v & 31));
             nf += 1;
             mf += symmetric ? (ie - ib) : (__ldg(a.row_ptr + v + 1) - __ldg(a.row_ptr + v));
+        } else if (look && has) {
+            // Look one level ahead.  v has no in-neighbour reached before this
+            // level, so d(v) >= step + 1, and each of its first two
+            // in-neighbours u (its whole row when it has at most two in-arcs)
+            // is unreached at step start too: an in-neighbour of u reached
+            // before this level puts u at this level and v at the next one.
+            // The two-hop test reads u's first two in-neighbours and their
+            // distances (the same step-start test as above).  It feeds the
+            // stop test only: when the vertices it shows are all that is
+            // left of the source's component, the loop ends here and the next
+            // level is not run.  Their dist is written now, and they stay in
+            // the list and out of the bitmap, so that a next level, if it
+            // runs, finds them again with the same value.
+            const int2 h0 = f2.x >= 0 ? __ldg(a.first2 + f2.x) : make_int2(-1, -1);
+            const int2 h1 = f2.y >= 0 ? __ldg(a.first2 + f2.y) : make_int2(-1, -1);
+            look_ahead(a, two_hop_hit(a, h0, h1, step), v, ie - ib, lane, step, symmetric);
         }
         warp_keep(has && !found, v, lane, keep, s_cn);
     }
@@ -1092,7 +1147,8 @@ __device__ __forceinline__ void next_level(const RuleArgs& a, LoopState& L, cons
     const bool lists = a.lists;
     const long long nf_cur = (long long)snap[1];
     const long long mf_cur = (long long)snap[2];
-    const long long nc_cur = (long long)snap[3];  // unreached candidates, after a pull
+    const long long nc_cur = (long long)(snap[3] & 0xffffffffull);  // unreached candidates, after a pull (the
+                                                                     // high word counts a list pull's look-ahead)
     if (nf_cur == 0 || step >= a.n) {
         L.kind = kStop;
         L.levels = step > 0 ? step - 1 : 0;
@@ -1139,8 +1195,12 @@ __global__ void __launch_bounds__(kThreads, DAWN_SSSP_MIN_CTAS) sssp_kernel(Sssp
     // The status load overlaps the clearing below.
     if (threadIdx.x == 0) s_status = ld_relaxed_s32(&ctl->status);
     const int lane = threadIdx.x & 31;
-    const bool tracer = blockIdx.x == 0 && threadIdx.x == 0;
-    int tslot = 0;
+    // the per-level trace: thread 0 of CTA 0, its record count kept in shared
+    // memory (not a register carried through the level loop)
+    const bool tracer = a.trace && blockIdx.x == 0 && threadIdx.x == 0;
+    __shared__ int s_tslot;
+    int& tslot = s_tslot;
+    if (tracer) tslot = 0;
     unsigned* bar = &ctl->bar[a.bar_parity].count;
     unsigned bar_target = 0;
     if (tracer) trace_rec(a, tslot, 0, 0, 1);
@@ -1258,14 +1318,17 @@ __global__ void __launch_bounds__(kThreads, DAWN_SSSP_MIN_CTAS) sssp_kernel(Sssp
         if (tracer) trace_rec(a, tslot, 1, 0, 1);
     }
 
-    uint32_t* vcur = a.vis0;
-    uint32_t* vnext = a.vis1;
-    int32_t* cl[2] = {a.cand0 + blockIdx.x * region, a.cand1 + blockIdx.x * region};
+    int vpar = 0;  // the current visited bitmap: vis0 or vis1 (they swap after a bitmap pull)
     int cpar = 0;  // the list the next list pull reads
     while (true) {
         const int kind = L.kind;  // chosen by thread 0 inside the last barrier
         if (kind == kStop) break;
         const int from = L.from;
+        uint32_t* const vcur = vpar ? a.vis1 : a.vis0;
+        uint32_t* const vnext = vpar ? a.vis0 : a.vis1;
+        // this CTA's two candidate lists
+        int32_t* const cl0 = (cpar ? a.cand1 : a.cand0) + blockIdx.x * region;
+        int32_t* const cl1 = (cpar ? a.cand0 : a.cand1) + blockIdx.x * region;
         CtrSlot* cur = &ctr[step % 3];
         // the frontier found at step s lives in queue (s & 1)
         const Queue qcur = (step & 1) ? Queue{a.q1, a.q1off} : Queue{a.q0, a.q0off};
@@ -1287,17 +1350,17 @@ __global__ void __launch_bounds__(kThreads, DAWN_SSSP_MIN_CTAS) sssp_kernel(Sssp
         CtrSlot* out = &ctr[(step + 1) % 3];
         long long nf = 0, mf = 0;
         if (kind == kBitmapPull) {
-            int32_t* keep = lists ? cl[cpar] : nullptr;
+            int32_t* keep = lists ? cl0 : nullptr;
             if (a.smem_words > 0) pull_level<true>(a, step + 1, vcur, vnext, nf, mf, keep, &s_cn);
             else pull_level<false>(a, step + 1, vcur, vnext, nf, mf, keep, &s_cn);
         } else if (kind == kListPull) {
-            const LevelCount lc = list_pull_level(a, step + 1, vcur, cl[cpar], s_cin, cl[cpar ^ 1], &s_cn);
+            const LevelCount lc = list_pull_level(a, step + 1, vcur, cl0, s_cin, cl1, &s_cn);
             nf = lc.nf;
             mf = lc.mf;
             cpar ^= 1;
         } else if (from == kFromList) {
             // the frontier: entries of the last list pull's input list found by it
-            const LevelCount lc = list_push_level(a, step + 1, vcur, cl[cpar ^ 1], s_cprev, out);
+            const LevelCount lc = list_push_level(a, step + 1, vcur, cl1, s_cprev, out);
             nf = lc.nf;
             mf = lc.mf;
         } else {
@@ -1315,14 +1378,31 @@ __global__ void __launch_bounds__(kThreads, DAWN_SSSP_MIN_CTAS) sssp_kernel(Sssp
             }))
             return;
         if (tracer) trace_rec(a, tslot, kind == kPush ? 2 : (kind == kBitmapPull ? 3 : 5), step + 1, (long long)s_snap[1]);
+        if (kind == kListPull && (s_snap[3] >> 32) != 0 && L.kind != kStop) {
+            // the list pull's look-ahead showed la vertices at level step + 2;
+            // when they are all that is left of the component (their dist is
+            // written), that level is not run.  It counts as a pull level (a
+            // pull test decided it) in place of the one the rule had chosen.
+            const long long la = (long long)(s_snap[3] >> 32);
+            if (L.reached + la >= a.reach_target) {
+                __syncthreads();  // every thread has read L.kind
+                if (threadIdx.x == 0) {
+                    L.reached += la;
+                    L.edges += (long long)s_snap[4];
+                    if (L.kind == kPush) --L.pushes;
+                    else --L.pulls;
+                    ++L.pulls;
+                    L.levels = step + 2;
+                }
+                break;
+            }
+        }
         if (kind == kBitmapPull) {
-            uint32_t* t = vcur;
-            vcur = vnext;
-            vnext = t;
+            vpar ^= 1;
         }
         ++step;
     }
-    if (gtid == 0 && a.stats) {
+    if (blockIdx.x == 0 && threadIdx.x == 0 && a.stats) {
         dawn_sssp_stats s;
         s.levels = L.levels;
         s.push_steps = L.pushes;

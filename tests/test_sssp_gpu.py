@@ -484,3 +484,75 @@ def test_many_sources_on_the_cluster_engine(dawn, where):
             check_stats(g, rows[i], dawn.stats_from_words(st[i]))
     finally:
         dawn.dawn_graph_free(h)
+
+
+def _trace_levels(dawn, h, g, src):
+    """dawn_sssp_ex with the per-level trace: the distances, the statistics and
+    the trace records {kind, step, count, time} (kind 5 = a list pull)."""
+    tr = torch.zeros((64, 4), dtype=torch.int64, device="cuda")
+    d, st = gpu_sssp(dawn, h, g.n, src, {"engine": 1, "trace": tr.data_ptr(), "trace_cap": 64})
+    recs = [r for r in tr.cpu().numpy() if r[3] != 0]
+    return d, st, recs
+
+
+def test_lookahead_stop_folds_the_last_level(dawn):
+    """A list pull on a symmetric graph tests the candidates it leaves
+    unreached one level further (through their first two in-neighbours and
+    theirs).  When that shows every vertex left in the source's component,
+    the loop stops there and the last level is not run: the trace then ends
+    with a list pull one step short of the eccentricity.  Distances and
+    statistics (reached, E_r, levels, push + pull levels) stay those of the
+    oracle whether or not it folds.  The second graph hangs a K4 off a path:
+    the K4's far vertices have a first two in-neighbours that lie at their own
+    level or the one before, so no two-hop test can place them and the level
+    that finds them runs."""
+    base = gg.rmat(16, seed=2)
+    folded = 0
+    h = upload(dawn, base)
+    try:
+        for src in gg.sample_sources(base, 24, seed=21):
+            src = int(src)
+            d, st, recs = _trace_levels(dawn, h, base, src)
+            np.testing.assert_array_equal(d, oracle.sssp_sovm(base.row_ptr, base.col_idx, src), err_msg=f"src={src}")
+            check_stats(base, d, st)
+            assert st["push_steps"] + st["pull_steps"] == st["levels"]
+            last = recs[-1]
+            if last[0] == 5 and last[1] == st["levels"] - 1:
+                folded += 1
+            else:
+                assert last[1] == st["levels"], (src, recs[-1], st)
+    finally:
+        dawn.dawn_graph_free(h)
+    assert folded >= 1
+
+    # the RMAT graph with a path to a K4 from its largest hub
+    rp, ci, n = base.row_ptr, base.col_idx, base.n
+    src_l = list(np.repeat(np.arange(n), np.diff(rp)))
+    dst_l = list(ci)
+    hub = int(np.argmax(base.out_degree()))
+
+    def edge(a, b):
+        src_l.extend([a, b])
+        dst_l.extend([b, a])
+    path = list(range(n, n + 5))
+    edge(hub, path[0])
+    for a, b in zip(path, path[1:]):
+        edge(a, b)
+    k4 = [n + 5, n + 6, n + 7, n + 8]
+    edge(path[-1], k4[0])
+    for i in range(4):
+        for j in range(i + 1, 4):
+            edge(k4[i], k4[j])
+    g = gg.from_arcs(n + 9, src_l, dst_l, symmetric=True)
+    h = upload(dawn, g)
+    try:
+        for src in list(gg.sample_sources(base, 8, seed=22)) + [hub, path[2], k4[3]]:
+            src = int(src)
+            d, st, recs = _trace_levels(dawn, h, g, src)
+            np.testing.assert_array_equal(d, oracle.sssp_sovm(g.row_ptr, g.col_idx, src), err_msg=f"src={src}")
+            check_stats(g, d, st)
+            assert st["push_steps"] + st["pull_steps"] == st["levels"]
+            if set(np.nonzero(d == d.max())[0].tolist()) <= set(k4[1:]):
+                assert recs[-1][1] == st["levels"], (src, recs[-1], st)  # the last level ran
+    finally:
+        dawn.dawn_graph_free(h)
