@@ -312,6 +312,58 @@ __device__ __forceinline__ void load_batch(const Queue& q, int qn, int b, int la
     eoff = i < qn ? __ldcg(q.off + i) : INT_MAX;
 }
 
+// The rows left in every warp's buffer at the end of a push level, queued
+// with one reservation for the whole CTA: the level's counter is a single
+// address, and with one reservation per warp the last warps of a heavy
+// level waited microseconds in line for it.  Reached by every warp of the
+// CTA (nbuf = 0 for a warp without work).
+__device__ __noinline__ void push_final_flush(const int2* buf, int nbuf, int lane, Queue q, CtrSlot* out) {
+    __shared__ int s_fr[kWarps], s_fa[kWarps], s_fl[kWarps];
+    const int warp = threadIdx.x >> 5;
+    int arcs = 0;
+    bool lng = false;
+    for (int i = lane; i < nbuf; i += 32) {
+        const int d = buf[i].y;
+        arcs += d;
+        lng |= d > kEntryArcs;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) arcs += __shfl_xor_sync(kFull, arcs, o);
+    lng = __any_sync(kFull, lng);
+    if (lane == 0) {
+        s_fr[warp] = nbuf;
+        s_fa[warp] = arcs;
+        s_fl[warp] = lng ? 1 : 0;
+    }
+    __syncthreads();
+    if (warp == 0) {  // kWarps == 32: one lane per warp
+        const int r = s_fr[lane], ar = s_fa[lane];
+        const int ri = warp_inclusive_scan(r, lane), ai = warp_inclusive_scan(ar, lane);
+        const int rows = __shfl_sync(kFull, ri, 31), tarcs = __shfl_sync(kFull, ai, 31);
+        const bool anylng = __any_sync(kFull, s_fl[lane] != 0);
+        unsigned long long base = 0;
+        if (lane == 0 && rows > 0) base = atomicAdd(&out->qpack, ((unsigned long long)rows << 32) | (unsigned)tarcs);
+        base = __shfl_sync(kFull, base, 0);
+        if (lane == 0 && anylng) atomicOr(&out->lr, 1ull);
+        s_fr[lane] = (int)(base >> 32) + ri - r;            // this warp's first slot
+        s_fa[lane] = (int)(base & 0xffffffffu) + ai - ar;  // and the arc offset of its first row
+    }
+    __syncthreads();
+    const int slot0 = s_fr[warp];
+    int carry = s_fa[warp];
+    for (int i0 = 0; i0 < nbuf; i0 += 32) {
+        const int i = i0 + lane;
+        const int2 e = i < nbuf ? buf[i] : make_int2(0, 0);
+        const int incl = warp_inclusive_scan(e.y, lane);
+        if (i < nbuf) {
+            q.ent[slot0 + i] = e;
+            q.off[slot0 + i] = carry + incl - e.y;
+        }
+        carry += __shfl_sync(kFull, incl, 31);
+    }
+    __syncwarp();
+}
+
 // Windows of 32 arcs a push takes per group (see push_level).
 constexpr int kPushGroup = 4;
 
@@ -415,7 +467,10 @@ __device__ void push_level(const SsspArgs& a, int step, uint32_t* vis, Queue qin
     if (light) {
         const long long per = (qn + nw - 1) / nw;
         const long long s0 = gw * per;
-        if (s0 >= qn) return;
+        if (s0 >= qn) {
+            push_final_flush(buf, 0, lane, qout, out);  // the CTA's reservation waits for every warp
+            return;
+        }
         const long long s1 = min((long long)qn, s0 + per);
         bstart = (int)s0;
         load_batch(qin, qn, bstart, lane, e, eoff);
@@ -426,7 +481,10 @@ __device__ void push_level(const SsspArgs& a, int step, uint32_t* vis, Queue qin
         long long chunk = (E + nw - 1) / nw;
         chunk = (chunk + 31) & ~31LL;
         a0 = gw * chunk;
-        if (a0 >= E) return;
+        if (a0 >= E) {
+            push_final_flush(buf, 0, lane, qout, out);
+            return;
+        }
         a1 = min(E, a0 + chunk);
         // largest slot i with off[i] <= a0 (off[0] = 0, so one exists)
         int lo = 0, hi = qn;
@@ -514,7 +572,7 @@ __device__ void push_level(const SsspArgs& a, int step, uint32_t* vis, Queue qin
             nbuf = 0;
         }
     }
-    if (nbuf > 0) warp_flush_rows(buf, nbuf, lane, qout, out);
+    push_final_flush(buf, nbuf, lane, qout, out);
 }
 
 // BOVM pull: every unreached vertex tests its in-neighbours against the
