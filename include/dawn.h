@@ -429,7 +429,13 @@ DAWN_API int dawn_centrality(dawn_graph_t g, const int32_t* sources, int32_t k, 
  * result is identical alone and in any mix.  A host thread owned by the
  * server admits requests and collects completions; while work is queued the
  * server's kernel occupies every SM (other kernels wait), and it exits
- * after about 2 ms without work.
+ * after about 2 ms without work.  A request of at most 4 sources on a graph
+ * served in AUTO mode that arrives while the server is idle (nothing queued
+ * or on the device) runs instead as single-source searches, each on the
+ * engine dawn_sssp would pick (on a low-degree graph, thread-block clusters
+ * side by side), on a stream of the server's, with the same rows as in the
+ * loop; the server then uses that graph's single-source work buffers too, so
+ * no other call may use the handle while the server is live.
  *   graphs          ngraphs handles (borrowed; must outlive the server).
  *   mem_budget_bytes  device bytes for the distance blocks of admitted
  *                   requests whose dist_out is host memory (k * n * dist_bytes

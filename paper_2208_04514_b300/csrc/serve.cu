@@ -932,6 +932,17 @@ struct dawn_server {
     std::vector<dawn::SvGraph> host_graphs;  // device pointers of each graph's server state
     int fatal = DAWN_OK;
     int device = 0;
+    // the idle fast path (see start_fast): a lone small request on an AUTO
+    // low-degree graph runs on the single-source cluster engine
+    std::vector<char> fast_ok;      // per graph
+    cudaStream_t fstream = nullptr;
+    cudaEvent_t fdone = nullptr;
+    uint64_t fast_req = 0;          // the request running there (0: none)
+    int32_t* fstage = nullptr;      // int32 rows when the request wants int16 rows
+    size_t fstage_bytes = 0;
+    int32_t* fsrc = nullptr;        // its sources on the device
+    int* fovf_dev = nullptr;        // set when a distance does not fit int16
+    int* fovf_host = nullptr;       // pinned copy
 };
 
 namespace dawn {
@@ -1005,6 +1016,106 @@ void fail_all(dawn_server* s, int code) {
     s->queue.clear();
 }
 
+// Every row of request q is in its block: copy a staged block out to the
+// host, or finish the request.  Called with s->mu held.
+void rows_complete(dawn_server* s, Request* q) {
+    if (!q->out_dev && q->err == DAWN_OK) {
+        cudaMemcpyAsync(q->dist_out, q->block, q->block_bytes, cudaMemcpyDeviceToHost, s->cstream);
+        cudaEventRecord(q->copied, s->cstream);
+    } else {
+        q->state = q->err == DAWN_OK ? DAWN_REQ_DONE : DAWN_REQ_FAILED;
+        q->t_done = now_s();
+        if (q->staged) { arena_free(s, q->arena_off, q->block_bytes); q->staged = false; }
+    }
+}
+
+// int32 distance rows to int16 rows; *ovf = 1 when a distance does not fit
+// (the request then fails with DAWN_E_OVERFLOW, as a lane of the loop does).
+__global__ void fast_rows16_kernel(const int32_t* __restrict__ d, long long total, int16_t* out, int* ovf) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+        const int v = d[i];
+        if (v > 32767) *ovf = 1;
+        out[i] = (int16_t)(v > 32767 ? 32767 : v);
+    }
+}
+
+// The idle fast path.  A request of at most kFastMaxK sources on a graph
+// served in AUTO mode, arriving while the server has nothing else queued or on
+// the device, runs as single-source searches on a stream of its own instead of
+// one bit lane each in the serving loop: on a low-degree graph (average
+// out-degree below 8: lattices, road-like graphs) on thread-block clusters
+// side by side (cluster_launch_many), else one launch per source with the
+// single-source AUTO engine.  A lone search in the loop advances one level per
+// loop iteration, several times slower than a cluster level or a grid level
+// of the single-source kernel.  The distances are the same (every engine is
+// exact).  Requests that arrive meanwhile queue for the loop, whose kernel
+// starts when the fast path's kernels release their SMs.  Returns DAWN_OK
+// when it started; otherwise the request stays in the queue (and a graph
+// whose engine could not be launched leaves the fast path).
+constexpr int kFastMaxK = 4;
+
+int start_fast(dawn_server* s, Request* q) {
+    dawn_graph* g = s->graphs[q->graph];
+    const int k = (int)q->sources.size();
+    const long long n = g->n;
+    if (!q->block) {
+        if (!arena_alloc(s, q->block_bytes, &q->arena_off)) return DAWN_E_NOMEM;
+        q->block = s->arena + q->arena_off;
+        q->staged = true;
+    }
+    int32_t* rows = reinterpret_cast<int32_t*>(q->block);
+    if (q->dist_bytes == 2) {
+        const size_t need = sizeof(int32_t) * (size_t)k * (size_t)n;
+        if (need > s->fstage_bytes) {
+            if (s->fstage) cudaFree(s->fstage);
+            s->fstage = nullptr;
+            s->fstage_bytes = 0;
+            if (cudaMalloc((void**)&s->fstage, need) != cudaSuccess) return DAWN_E_NOMEM;
+            s->fstage_bytes = need;
+        }
+        rows = s->fstage;
+    }
+    cudaError_t e = cudaMemcpyAsync(s->fsrc, q->sources.data(), sizeof(int32_t) * (size_t)k, cudaMemcpyHostToDevice,
+                                    s->fstream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->fovf_dev, 0, sizeof(int), s->fstream);
+    if (e != cudaSuccess) return cuda_fail(e, "serving fast path", __FILE__, __LINE__);
+    int rc = DAWN_OK;
+    if (g->m < 8 * (int64_t)g->n && g->cl_size >= 0) {
+        rc = cluster_launch_many(g, s->fsrc, k, rows, n, nullptr, nullptr, s->fstream);
+    } else {
+        for (int i = 0; i < k && rc == DAWN_OK; ++i)
+            rc = sssp_launch(g, q->sources[(size_t)i], rows + (size_t)i * (size_t)n, nullptr, nullptr, s->fstream);
+    }
+    if (rc != DAWN_OK) {
+        s->fast_ok[q->graph] = 0;
+        if (q->staged) { arena_free(s, q->arena_off, q->block_bytes); q->staged = false; q->block = nullptr; }
+        return rc;
+    }
+    if (q->dist_bytes == 2) {
+        const long long total = (long long)k * n;
+        const int blocks = (int)std::min<long long>((total + 255) / 256, 4LL * s->sms);
+        fast_rows16_kernel<<<blocks, 256, 0, s->fstream>>>(rows, total, reinterpret_cast<int16_t*>(q->block), s->fovf_dev);
+    }
+    cudaMemcpyAsync(s->fovf_host, s->fovf_dev, sizeof(int), cudaMemcpyDeviceToHost, s->fstream);
+    cudaEventRecord(s->fdone, s->fstream);
+    q->next = k;
+    q->state = DAWN_REQ_RUNNING;
+    s->fast_req = q->id;
+    return DAWN_OK;
+}
+
+// The fast path's request once its stream reached fdone.
+void finish_fast(dawn_server* s) {
+    Request* q = s->reqs.count(s->fast_req) ? s->reqs[s->fast_req] : nullptr;
+    const int rc = graph_sync_status(s->graphs[q ? q->graph : 0], s->fstream);
+    s->fast_req = 0;
+    if (!q) return;
+    if (rc != DAWN_OK) q->err = rc;
+    else if (*s->fovf_host) q->err = DAWN_E_OVERFLOW;
+    q->rows_done = (int)q->sources.size();
+    rows_complete(s, q);
+}
+
 // One pass of the host side of the loop.  Called with s->mu held.
 bool service(dawn_server* s) {
     bool progress = false;
@@ -1027,18 +1138,14 @@ bool service(dawn_server* s) {
         if (!q) continue;
         if (r.status == DEV_OVERFLOW) q->err = DAWN_E_OVERFLOW;
         q->rows_done += 1;
-        if (q->rows_done == (int)q->sources.size()) {
-            if (!q->out_dev && q->err == DAWN_OK) {
-                cudaMemcpyAsync(q->dist_out, q->block, q->block_bytes, cudaMemcpyDeviceToHost, s->cstream);
-                cudaEventRecord(q->copied, s->cstream);
-            } else {
-                q->state = q->err == DAWN_OK ? DAWN_REQ_DONE : DAWN_REQ_FAILED;
-                q->t_done = now_s();
-                if (q->staged) { arena_free(s, q->arena_off, q->block_bytes); q->staged = false; }
-            }
-        }
+        if (q->rows_done == (int)q->sources.size()) rows_complete(s, q);
     }
     s->hs->done_head = head;
+    // ---- the idle fast path: its request, once its stream is through
+    if (s->fast_req && cudaEventQuery(s->fdone) != cudaErrorNotReady) {
+        finish_fast(s);
+        progress = true;
+    }
     // ---- finished host copies
     for (auto& kv : s->reqs) {
         Request* q = kv.second;
@@ -1049,6 +1156,18 @@ bool service(dawn_server* s) {
                 if (q->staged) { arena_free(s, q->arena_off, q->block_bytes); q->staged = false; }
                 progress = true;
             }
+        }
+    }
+    // ---- the idle fast path: a lone small request on a low-degree AUTO graph
+    //      while the loop has nothing queued, admitted or running
+    if (!s->fast_req && !s->kernel_live && s->hs->batch_ack == s->batch_seq && s->queue.size() == 1) {
+        Request* q = s->reqs[s->queue.front()];
+        bool idle = true;
+        for (size_t g = 0; g < s->graphs.size(); ++g) idle &= (int)s->free_lanes[g].size() == s->lanes;
+        if (idle && q->state == DAWN_REQ_PENDING && q->next == 0 && s->fast_ok[q->graph] &&
+            (int)q->sources.size() <= kFastMaxK && start_fast(s, q) == DAWN_OK) {
+            s->queue.pop_front();
+            progress = true;
         }
     }
     // ---- admissions: one batch at a time, the device acknowledges it
@@ -1151,6 +1270,13 @@ void server_release(dawn_server* s) {
     }
     if (s->kstream) cudaStreamSynchronize(s->kstream);
     if (s->cstream) cudaStreamSynchronize(s->cstream);
+    if (s->fstream) cudaStreamSynchronize(s->fstream);
+    if (s->fstage) cudaFree(s->fstage);
+    if (s->fsrc) cudaFree(s->fsrc);
+    if (s->fovf_dev) cudaFree(s->fovf_dev);
+    if (s->fovf_host) cudaFreeHost(s->fovf_host);
+    if (s->fdone) cudaEventDestroy(s->fdone);
+    if (s->fstream) cudaStreamDestroy(s->fstream);
     for (auto& hg : s->host_graphs) free_graph_state(hg);
     if (s->d_graphs) cudaFree(s->d_graphs);
     if (s->d_ctl) cudaFree(s->d_ctl);
@@ -1249,6 +1375,17 @@ DAWN_API int dawn_serve_create_ex(const dawn_graph_t* graphs, int ngraphs, size_
         std::vector<int> fl;
         for (int l = max_lanes - 1; l >= 0; --l) fl.push_back(l);
         s->free_lanes.push_back(fl);
+        // the idle fast path: graphs served in AUTO mode
+        s->fast_ok.push_back(md == DAWN_SERVE_AUTO ? 1 : 0);
+    }
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->fstream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->fdone, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&s->fsrc, sizeof(int32_t) * kFastMaxK);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&s->fovf_dev, sizeof(int));
+    if (e == cudaSuccess) e = cudaHostAlloc((void**)&s->fovf_host, sizeof(int), cudaHostAllocDefault);
+    if (e != cudaSuccess) {
+        server_release(s);
+        return cuda_fail(e, "dawn_serve_create (fast path)", __FILE__, __LINE__);
     }
     e = cudaMemcpy(s->d_graphs, hg.data(), sizeof(SvGraph) * ngraphs, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {

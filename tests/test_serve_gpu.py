@@ -222,3 +222,59 @@ def test_serving_graphs_at_full_size(dawn, mode):
         dawn.dawn_serve_destroy(s)
         for h in hs:
             dawn.dawn_graph_free(h)
+
+
+@pytest.mark.parametrize("dist_bytes", [2, 4])
+def test_idle_fast_path_on_a_low_degree_graph(dawn, dist_bytes):
+    """A lone request of at most four sources on a graph served in AUTO mode
+    whose average out-degree is below 8 runs, while the server is idle, as
+    single-source searches on thread-block clusters; requests that arrive
+    together run in the serving loop.  Either way every row is the oracle's
+    (Alg. 2), in int16 or int32, to host or device memory, and the same
+    sources give the same rows both ways."""
+    lat = gg.lattice(1024, 1024, 0.1, seed=3)   # m < 8n: the fast path's kind of graph
+    rm = gg.rmat(12, seed=22)
+    hs = [dawn.dawn_graph_upload(lat.row_ptr, lat.col_idx, flags=dawn.DAWN_SYMMETRIC),
+          dawn.dawn_graph_upload(rm.row_ptr, rm.col_idx, flags=dawn.DAWN_SYMMETRIC)]
+    s = dawn.dawn_serve_create(hs, 0, 64)
+    dt = np.int16 if dist_bytes == 2 else np.int32
+    tdt = torch.int16 if dist_bytes == 2 else torch.int32
+    try:
+        pool = gg.sample_sources(lat, 8, seed=41)
+        lone = {}
+        for i, where in enumerate(("device", "host", "device")):
+            srcs = pool[i:i + 1 + i]   # 1, 2, 3 sources
+            if where == "device":
+                out = torch.full((len(srcs), lat.n), 77, dtype=tdt, device="cuda")
+            else:
+                out = np.full((len(srcs), lat.n), 77, dtype=dt)
+            rid = dawn.dawn_serve_submit(s, 0, np.ascontiguousarray(srcs, dtype=np.int32), dist_bytes=dist_bytes,
+                                         dist_out=out)
+            wait_done(dawn, s, rid)
+            got = out.cpu().numpy() if where == "device" else out
+            for j, src in enumerate(srcs):
+                want = oracle.bfs_queue(lat.row_ptr, lat.col_idx, int(src)).astype(dt)
+                np.testing.assert_array_equal(got[j], want)
+                lone[int(src)] = got[j].copy()
+        # a burst: requests on both graphs at once (the loop), lattice rows as when alone
+        reqs = []
+        for gi, g in enumerate((lat, rm)):
+            for r in range(3):
+                srcs = pool[r:r + 2] if gi == 0 else gg.sample_sources(g, 2, seed=50 + r)
+                out = torch.full((len(srcs), g.n), 77, dtype=tdt, device="cuda")
+                rid = dawn.dawn_serve_submit(s, gi, np.ascontiguousarray(srcs, dtype=np.int32),
+                                             dist_bytes=dist_bytes, dist_out=out)
+                reqs.append((g, srcs, out, rid))
+        dawn.dawn_serve_drain(s, 120000)
+        for g, srcs, out, rid in reqs:
+            assert dawn.dawn_serve_poll(s, rid) == dawn.DAWN_REQ_DONE
+            got = out.cpu().numpy()
+            for j, src in enumerate(srcs):
+                want = oracle.bfs_queue(g.row_ptr, g.col_idx, int(src)).astype(dt)
+                np.testing.assert_array_equal(got[j], want)
+                if g is lat and int(src) in lone:
+                    np.testing.assert_array_equal(got[j], lone[int(src)])
+    finally:
+        dawn.dawn_serve_destroy(s)
+        for h in hs:
+            dawn.dawn_graph_free(h)
