@@ -128,6 +128,9 @@ struct alignas(128) SvCtl {
     int qn[3][kSvMaxGraphs];
     AdmitEntry admit[2][kSvMaxAdmit];     // sorted by (graph, src)
     long long seg_prefix[2][kSvMaxAdmit + 1];  // row-fill work items before each entry
+    // the host mailbox {batch_seq, stop} as the last CTA read it during
+    // iteration t, in mbox[t & 1] (CTA 0 decides with it one iteration later)
+    alignas(128) unsigned mbox[2][32];
 };
 
 struct SvArgs {
@@ -186,6 +189,8 @@ __device__ __forceinline__ AdmitEntry ld_entry(const AdmitEntry* p) {
     return e;
 }
 
+constexpr int kSvSnapMax = 2 + kSvMaxGraphs + 1;  // ints a barrier snapshot copies at most (per array)
+
 // With `snap`, thread 0 copies nsnap ints (and nsnap2 from snap2) after the
 // acquire into shared memory for the whole CTA (one L2 request per CTA, not
 // one per warp).
@@ -209,8 +214,18 @@ __device__ bool sv_barrier(SvCtl* ctl, unsigned* count, unsigned& target, long l
             if ((++polls & 15u) == 0 && sv_ld_relaxed_s32(&ctl->status) != DEV_OK) { ok = 0; break; }
         }
         if (ok) {
-            for (int i = 0; i < nsnap; ++i) s_snap[i] = sv_ld_relaxed_s32(snap + i);
-            for (int i = 0; i < nsnap2; ++i) s_snap2[i] = sv_ld_relaxed_s32(snap2 + i);
+            // every load issued before the first store: one round trip, not one per word
+            int v[kSvSnapMax], v2[kSvSnapMax];
+#pragma unroll
+            for (int i = 0; i < kSvSnapMax; ++i) {
+                v[i] = i < nsnap ? sv_ld_relaxed_s32(snap + i) : 0;
+                v2[i] = i < nsnap2 ? sv_ld_relaxed_s32(snap2 + i) : 0;
+            }
+#pragma unroll
+            for (int i = 0; i < kSvSnapMax; ++i) {
+                if (i < nsnap) s_snap[i] = v[i];
+                if (i < nsnap2) s_snap2[i] = v2[i];
+            }
         }
         s_ok = ok;
     }
@@ -259,15 +274,23 @@ __device__ __forceinline__ unsigned sv_push_arcs(uint64_t* Vw, uint64_t* Fw, con
     for (int q = 0; q < 4; ++q) x[q] = q < cnt ? __ldg(ci + j + q) : 0;
 #pragma unroll
     for (int q = 0; q < 4; ++q) have[q] = q < cnt ? __ldcg(Vw + x[q]) : ~0ull;
+    // The lanes of x not visited at the start of the iteration (have is read
+    // after the last barrier, so it holds every earlier iteration's bits) are
+    // new at this iteration, whichever thread sets them first: the visited and
+    // frontier words take them together (the visited word's old value is not
+    // needed, which spares a round trip), and a repeated claim of the same
+    // lane by another thread writes the same distance.  The key is queued by
+    // the claim that finds its frontier word empty.
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        nb[q] = f & ~have[q];
-        if (nb[q]) nb[q] &= ~atomicOr(reinterpret_cast<unsigned long long*>(Vw + x[q]), nb[q]);
-    }
+    for (int q = 0; q < 4; ++q) nb[q] = f & ~have[q];
     unsigned app = 0u;
 #pragma unroll
-    for (int q = 0; q < 4; ++q)
-        if (nb[q] && atomicOr(reinterpret_cast<unsigned long long*>(Fw + x[q]), nb[q]) == 0ull) app |= 1u << q;
+    for (int q = 0; q < 4; ++q) {
+        if (nb[q]) {
+            atomicOr(reinterpret_cast<unsigned long long*>(Vw + x[q]), nb[q]);
+            if (atomicOr(reinterpret_cast<unsigned long long*>(Fw + x[q]), nb[q]) == 0ull) app |= 1u << q;
+        }
+    }
     unsigned long long grew = 0ull, over = 0ull;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
@@ -372,6 +395,8 @@ __global__ void __launch_bounds__(kSvThreads, 1) serve_kernel(SvArgs a) {
             s_take = seq != seen_seq ? (int)min(hs->count, (unsigned)kSvMaxAdmit) : -1;
             if (s_take >= 0) seen_seq = seq;
             for (int i = 0; i < 32; ++i) ctl->pub[0][i] = ctl->pub[1][i] = 0;
+            ctl->mbox[1][0] = seen_seq;  // what iteration 0 decides with: nothing new yet
+            ctl->mbox[1][1] = 0u;
         }
         __syncthreads();
         const int take = s_take;
@@ -413,12 +438,22 @@ __global__ void __launch_bounds__(kSvThreads, 1) serve_kernel(SvArgs a) {
         const int par = t & 1;
         const int na = s_pub[0];
         const long long* seg = ctl->seg_prefix[par];
-        // CTA 0 issues its reads of the host mailbox now and uses them at the
-        // end of the iteration, so the PCIe round trip overlaps the level
+        // The host mailbox is read over PCIe (~2 us, during which the reading
+        // thread stalls) by the last CTA, which has the least work when the
+        // frontiers are small; CTA 0 decides with what it read during the
+        // iteration before (ordered by that iteration's barrier), so a batch or
+        // a stop is taken one iteration later.  The load of that copy is
+        // issued now and used at the end of the iteration.
         unsigned seq_early = 0u, stop_early = 0u;
+        if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) {
+            const unsigned sq = sv_ld_relaxed_sys(&hs->batch_seq);
+            const unsigned sp = *(volatile unsigned*)&hs->stop;
+            ctl->mbox[par][0] = sq;
+            ctl->mbox[par][1] = sp;
+        }
         if (blockIdx.x == 0 && threadIdx.x == 0) {
-            seq_early = sv_ld_relaxed_sys(&hs->batch_seq);
-            stop_early = *(volatile unsigned*)&hs->stop;
+            seq_early = __ldcg(&ctl->mbox[par ^ 1][0]);
+            stop_early = __ldcg(&ctl->mbox[par ^ 1][1]);
         }
         // lanes admitted now, per graph
         if (na > 0) {
@@ -762,9 +797,11 @@ __global__ void __launch_bounds__(kSvThreads, 1) serve_kernel(SvArgs a) {
             __shared__ int s_take;
             const int npar = par ^ 1;
             if (threadIdx.x == 0) {
-                const unsigned seq = seq_early;
                 s_take = 0;
-                if (seq != seen_seq) {
+                if (seq_early != seen_seq) {
+                    // a new batch: read its sequence number here too, so that this
+                    // thread's own read orders its reads of the batch
+                    const unsigned seq = sv_ld_acquire_sys(&hs->batch_seq);
                     __threadfence_system();  // the batch was written before its sequence number
                     s_take = (int)min(hs->count, (unsigned)kSvMaxAdmit);
                     seen_seq = seq;
