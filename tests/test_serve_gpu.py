@@ -278,3 +278,35 @@ def test_idle_fast_path_on_a_low_degree_graph(dawn, dist_bytes):
         dawn.dawn_serve_destroy(s)
         for h in hs:
             dawn.dawn_graph_free(h)
+
+
+def test_idle_fast_path_overflow_and_int32(dawn):
+    """The idle fast path keeps the loop's int16 rule: on a 40,000-vertex
+    path served in AUTO mode, a lone int16 request from one end fails with
+    DAWN_E_OVERFLOW (levels past 32767), a lone int32 request completes
+    exactly, and so do int16 requests whose levels all fit."""
+    n = 40000
+    s_ = np.arange(n - 1)
+    path = gg.from_arcs(n, np.r_[s_, s_ + 1], np.r_[s_ + 1, s_], symmetric=True)
+    h = dawn.dawn_graph_upload(path.row_ptr, path.col_idx, flags=dawn.DAWN_SYMMETRIC)
+    s = dawn.dawn_serve_create([h], 0, 64)
+    try:
+        out16 = np.zeros((1, n), dtype=np.int16)
+        r16 = dawn.dawn_serve_submit(s, 0, np.array([0], dtype=np.int32), dist_bytes=2, dist_out=out16)
+        dawn.dawn_serve_drain(s, 120000)
+        with pytest.raises(dawn.DawnError) as ei:
+            dawn.dawn_serve_poll(s, r16)
+        assert ei.value.code == dawn.DAWN_E_OVERFLOW
+        out32 = torch.zeros((1, n), dtype=torch.int32, device="cuda")
+        r32 = dawn.dawn_serve_submit(s, 0, np.array([0], dtype=np.int32), dist_bytes=4, dist_out=out32)
+        wait_done(dawn, s, r32)
+        np.testing.assert_array_equal(out32[0].cpu().numpy(), np.arange(n))
+        mid = np.array([n // 2, n // 2 + 7], dtype=np.int32)  # farthest levels 20,000 and 20,006: they fit
+        out_m = np.zeros((2, n), dtype=np.int16)
+        rm = dawn.dawn_serve_submit(s, 0, mid, dist_bytes=2, dist_out=out_m)
+        wait_done(dawn, s, rm)
+        for j, src in enumerate(mid):
+            np.testing.assert_array_equal(out_m[j], np.abs(np.arange(n) - int(src)).astype(np.int16))
+    finally:
+        dawn.dawn_serve_destroy(s)
+        dawn.dawn_graph_free(h)
