@@ -1483,7 +1483,8 @@ int sssp_dynamic_smem(int bitmap_bytes) { return bitmap_bytes > kPushBufBytes ? 
 
 int sssp_occupancy(dawn_graph* g) {
     int nb = 0;
-    DAWN_CUDA_TRY(cudaFuncSetAttribute(sssp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBitmapMax));
+    DAWN_CUDA_TRY(cudaFuncSetAttribute(sssp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       sssp_dynamic_smem(kSmemBitmapMax)));
     const size_t words4 = (size_t)(g->nwords + 3) / 4 * 4;
     g->sssp_smem_bytes = words4 * 4 <= (size_t)kSmemBitmapMax ? (int)(words4 * 4) : 0;
     DAWN_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sssp_kernel, kThreads,
@@ -1620,7 +1621,8 @@ int noalloc_setup(NoAllocDevice** out) {
         void* p = nullptr;
         DAWN_CUDA_TRY(cudaGetSymbolAddress(&p, g_noalloc_scratch));
         DAWN_CUDA_TRY(cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev));
-        DAWN_CUDA_TRY(cudaFuncSetAttribute(sssp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBitmapMax));
+        DAWN_CUDA_TRY(cudaFuncSetAttribute(sssp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       sssp_dynamic_smem(kSmemBitmapMax)));
         DAWN_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d.blocks_per_sm, sssp_kernel, kThreads,
                                                                     kPushBufBytes));
         if (d.blocks_per_sm < 1) return fail(DAWN_E_CUDA, "persistent SSSP kernel cannot be resident on an SM");
