@@ -52,6 +52,7 @@ struct alignas(128) CtrSlot {
                                // list pulls: vertices their look-ahead showed at the next level, high 32 bits
     unsigned long long lr;     // nonzero when a queued row has more than kEntryArcs arcs; list pulls
                                // (which queue nothing): the out-degree sum of the look-ahead's vertices
+                               // (low 32 bits) and how many of them it placed two levels ahead (high 32)
     unsigned long long pad[11];
 };
 

@@ -47,6 +47,9 @@ namespace {
 #ifndef DAWN_LOOKAHEAD
 #define DAWN_LOOKAHEAD 1  // list pulls look one level ahead for the stop at the component's size
 #endif
+#ifndef DAWN_LOOKAHEAD_DEEP
+#define DAWN_LOOKAHEAD_DEEP 1  // and two levels ahead for vertices with short rows
+#endif
 #ifndef DAWN_SSSP_SMEM_BITMAP_MAX
 #define DAWN_SSSP_SMEM_BITMAP_MAX (200 * 1024)
 #endif
@@ -786,23 +789,45 @@ __device__ __forceinline__ bool two_hop_hit(const SsspArgs& a, int2 h0, int2 h1,
     return hit;
 }
 
-// A vertex v the look-ahead placed at level step + 1 (lanes with `ahead`;
-// called by the lanes that ran the test, possibly divergent): dist is
-// written now, and the count and out-degrees go straight to the level's
-// counter slot (step % 3, as the loop picks it) with one pair of atomics
-// per warp: the count in nc's high word, the degrees in lr (a list pull
-// queues nothing).  indeg: v's in-degree (its out-degree on a symmetric graph).
-__device__ __forceinline__ void look_ahead(const SsspArgs& a, bool ahead, int v, int indeg, int lane, int step,
-                                           bool symmetric) {
-    const unsigned hb = __ballot_sync(__activemask(), ahead);
-    if (!ahead) return;
-    a.dist[v] = step + 1;
+// The look-ahead's third hop, for a vertex v whose in-degree and whose
+// in-neighbours' in-degrees are at most two (so that h0 and h1 hold every
+// in-neighbour w of each in-neighbour u of v): whether one of the first two
+// in-neighbours x of some w (g[] = first2 of h0.x, h0.y, h1.x, h1.y) was
+// reached before the level `step`.
+__device__ __forceinline__ bool three_hop_hit(const SsspArgs& a, const int2 (&g)[4], int step) {
+    int dx[8];
+#pragma unroll
+    for (int x = 0; x < 4; ++x) {
+        dx[2 * x] = g[x].x >= 0 ? __ldcg(a.dist + g[x].x) : -1;
+        dx[2 * x + 1] = g[x].y >= 0 ? __ldcg(a.dist + g[x].y) : -1;
+    }
+    bool hit = false;
+#pragma unroll
+    for (int x = 0; x < 8; ++x) hit |= dx[x] >= 0 && dx[x] < step;
+    return hit;
+}
+
+// A vertex v the look-ahead placed at level step + 1 (lanes with `ahead`) or
+// step + 2 (lanes with `ahead2`; the two exclude each other), called by the
+// lanes that ran the test, possibly divergent: dist is written now, and the
+// count and out-degrees go straight to the level's counter slot (step % 3,
+// as the loop picks it) with one pair of atomics per warp: the count of
+// both in nc's high word; in lr (a list pull queues nothing) the degrees in
+// the low word and the count of step + 2 placements in the high word.
+// indeg: v's in-degree (its out-degree on a symmetric graph).
+__device__ __forceinline__ void look_ahead(const SsspArgs& a, bool ahead, bool ahead2, int v, int indeg, int lane,
+                                           int step, bool symmetric) {
+    const unsigned am = __activemask();
+    const unsigned hb = __ballot_sync(am, ahead || ahead2);
+    const unsigned hb2 = __ballot_sync(am, ahead2);
+    if (!(ahead || ahead2)) return;
+    a.dist[v] = ahead ? step + 1 : step + 2;
     const unsigned deg = (unsigned)(symmetric ? indeg : (__ldg(a.row_ptr + v + 1) - __ldg(a.row_ptr + v)));
     const unsigned dsum = __reduce_add_sync(hb, deg);  // < m < 2^31: row_ptr is int32
     if (lane == __ffs(hb) - 1) {
         CtrSlot* out = &a.ctl->ctr[a.bar_parity][step % 3];
         atomicAdd(&out->nc, (unsigned long long)__popc(hb) << 32);
-        atomicAdd(&out->lr, (unsigned long long)dsum);
+        atomicAdd(&out->lr, ((unsigned long long)__popc(hb2) << 32) | dsum);
     }
 }
 
@@ -904,7 +929,29 @@ __device__ __noinline__ LevelCount list_pull_level(const SsspArgs& a, int step, 
             // runs, finds them again with the same value.
             const int2 h0 = f2.x >= 0 ? __ldg(a.first2 + f2.x) : make_int2(-1, -1);
             const int2 h1 = f2.y >= 0 ? __ldg(a.first2 + f2.y) : make_int2(-1, -1);
-            look_ahead(a, two_hop_hit(a, h0, h1, step), v, ie - ib, lane, step, symmetric);
+            // Two levels ahead, for short rows: when v has at most two in-arcs
+            // and so has each of its in-neighbours u, the two-hop test reads
+            // every in-neighbour w of every u; if none was reached before this
+            // level, no u is found at it, so d(u) >= step + 1 for all of them
+            // and d(v) >= step + 2.  A w with an in-neighbour x reached before
+            // this level (x among w's first two) bounds d(w) <= step, so
+            // d(v) <= step + 2: then v is placed at step + 2.  The first two
+            // in-neighbours of the w are loaded beside their distances.
+            bool deep = DAWN_LOOKAHEAD_DEEP && ie - ib <= 2;
+            if (deep) {
+                const int lu0 = f2.x >= 0 ? __ldg(a.in_ptr + f2.x + 1) - __ldg(a.in_ptr + f2.x) : 0;
+                const int lu1 = f2.y >= 0 ? __ldg(a.in_ptr + f2.y + 1) - __ldg(a.in_ptr + f2.y) : 0;
+                deep = lu0 <= 2 && lu1 <= 2;
+            }
+            int2 gw[4];
+            {
+                const int ws[4] = {h0.x, h0.y, h1.x, h1.y};
+#pragma unroll
+                for (int x = 0; x < 4; ++x) gw[x] = (deep && ws[x] >= 0) ? __ldg(a.first2 + ws[x]) : make_int2(-1, -1);
+            }
+            const bool hit = two_hop_hit(a, h0, h1, step);
+            const bool hit2 = !hit && deep && three_hop_hit(a, gw, step);
+            look_ahead(a, hit, hit2, v, ie - ib, lane, step, symmetric);
         }
         warp_keep(has && !found, v, lane, keep, s_cn);
     }
@@ -1437,20 +1484,22 @@ __global__ void __launch_bounds__(kThreads, DAWN_SSSP_MIN_CTAS) sssp_kernel(Sssp
             return;
         if (tracer) trace_rec(a, tslot, kind == kPush ? 2 : (kind == kBitmapPull ? 3 : 5), step + 1, (long long)s_snap[1]);
         if (kind == kListPull && (s_snap[3] >> 32) != 0 && L.kind != kStop) {
-            // the list pull's look-ahead showed la vertices at level step + 2;
-            // when they are all that is left of the component (their dist is
-            // written), that level is not run.  It counts as a pull level (a
-            // pull test decided it) in place of the one the rule had chosen.
+            // the list pull's look-ahead showed la vertices at levels step + 2
+            // and step + 3 (la2 of them at step + 3); when they are all that
+            // is left of the component (their dist is written), those levels
+            // are not run.  They count as pull levels (pull tests decided
+            // them), the first in place of the one the rule had chosen.
             const long long la = (long long)(s_snap[3] >> 32);
             if (L.reached + la >= a.reach_target) {
                 __syncthreads();  // every thread has read L.kind
                 if (threadIdx.x == 0) {
+                    const bool la2 = (s_snap[4] >> 32) != 0;
                     L.reached += la;
-                    L.edges += (long long)s_snap[4];
+                    L.edges += (long long)(s_snap[4] & 0xffffffffull);
                     if (L.kind == kPush) --L.pushes;
                     else --L.pulls;
-                    ++L.pulls;
-                    L.levels = step + 2;
+                    L.pulls += la2 ? 2 : 1;
+                    L.levels = step + (la2 ? 3 : 2);
                 }
                 break;
             }

@@ -498,9 +498,11 @@ def _trace_levels(dawn, h, g, src):
 def test_lookahead_stop_folds_the_last_level(dawn):
     """A list pull on a symmetric graph tests the candidates it leaves
     unreached one level further (through their first two in-neighbours and
-    theirs).  When that shows every vertex left in the source's component,
-    the loop stops there and the last level is not run: the trace then ends
-    with a list pull one step short of the eccentricity.  Distances and
+    theirs), and two levels further for vertices whose rows and whose
+    in-neighbours' rows are short.  When that shows every vertex left in the
+    source's component, the loop stops there and the last levels are not run:
+    the trace then ends with a list pull one or two steps short of the
+    eccentricity.  Distances and
     statistics (reached, E_r, levels, push + pull levels) stay those of the
     oracle whether or not it folds.  The second graph hangs a K4 off a path:
     the K4's far vertices have a first two in-neighbours that lie at their own
@@ -517,7 +519,7 @@ def test_lookahead_stop_folds_the_last_level(dawn):
             check_stats(base, d, st)
             assert st["push_steps"] + st["pull_steps"] == st["levels"]
             last = recs[-1]
-            if last[0] == 5 and last[1] == st["levels"] - 1:
+            if last[0] == 5 and last[1] in (st["levels"] - 1, st["levels"] - 2):
                 folded += 1
             else:
                 assert last[1] == st["levels"], (src, recs[-1], st)
@@ -556,3 +558,43 @@ def test_lookahead_stop_folds_the_last_level(dawn):
                 assert recs[-1][1] == st["levels"], (src, recs[-1], st)  # the last level ran
     finally:
         dawn.dawn_graph_free(h)
+
+
+def test_lookahead_two_levels_on_tails(dawn):
+    """An RMAT graph with a two-vertex tail hung on every vertex of degree 1:
+    a tail's first vertex has two in-arcs and its end one, so a list pull at
+    the level of the leaf the tail hangs on places the first vertex one level
+    ahead (two-hop test) and the end two levels ahead (both rows short, the
+    leaf's neighbour reached before the level).  When the farthest base level
+    is a list pull, both tail levels fold into it: the trace ends two steps
+    short of the eccentricity.  Every source's distances and statistics are
+    the oracle's whether or not it folds."""
+    base = gg.rmat(14, seed=4)
+    rp, ci, n = base.row_ptr, base.col_idx, base.n
+    deg = np.diff(rp)
+    src_l = list(np.repeat(np.arange(n), deg))
+    dst_l = list(ci)
+    nn = n
+    for leaf in np.nonzero(deg == 1)[0]:
+        t1, t2 = nn, nn + 1
+        nn += 2
+        src_l += [int(leaf), t1, t1, t2]
+        dst_l += [t1, int(leaf), t2, t1]
+    g = gg.from_arcs(nn, src_l, dst_l, symmetric=True)
+    h = upload(dawn, g)
+    double = 0
+    try:
+        for src in gg.sample_sources(base, 24, seed=31):
+            src = int(src)
+            d, st, recs = _trace_levels(dawn, h, g, src)
+            np.testing.assert_array_equal(d, oracle.sssp_sovm(g.row_ptr, g.col_idx, src), err_msg=f"src={src}")
+            check_stats(g, d, st)
+            assert st["push_steps"] + st["pull_steps"] == st["levels"]
+            last = recs[-1]
+            if last[0] == 5 and last[1] == st["levels"] - 2:
+                double += 1
+            elif not (last[0] == 5 and last[1] == st["levels"] - 1):
+                assert last[1] == st["levels"], (src, recs[-1], st)
+    finally:
+        dawn.dawn_graph_free(h)
+    assert double >= 1
