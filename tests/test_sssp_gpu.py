@@ -598,3 +598,43 @@ def test_lookahead_two_levels_on_tails(dawn):
     finally:
         dawn.dawn_graph_free(h)
     assert double >= 1
+
+
+def test_lookahead_two_levels_needs_short_second_hop(dawn):
+    """The two-level test needs every in-neighbour of v's in-neighbours read:
+    with a fork on every leaf (t1 joined to the leaf and to two ends t2, t3),
+    t1 has three in-arcs, so the ends cannot be placed two levels ahead.  When
+    the farthest vertices are such ends, the level before them runs and its
+    one-level look-ahead folds the last level: the trace ends one step short
+    of the eccentricity, never two.  Distances and statistics are the
+    oracle's."""
+    base = gg.rmat(14, seed=4)
+    rp, ci, n = base.row_ptr, base.col_idx, base.n
+    deg = np.diff(rp)
+    src_l = list(np.repeat(np.arange(n), deg))
+    dst_l = list(ci)
+    nn = n
+    ends = set()
+    for leaf in np.nonzero(deg == 1)[0]:
+        t1, t2, t3 = nn, nn + 1, nn + 2
+        nn += 3
+        for x, y in ((int(leaf), t1), (t1, t2), (t1, t3)):
+            src_l += [x, y]
+            dst_l += [y, x]
+        ends.update((t2, t3))
+    g = gg.from_arcs(nn, src_l, dst_l, symmetric=True)
+    h = upload(dawn, g)
+    checked = 0
+    try:
+        for src in gg.sample_sources(base, 24, seed=31):
+            src = int(src)
+            d, st, recs = _trace_levels(dawn, h, g, src)
+            np.testing.assert_array_equal(d, oracle.sssp_sovm(g.row_ptr, g.col_idx, src), err_msg=f"src={src}")
+            check_stats(g, d, st)
+            assert st["push_steps"] + st["pull_steps"] == st["levels"]
+            if st["levels"] > 0 and set(np.nonzero(d == d.max())[0].tolist()) <= ends:
+                assert recs[-1][1] >= st["levels"] - 1, (src, recs[-1], st)
+                checked += 1
+    finally:
+        dawn.dawn_graph_free(h)
+    assert checked >= 1
